@@ -1,0 +1,257 @@
+/*
+ * crum.h -- C ABI of the B300 capture/restore library for device-resident
+ * managed allocations (CRUM: Checkpoint-Restart Support for CUDA's Unified
+ * Memory, Garg, Mohan, Sullivan, Cooperman, 2018).
+ *
+ * Conventions for every entry point:
+ *   - Returns a crum_status; CRUM_OK is 0.  No C++ exception crosses this
+ *     boundary.  crum_last_error() gives a message for the calling thread's
+ *     last failure.
+ *   - "device pointer" means a pointer the current CUDA device can read
+ *     and write (cudaMalloc, cudaMallocManaged with the device as preferred
+ *     location, or a PyTorch CUDA tensor's data pointer).  "host pointer" is
+ *     ordinary process memory.
+ *   - crum_stream_t is a cudaStream_t passed as an opaque pointer (0 means
+ *     the legacy default stream).
+ *   - Work is stream ordered: a call that takes a stream sees every earlier
+ *     operation on that stream and nothing later.
+ *   - Page size is fixed at CRUM_PAGE_SIZE bytes.  Page p of an allocation
+ *     of B bytes covers bytes [p*P, min((p+1)*P, B)); the last page may be
+ *     partial ("tail page").
+ *   - The library owns sets, images, staging buffers, pinned host memory and
+ *     hash tables.  The caller owns the registered allocations; the library
+ *     never frees, moves or resizes them.
+ *
+ * Page hash used for dirty detection (stands in for the write-fault dirty
+ * tracking of Algorithm 1 / Section 3.2, since device stores cannot be
+ * trapped): for a page with v valid bytes, read as ceil(v/8) little-endian
+ * 64-bit words w_i (a final partial word zero-padded),
+ *     h = sum_i mix(w_i XOR (i * 0x9E3779B97F4A7C15))   (mod 2^64)
+ * where mix is splitmix64's output function (Steele, Lea, Flood, 2014).
+ *
+ * Image byte layout (little-endian), produced by crum_checkpoint and read by
+ * crum_image_load / crum_restore:
+ *   header (64 B): "CRUMIMG1", u32 version=1, u32 flags (bit0 full),
+ *     u64 seq, u64 parent seq (all ones for a full image), u32 page size,
+ *     u32 allocation count A, u64 dirty page count n, u64 payload offset
+ *     (64+16A+16n), u64 image size including the trailer;
+ *   allocation table A x {u32 id, u32 0, u64 bytes};
+ *   page table n x {u32 allocation index, u32 page index}, ascending;
+ *   page hashes n x u64;
+ *   payload n x CRUM_PAGE_SIZE bytes (valid bytes, then zeros);
+ *   trailer u64 = the hash formula above over every preceding image byte,
+ *     word indices counted from the start of the image.
+ */
+#ifndef CRUM_H
+#define CRUM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CRUM_PAGE_SIZE 65536u
+#define CRUM_NO_PARENT 0xFFFFFFFFFFFFFFFFull
+
+typedef enum crum_status {
+    CRUM_OK = 0,
+    CRUM_EINVAL = 1,      /* bad argument (null, misaligned, overlapping, out of range) */
+    CRUM_ENOMEM = 2,      /* device or pinned host allocation failed */
+    CRUM_EBUSY = 3,       /* the set has work in flight that forbids the call */
+    CRUM_ECUDA = 4,       /* a CUDA runtime call failed; crum_last_error has its text */
+    CRUM_EIO = 5,         /* the image sink or a file read/write failed */
+    CRUM_EMISMATCH = 6,   /* image allocation table differs from the set's registrations */
+    CRUM_ECOLLISION = 7,  /* verify mode found pages whose hash matched but bytes differ */
+    CRUM_ETIMEOUT = 8,    /* a bounded wait ran out (host wait or a device-side spin) */
+    CRUM_ECORRUPT = 9     /* image failed its structural or checksum checks */
+} crum_status;
+
+typedef void *crum_stream_t; /* a cudaStream_t */
+typedef struct crum_set crum_set;
+typedef struct crum_image crum_image;
+
+/* Where a checkpoint image goes once it has reached host memory. */
+typedef enum crum_sink {
+    CRUM_SINK_MEMORY = 0, /* keep the image in library-owned pinned host memory */
+    CRUM_SINK_FILE = 1,   /* also write it to <sink_dir>/crum_<set>_<seq>.img */
+    CRUM_SINK_NULL = 2    /* drain to host, then drop the payload (link benchmark) */
+} crum_sink;
+
+typedef struct crum_config {
+    int device;                /* CUDA device ordinal the set lives on */
+    uint64_t staging_bytes;    /* device staging budget, split into two halves that
+                                  alternate between consecutive checkpoints; 0: 1 GiB */
+    uint64_t chunk_bytes;      /* device->host drain chunk; 0: 64 MiB */
+    uint64_t host_pool_bytes;  /* initial pinned host pool for images; 0: grow on demand */
+    int sink;                  /* crum_sink */
+    const char *sink_dir;      /* directory for CRUM_SINK_FILE (copied at create) */
+    int verify;                /* 1: keep a device copy of the last checkpointed
+                                  contents so CRUM_VERIFY checkpoints can byte-compare */
+    int fsync;                 /* 1: fsync image files before reporting PERSISTED */
+} crum_config;
+
+/* Fill *cfg with defaults (device 0, 1 GiB staging, 64 MiB chunks, memory sink). */
+void crum_config_default(crum_config *cfg);
+
+/* Thread-local text of the calling thread's last error ("" if none).  The
+   pointer stays valid until that thread's next crum_* call. */
+const char *crum_last_error(void);
+
+/* Library version string, e.g. "crum-b300 1.0 sm_103a". */
+const char *crum_version(void);
+
+/* ---- registration set (Section 3.2: regions tracked per allocation;
+        Algorithm 1 "create region": a new region starts with every page
+        dirty) ---- */
+
+/* Create a set on cfg->device (NULL: defaults).  Allocates the staging
+   halves, hash table capacity grows with registrations.
+   Errors: EINVAL (bad config), ENOMEM, ECUDA. */
+crum_status crum_set_create(const crum_config *cfg, crum_set **out);
+
+/* Wait for all in-flight checkpoints of the set to persist, stop its writer
+   thread and free its device/host memory.  Images the caller still holds
+   stay valid (they keep their own host memory).  NULL is a no-op. */
+crum_status crum_set_destroy(crum_set *set);
+
+/* Register the allocation [ptr, ptr+bytes) (device pointer, caller owned).
+   ptr must be 16-byte aligned and bytes > 0, and the range must not overlap
+   a registered one; otherwise EINVAL.  Its pages are dirty at the next
+   checkpoint (Algorithm 1: a new region starts all dirty).  *alloc_id gets
+   a set-unique id.  Registration order fixes the page order of images.
+   Errors: EINVAL, EBUSY (a checkpoint is being captured), ENOMEM. */
+crum_status crum_register(crum_set *set, void *ptr, size_t bytes, uint32_t *alloc_id);
+
+/* Remove a registration.  Errors: EINVAL (unknown id), EBUSY. */
+crum_status crum_unregister(crum_set *set, uint32_t alloc_id);
+
+/* Number of registrations and total pages of the set. */
+crum_status crum_set_info(const crum_set *set, uint32_t *n_allocs, uint64_t *n_pages);
+
+/* ---- checkpoint (Section 3.4: read every region from the device and save
+        it; Section 3.3: drain the device, then let storage proceed while the
+        application runs) ---- */
+
+#define CRUM_INCR   0  /* pages whose hash changed, plus never-checkpointed pages */
+#define CRUM_FULL   1  /* every page */
+#define CRUM_VERIFY 2  /* also byte-compare hash-clean pages (needs cfg.verify) */
+
+/* Take a checkpoint of every registered allocation as of this point in
+   app_stream's order.  The capture runs on the set's own streams after the
+   work already queued on app_stream; app_stream is made to wait (on the
+   device) only until the dirty pages are copied into device staging
+   ("captured"); draining to host and persisting continue in the background.
+   *out receives a new image handle (refcount 1) whose parent is the
+   previous checkpoint's image.  The first checkpoint of a set, and any
+   checkpoint after a failed one, is full.
+   Returns without waiting for the device when the staging half can hold
+   every page of the set; otherwise it waits on the host until the dirty
+   count is known (the hash pass), then proceeds in staging-sized chunks,
+   and app_stream waits until the last chunk is captured.
+   Errors: EINVAL (no registrations, CRUM_VERIFY without cfg.verify),
+   ENOMEM, ECUDA, ETIMEOUT. */
+crum_status crum_checkpoint(crum_set *set, crum_stream_t app_stream, int flags,
+                            crum_image **out);
+
+#define CRUM_WAIT_CAPTURED  1  /* dirty pages copied to device staging */
+#define CRUM_WAIT_DRAINED   2  /* image bytes are in host memory */
+#define CRUM_WAIT_PERSISTED 3  /* the sink has accepted the image */
+
+/* Block until the image reaches stage `what` or timeout_ns passes (<0: no
+   limit).  Returns the image's final status once it is PERSISTED or failed:
+   EIO (sink failure; the set's next checkpoint is then full), ECOLLISION
+   (verify mode found collisions; the image is still complete and correct,
+   the colliding pages were captured), ECUDA, ETIMEOUT. */
+crum_status crum_image_wait(crum_image *img, int what, int64_t timeout_ns);
+
+typedef struct crum_image_info {
+    uint64_t seq;            /* checkpoint sequence number within the set */
+    uint64_t parent_seq;     /* CRUM_NO_PARENT for a full image */
+    uint64_t n_dirty;        /* pages in the image */
+    uint64_t n_pages;        /* pages of the set when it was taken */
+    uint64_t image_bytes;    /* serialized size, trailer included */
+    uint64_t checksum;       /* trailer value */
+    uint64_t collisions;     /* verify mode: hash-clean pages whose bytes differed */
+    uint32_t n_allocs;
+    uint32_t full;           /* 1 if this image holds every page */
+    int stage;               /* highest CRUM_WAIT_* reached (0: submitted) */
+    int status;              /* crum_status of the image so far */
+    double t_captured_ms;    /* device time submit->captured (CUDA events) */
+    double t_drained_ms;     /* device time submit->drained */
+    double t_persisted_ms;   /* host time submit->persisted */
+} crum_image_info;
+
+/* Fill *info.  Fields past `stage` are zero until the image gets there. */
+crum_status crum_image_info_get(const crum_image *img, crum_image_info *info);
+
+/* Copy the serialized image (image_bytes bytes) into host memory dst, which
+   must hold dst_bytes >= image_bytes.  Waits for DRAINED.
+   Errors: EINVAL (dst too small), EIO. */
+crum_status crum_image_copy(crum_image *img, void *dst, uint64_t dst_bytes);
+
+/* Write the serialized image to a file.  Waits for DRAINED.  Errors: EIO. */
+crum_status crum_image_save(crum_image *img, const char *path);
+
+/* Read an image from a file or a host buffer and check it on the set's
+   device: structure, sizes and the trailer checksum (ECORRUPT on any
+   failure, ENOENT-like failures are EIO).  parent must be the image with
+   seq equal to the file's parent seq (NULL for a full image), else
+   EMISMATCH.  The new handle holds a reference to parent. */
+crum_status crum_image_load(crum_set *set, const char *path, crum_image *parent,
+                            crum_image **out);
+crum_status crum_image_from_bytes(crum_set *set, const void *bytes, uint64_t n,
+                                  crum_image *parent, crum_image **out);
+
+/* Drop a reference.  The image's memory is freed, and its parent released,
+   when the last reference goes. */
+crum_status crum_image_release(crum_image *img);
+
+/* ---- restore (Section 3.4: replay allocations, copy the saved data back;
+        Section 5: regions must come back at matching places) ---- */
+
+/* Restore the set's registered allocations to the state captured by
+   chain_end: the chain's full base image first, then each incremental in
+   order, later pages winning.  Only each page's valid bytes are written.
+   The set's hash table becomes the chain's hashes, so the next incremental
+   checkpoint is relative to chain_end (its parent).  Stream ordered on
+   `stream`; returns once the work is queued, and the caller's host image
+   memory stays owned by the images.
+   Errors: EMISMATCH (allocation count or sizes differ, in registration
+   order), ECORRUPT (broken chain), EBUSY (checkpoint being captured),
+   ECUDA. */
+crum_status crum_restore(crum_set *set, const crum_image *chain_end, crum_stream_t stream);
+
+/* ---- single-step entry points (each a single step of the path, for tests
+        and for callers that manage their own memory) ---- */
+
+/* Page hashes of one allocation: out[p] for every page p of [ptr, ptr+bytes).
+   ptr 16-byte aligned device pointer; out a device array of
+   ceil(bytes/65536) u64.  Errors: EINVAL, ECUDA. */
+crum_status crum_hash_pages(const void *ptr, uint64_t bytes, uint64_t *out,
+                            crum_stream_t stream);
+
+/* The same hash over an arbitrary byte string with word indices starting at
+   first_index (the image checksum uses first_index 0 over the whole image):
+   *out (device u64) = sum of mix(w_i XOR (first_index+i)*phi).  ptr 16-byte
+   aligned device pointer.  Errors: EINVAL, ECUDA. */
+crum_status crum_hash_bytes(const void *ptr, uint64_t bytes, uint64_t first_index,
+                            uint64_t *out, crum_stream_t stream);
+
+/* Copy the set's committed page-hash table (n_pages u64, global page order:
+   registration order, then page index) to host memory.  Synchronous. */
+crum_status crum_get_hashes(crum_set *set, uint64_t *host_out, uint64_t n);
+
+/* Overwrite one committed page hash (test hook for collision injection:
+   verify mode must then report the page).  Synchronous. */
+crum_status crum_poke_hash(crum_set *set, uint64_t global_page, uint64_t value);
+
+/* Kernel launches the library has issued since load (for launch accounting). */
+uint64_t crum_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CRUM_H */
