@@ -1,0 +1,1141 @@
+// Registration sets, checkpoint orchestration, images, drain/writer threads
+// and the extern "C" entry points declared in include/crum.h.
+#include <fcntl.h>
+#include <sys/stat.h>
+#include <unistd.h>
+
+#include <algorithm>
+#include <cerrno>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+
+#include "engine.h"
+#include "kernels.h"
+
+using crum::Alloc;
+using crum::DevAlloc;
+using crum::Half;
+using crum::kHeaderBytes;
+using crum::kPage;
+
+namespace {
+
+thread_local std::string t_err;
+
+crum_status fail(crum_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return st;
+}
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return fail(CRUM_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                  __FILE__, __LINE__);                                                \
+  } while (0)
+
+// Makes `dev` current for the scope, restoring the caller's device after.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+constexpr uint64_t kDefaultStaging = 1ull << 30;
+constexpr uint64_t kDefaultChunk = 64ull << 20;
+constexpr int64_t kBackgroundLimitNs = 600ll * 1000 * 1000 * 1000;  // 10 min
+
+uint64_t pages_of(uint64_t bytes) { return (bytes + kPage - 1) / kPage; }
+uint64_t meta_bytes(uint64_t A, uint64_t n) { return kHeaderBytes + 16 * A + 16 * n; }
+uint64_t image_size(uint64_t A, uint64_t n) { return meta_bytes(A, n) + n * kPage + 8; }
+
+std::atomic<uint32_t> g_set_ids{0};
+
+// Poll an event until it completes or `limit_ns` passes.
+crum_status wait_event(cudaEvent_t ev, int64_t limit_ns) {
+  const auto t0 = std::chrono::steady_clock::now();
+  int spins = 0;
+  for (;;) {
+    const cudaError_t e = cudaEventQuery(ev);
+    if (e == cudaSuccess) return CRUM_OK;
+    if (e != cudaErrorNotReady)
+      return fail(CRUM_ECUDA, "event wait failed: %s", cudaGetErrorString(e));
+    if (limit_ns >= 0 &&
+        std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now() - t0)
+                .count() > limit_ns)
+      return fail(CRUM_ETIMEOUT, "timed out waiting for the device");
+    if (++spins > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+}
+
+void image_set_stage(crum_image* img, int stage, crum_status st, const std::string& err) {
+  std::lock_guard<std::mutex> lk(img->mu);
+  if (st != CRUM_OK && (img->status == CRUM_OK || img->status == CRUM_ECOLLISION)) {
+    img->status = st;
+    img->err = err;
+  }
+  if (stage > img->stage) img->stage = stage;
+  img->cv.notify_all();
+}
+
+void image_unref(crum_image* img) {
+  while (img != nullptr) {
+    if (img->refs.fetch_sub(1) != 1) return;
+    crum_image* parent = img->parent;
+    if (img->host != nullptr && img->pool) img->pool->free(img->host, img->host_len);
+    if (img->ev_submit) cudaEventDestroy(img->ev_submit);
+    if (img->ev_captured) cudaEventDestroy(img->ev_captured);
+    if (img->ev_drained) cudaEventDestroy(img->ev_drained);
+    delete img;
+    img = parent;
+  }
+}
+
+void image_ref(crum_image* img) {
+  if (img) img->refs.fetch_add(1);
+}
+
+// Quiesce: every queued drain is enqueued and the set's streams are idle.
+// Caller holds s->mu via lk.
+crum_status quiesce(crum_set* s, std::unique_lock<std::mutex>& lk) {
+  const bool ok = s->cv.wait_for(lk, std::chrono::seconds(600), [&] {
+    return s->half[0].drain_enqueued && s->half[1].drain_enqueued;
+  });
+  if (!ok) return fail(CRUM_ETIMEOUT, "timed out waiting for pending drains");
+  CK(cudaStreamSynchronize(s->cap_stream));
+  CK(cudaStreamSynchronize(s->drain_stream));
+  return CRUM_OK;
+}
+
+template <typename T>
+crum_status grow_device(T** p, size_t* cap, size_t need, bool keep) {
+  if (need <= *cap) return CRUM_OK;
+  size_t n = std::max(need, *cap + *cap / 2);
+  T* q = nullptr;
+  CK(cudaMalloc(&q, n * sizeof(T)));
+  if (keep && *p != nullptr && *cap > 0) CK(cudaMemcpy(q, *p, *cap * sizeof(T), cudaMemcpyDeviceToDevice));
+  if (*p != nullptr) CK(cudaFree(*p));
+  *p = q;
+  *cap = n;
+  return CRUM_OK;
+}
+
+// Device buffers sized for the current registrations.  Caller holds the
+// lock and has made sure nothing in flight uses the buffers it may move.
+crum_status ensure_capacity(crum_set* s, std::unique_lock<std::mutex>& lk) {
+  const size_t A = s->allocs.size();
+  const uint64_t words = (s->n_pages + 31) / 32;
+  const size_t meta_need = meta_bytes(A, s->n_pages);
+  const bool grow = A > s->alloc_cap || s->n_pages > s->h_cap || words + 1 > s->words_cap ||
+                    meta_need > s->half[0].meta_cap || meta_need > s->half[1].meta_cap ||
+                    (s->cfg.verify && s->n_pages > s->shadow_cap);
+  if (!grow) return CRUM_OK;
+  crum_status st = quiesce(s, lk);
+  if (st != CRUM_OK) return st;
+  size_t cap_a = s->alloc_cap;
+  st = grow_device(&s->d_allocs, &cap_a, std::max<size_t>(A, 16), false);
+  if (st != CRUM_OK) return st;
+  size_t cap_f = s->alloc_cap;
+  st = grow_device(&s->d_first_page, &cap_f, std::max<size_t>(A, 16), false);
+  if (st != CRUM_OK) return st;
+  s->alloc_cap = std::min(cap_a, cap_f);
+  st = grow_device(&s->d_h, &s->h_cap, s->n_pages, true);
+  if (st != CRUM_OK) return st;
+  size_t wc = s->words_cap;
+  st = grow_device(&s->d_mask, &wc, words + 1, false);
+  if (st != CRUM_OK) return st;
+  wc = s->words_cap;
+  st = grow_device(&s->d_word_offset, &wc, words + 1, false);
+  if (st != CRUM_OK) return st;
+  s->words_cap = wc;
+  for (Half& H : s->half) {
+    st = grow_device(&H.meta, &H.meta_cap, meta_need, false);
+    if (st != CRUM_OK) return st;
+  }
+  if (s->cfg.verify && s->n_pages > s->shadow_cap) {
+    if (s->d_shadow) CK(cudaFree(s->d_shadow));
+    s->d_shadow = nullptr;
+    CK(cudaMalloc(&s->d_shadow, s->n_pages * kPage));
+    s->shadow_cap = s->n_pages;
+    s->needs_full = true;  // the shadow starts empty
+  }
+  s->table_dirty = true;
+  return CRUM_OK;
+}
+
+crum_status upload_table(crum_set* s) {
+  if (!s->table_dirty) return CRUM_OK;
+  std::vector<DevAlloc> t(s->allocs.size());
+  std::vector<uint64_t> f(s->allocs.size());
+  for (size_t i = 0; i < s->allocs.size(); ++i) {
+    const Alloc& a = s->allocs[i];
+    t[i] = DevAlloc{a.ptr, a.bytes, a.first_page, a.id, static_cast<uint32_t>(a.n_pages)};
+    f[i] = a.first_page;
+  }
+  // pageable source: the runtime stages it before returning, so the vectors
+  // may go out of scope; the copy stays ordered on the capture stream
+  CK(cudaMemcpyAsync(s->d_allocs, t.data(), t.size() * sizeof(DevAlloc), cudaMemcpyHostToDevice,
+                     s->cap_stream));
+  CK(cudaMemcpyAsync(s->d_first_page, f.data(), f.size() * sizeof(uint64_t),
+                     cudaMemcpyHostToDevice, s->cap_stream));
+  s->table_dirty = false;
+  return CRUM_OK;
+}
+
+// Queue the device->host copies of a captured image from half H into its
+// pinned host buffer, on the drain stream.
+crum_status enqueue_drain(crum_set* s, crum_image* img, Half& H) {
+  const uint64_t A = img->n_allocs, n = img->n_dirty;
+  CK(cudaStreamWaitEvent(s->drain_stream, img->ev_captured, 0));
+  CK(cudaMemcpyAsync(img->host, H.meta, meta_bytes(A, n), cudaMemcpyDeviceToHost, s->drain_stream));
+  if (n > 0 && !img->drop_payload)
+    CK(cudaMemcpyAsync(img->host + meta_bytes(A, n), H.payload, n * kPage, cudaMemcpyDeviceToHost,
+                       s->drain_stream));
+  CK(cudaMemcpyAsync(img->host + img->image_bytes - 8, H.scalars + 1, 8, cudaMemcpyDeviceToHost,
+                     s->drain_stream));
+  CK(cudaEventRecord(img->ev_drained, s->drain_stream));
+  CK(cudaEventRecord(H.ev_drained, s->drain_stream));
+  return CRUM_OK;
+}
+
+crum_status alloc_image_host(crum_set* s, crum_image* img) {
+  img->image_bytes = image_size(img->n_allocs, img->n_dirty);
+  // null sink: the payload still crosses the link, into a pooled buffer that
+  // is handed back as soon as the drain ends
+  img->host_len = img->image_bytes;
+  img->host = s->pool->alloc(img->host_len);
+  if (img->host == nullptr) return fail(CRUM_ENOMEM, "pinned host pool exhausted (%zu bytes)", img->host_len);
+  return CRUM_OK;
+}
+
+void planner_main(crum_set* s) {
+  DeviceGuard dg(s->device);
+  for (;;) {
+    crum_image* img;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->plan_cv.wait(lk, [&] { return s->stop || !s->plan_q.empty(); });
+      if (s->plan_q.empty()) return;
+      img = s->plan_q.front();
+      s->plan_q.pop_front();
+    }
+    Half& H = s->half[img->half];
+    crum_status st = wait_event(H.ev_scanned, kBackgroundLimitNs);
+    std::string err = st == CRUM_OK ? "" : t_err;
+    if (st == CRUM_OK) {
+      img->n_dirty = reinterpret_cast<volatile uint64_t*>(H.mailbox)[0];
+      img->collisions = reinterpret_cast<volatile uint64_t*>(H.mailbox)[1];
+      st = alloc_image_host(s, img);
+      if (st == CRUM_OK) st = enqueue_drain(s, img, H);
+      if (st != CRUM_OK) err = t_err;
+    }
+    if (st != CRUM_OK) {
+      // keep later users of this half ordered after the capture
+      cudaEventRecord(H.ev_drained, s->cap_stream);
+      image_set_stage(img, CRUM_WAIT_PERSISTED, st, err);
+    }
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      H.drain_enqueued = true;
+      if (st != CRUM_OK) {
+        s->needs_full = true;
+        --s->inflight;
+      } else {
+        s->write_q.push_back(img);
+        s->write_cv.notify_one();
+      }
+      s->cv.notify_all();
+    }
+    if (st != CRUM_OK) image_unref(img);
+  }
+}
+
+crum_status write_file(const uint8_t* data, uint64_t n, const char* path, bool do_fsync) {
+  const int fd = ::open(path, O_WRONLY | O_CREAT | O_TRUNC, 0644);
+  if (fd < 0) return fail(CRUM_EIO, "open %s: %s", path, strerror(errno));
+  uint64_t off = 0;
+  while (off < n) {
+    const size_t want = static_cast<size_t>(std::min<uint64_t>(n - off, 1ull << 30));
+    const ssize_t w = ::write(fd, data + off, want);
+    if (w <= 0) {
+      const int e = errno;
+      ::close(fd);
+      return fail(CRUM_EIO, "write %s: %s", path, w == 0 ? "short write" : strerror(e));
+    }
+    off += static_cast<uint64_t>(w);
+  }
+  if (do_fsync && ::fsync(fd) != 0) {
+    const int e = errno;
+    ::close(fd);
+    return fail(CRUM_EIO, "fsync %s: %s", path, strerror(e));
+  }
+  if (::close(fd) != 0) return fail(CRUM_EIO, "close %s: %s", path, strerror(errno));
+  return CRUM_OK;
+}
+
+void writer_main(crum_set* s) {
+  DeviceGuard dg(s->device);
+  for (;;) {
+    crum_image* img;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->write_cv.wait(lk, [&] { return s->stop || !s->write_q.empty(); });
+      if (s->write_q.empty()) return;
+      img = s->write_q.front();
+      s->write_q.pop_front();
+    }
+    crum_status st = wait_event(img->ev_drained, kBackgroundLimitNs);
+    std::string err = st == CRUM_OK ? "" : t_err;
+    if (st == CRUM_OK) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, img->ev_submit, img->ev_captured) == cudaSuccess)
+        img->t_captured_ms = ms;
+      if (cudaEventElapsedTime(&ms, img->ev_submit, img->ev_drained) == cudaSuccess)
+        img->t_drained_ms = ms;
+      std::memcpy(&img->checksum, img->host + img->image_bytes - 8, 8);
+      image_set_stage(img, CRUM_WAIT_DRAINED, img->collisions ? CRUM_ECOLLISION : CRUM_OK, "");
+      if (img->drop_payload) {
+        std::lock_guard<std::mutex> lk(img->mu);
+        img->pool->free(img->host, img->host_len);
+        img->host = nullptr;
+        img->host_len = 0;
+      } else if (!img->sink_path.empty()) {
+        st = write_file(img->host, img->image_bytes, img->sink_path.c_str(), img->do_fsync);
+        if (st != CRUM_OK) err = t_err;
+      }
+    }
+    img->t_persisted_ms = std::chrono::duration<double, std::milli>(
+                              std::chrono::steady_clock::now() - img->t_submit)
+                              .count();
+    image_set_stage(img, CRUM_WAIT_PERSISTED, st, err);
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      if (st != CRUM_OK) s->needs_full = true;
+      --s->inflight;
+      s->cv.notify_all();
+    }
+    image_unref(img);
+  }
+}
+
+crum_status new_image_events(crum_image* img) {
+  CK(cudaEventCreate(&img->ev_submit));
+  CK(cudaEventCreate(&img->ev_captured));
+  CK(cudaEventCreate(&img->ev_drained));
+  return CRUM_OK;
+}
+
+// Captures in staging-sized chunks when the set has more pages than one
+// staging half holds.  The dirty count is read on the host first.
+crum_status checkpoint_chunked(crum_set* s, crum_image* img, cudaStream_t app,
+                               std::unique_lock<std::mutex>& lk, const crum::GatherArgs& base) {
+  Half& H0 = s->half[img->half];
+  crum_status st = wait_event(H0.ev_scanned, kBackgroundLimitNs);
+  if (st != CRUM_OK) return st;
+  img->n_dirty = reinterpret_cast<volatile uint64_t*>(H0.mailbox)[0];
+  img->collisions = reinterpret_cast<volatile uint64_t*>(H0.mailbox)[1];
+  st = alloc_image_host(s, img);
+  if (st != CRUM_OK) return st;
+  const uint64_t n = img->n_dirty, A = img->n_allocs, hs = s->half_slots;
+  int h = img->half;
+  for (uint64_t s0 = 0; s0 < n || s0 == 0; s0 += hs) {
+    const uint64_t s1 = std::min(n, s0 + hs);
+    Half& H = s->half[h];
+    if (&H != &H0) {
+      const bool ok = s->cv.wait_for(lk, std::chrono::seconds(600), [&] { return H.drain_enqueued; });
+      if (!ok) return fail(CRUM_ETIMEOUT, "timed out waiting for a staging half");
+    }
+    CK(cudaStreamWaitEvent(s->cap_stream, H.ev_drained, 0));
+    crum::GatherArgs g = base;
+    g.payload = H.payload;
+    g.s_begin = s0;
+    g.s_end = s1;
+    CK(crum::launch_gather(g, s1 - s0, s->map_gather, false, s->cap_stream));
+    if (n == 0) break;
+    cudaEvent_t ev;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CK(cudaEventRecord(ev, s->cap_stream));
+    CK(cudaStreamWaitEvent(s->drain_stream, ev, 0));
+    CK(cudaEventDestroy(ev));  // released once the recorded work completes
+    if (!img->drop_payload)
+      CK(cudaMemcpyAsync(img->host + meta_bytes(A, n) + s0 * kPage, H.payload, (s1 - s0) * kPage,
+                         cudaMemcpyDeviceToHost, s->drain_stream));
+    CK(cudaEventRecord(H.ev_drained, s->drain_stream));
+    h ^= 1;
+  }
+  CK(cudaEventRecord(img->ev_captured, s->cap_stream));
+  CK(cudaStreamWaitEvent(app, img->ev_captured, 0));
+  CK(cudaStreamWaitEvent(s->drain_stream, img->ev_captured, 0));
+  CK(cudaMemcpyAsync(img->host, H0.meta, meta_bytes(A, n), cudaMemcpyDeviceToHost, s->drain_stream));
+  CK(cudaMemcpyAsync(img->host + img->image_bytes - 8, H0.scalars + 1, 8, cudaMemcpyDeviceToHost,
+                     s->drain_stream));
+  CK(cudaEventRecord(img->ev_drained, s->drain_stream));
+  CK(cudaEventRecord(s->half[0].ev_drained, s->drain_stream));
+  CK(cudaEventRecord(s->half[1].ev_drained, s->drain_stream));
+  s->next_half = h;
+  return CRUM_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ PinnedPool ---
+
+namespace crum {
+
+PinnedPool::PinnedPool(size_t initial) : initial_(initial) {}
+
+PinnedPool::~PinnedPool() {
+  for (Arena& a : arenas_) cudaFreeHost(a.base);
+}
+
+uint8_t* PinnedPool::alloc(size_t n) {
+  n = (n + 4095) & ~size_t(4095);
+  std::lock_guard<std::mutex> lk(mu_);
+  for (Arena& a : arenas_)
+    for (auto it = a.free_list.begin(); it != a.free_list.end(); ++it)
+      if (it->second >= n) {
+        const size_t off = it->first, len = it->second;
+        a.free_list.erase(it);
+        if (len > n) a.free_list.emplace(off + n, len - n);
+        return a.base + off;
+      }
+  size_t size = std::max(n, arenas_.empty() ? initial_ : size_t(0));
+  size = std::max(size, size_t(256) << 20);
+  uint8_t* p = nullptr;
+  if (cudaHostAlloc(reinterpret_cast<void**>(&p), size, cudaHostAllocPortable) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  Arena a{p, size, {}};
+  if (size > n) a.free_list.emplace(n, size - n);
+  arenas_.push_back(std::move(a));
+  reserved_ += size;
+  return p;
+}
+
+void PinnedPool::free(uint8_t* p, size_t n) {
+  if (p == nullptr) return;
+  n = (n + 4095) & ~size_t(4095);
+  std::lock_guard<std::mutex> lk(mu_);
+  for (Arena& a : arenas_) {
+    if (p < a.base || p >= a.base + a.size) continue;
+    size_t off = static_cast<size_t>(p - a.base), len = n;
+    auto next = a.free_list.lower_bound(off);
+    if (next != a.free_list.end() && next->first == off + len) {
+      len += next->second;
+      next = a.free_list.erase(next);
+    }
+    if (next != a.free_list.begin()) {
+      auto prev = std::prev(next);
+      if (prev->first + prev->second == off) {
+        off = prev->first;
+        len += prev->second;
+        a.free_list.erase(prev);
+      }
+    }
+    a.free_list.emplace(off, len);
+    return;
+  }
+}
+
+}  // namespace crum
+
+// ------------------------------------------------------------------ C ABI ---
+
+extern "C" {
+
+void crum_config_default(crum_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof *cfg);
+  cfg->device = 0;
+  cfg->staging_bytes = kDefaultStaging;
+  cfg->chunk_bytes = kDefaultChunk;
+  cfg->sink = CRUM_SINK_MEMORY;
+}
+
+const char* crum_last_error(void) { return t_err.c_str(); }
+
+const char* crum_version(void) { return "crum-b300 1.0 sm_103a"; }
+
+uint64_t crum_kernel_launches(void) { return crum::g_kernel_launches.load(); }
+
+crum_status crum_set_create(const crum_config* cfg_in, crum_set** out) {
+  t_err.clear();
+  if (out == nullptr) return fail(CRUM_EINVAL, "out is null");
+  *out = nullptr;
+  crum_config cfg;
+  crum_config_default(&cfg);
+  if (cfg_in) cfg = *cfg_in;
+  if (cfg.staging_bytes == 0) cfg.staging_bytes = kDefaultStaging;
+  if (cfg.chunk_bytes == 0) cfg.chunk_bytes = kDefaultChunk;
+  if (cfg.staging_bytes < 2ull * kPage)
+    return fail(CRUM_EINVAL, "staging_bytes must hold at least one page per half");
+  if (cfg.sink < CRUM_SINK_MEMORY || cfg.sink > CRUM_SINK_NULL) return fail(CRUM_EINVAL, "bad sink");
+  if (cfg.sink == CRUM_SINK_FILE && (cfg.sink_dir == nullptr || cfg.sink_dir[0] == 0))
+    return fail(CRUM_EINVAL, "file sink needs sink_dir");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg.device < 0 || cfg.device >= ndev) {
+    cudaGetLastError();
+    return fail(CRUM_EINVAL, "no CUDA device %d", cfg.device);
+  }
+  DeviceGuard dg(cfg.device);
+  auto s = std::make_unique<crum_set>();
+  s->cfg = cfg;
+  if (cfg.sink_dir) s->sink_dir = cfg.sink_dir;
+  s->cfg.sink_dir = nullptr;
+  s->device = cfg.device;
+  s->set_id = g_set_ids.fetch_add(1);
+  s->half_slots = cfg.staging_bytes / 2 / kPage;
+  s->pool = std::make_shared<crum::PinnedPool>(cfg.host_pool_bytes);
+  if (cfg.host_pool_bytes) {
+    uint8_t* p = s->pool->alloc(cfg.host_pool_bytes);
+    if (!p) return fail(CRUM_ENOMEM, "cannot pin %llu host bytes", (unsigned long long)cfg.host_pool_bytes);
+    s->pool->free(p, cfg.host_pool_bytes);
+  }
+  CK(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&s->drain_stream, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&s->ev_app, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&s->ev_done, cudaEventDisableTiming));
+  CK(cudaMalloc(&s->d_collisions, sizeof(unsigned long long)));
+  for (Half& H : s->half) {
+    if (cudaMalloc(&H.payload, s->half_slots * kPage) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(CRUM_ENOMEM, "cannot allocate %llu bytes of staging",
+                  (unsigned long long)(s->half_slots * kPage));
+    }
+    CK(cudaMalloc(&H.scalars, 2 * sizeof(uint64_t)));
+    CK(cudaHostAlloc(reinterpret_cast<void**>(&H.mailbox), 2 * sizeof(uint64_t), cudaHostAllocMapped));
+    CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&H.mailbox_dev), H.mailbox, 0));
+    CK(cudaEventCreateWithFlags(&H.ev_scanned, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&H.ev_drained, cudaEventDisableTiming));
+    CK(cudaEventRecord(H.ev_drained, s->drain_stream));
+  }
+  crum_set* raw = s.release();
+  raw->planner = std::thread(planner_main, raw);
+  raw->writer = std::thread(writer_main, raw);
+  *out = raw;
+  return CRUM_OK;
+}
+
+crum_status crum_set_destroy(crum_set* s) {
+  t_err.clear();
+  if (s == nullptr) return CRUM_OK;
+  DeviceGuard dg(s->device);
+  {
+    std::unique_lock<std::mutex> lk(s->mu);
+    s->cv.wait_for(lk, std::chrono::seconds(600), [&] { return s->inflight == 0; });
+    s->stop = true;
+    s->plan_cv.notify_all();
+    s->write_cv.notify_all();
+  }
+  if (s->planner.joinable()) s->planner.join();
+  if (s->writer.joinable()) s->writer.join();
+  cudaStreamSynchronize(s->cap_stream);
+  cudaStreamSynchronize(s->drain_stream);
+  image_unref(s->last);
+  for (Half& H : s->half) {
+    cudaFree(H.meta);
+    cudaFree(H.payload);
+    cudaFree(H.scalars);
+    cudaFreeHost(H.mailbox);
+    cudaEventDestroy(H.ev_scanned);
+    cudaEventDestroy(H.ev_drained);
+  }
+  cudaFree(s->d_allocs);
+  cudaFree(s->d_first_page);
+  cudaFree(s->d_h);
+  cudaFree(s->d_mask);
+  cudaFree(s->d_word_offset);
+  cudaFree(s->d_collisions);
+  cudaFree(s->d_shadow);
+  cudaEventDestroy(s->ev_app);
+  cudaEventDestroy(s->ev_done);
+  cudaStreamDestroy(s->cap_stream);
+  cudaStreamDestroy(s->drain_stream);
+  delete s;
+  return CRUM_OK;
+}
+
+crum_status crum_register(crum_set* s, void* ptr, size_t bytes, uint32_t* alloc_id) {
+  t_err.clear();
+  if (s == nullptr || ptr == nullptr) return fail(CRUM_EINVAL, "null set or pointer");
+  if (bytes == 0) return fail(CRUM_EINVAL, "zero-byte registration");
+  if (reinterpret_cast<uintptr_t>(ptr) % 16 != 0) return fail(CRUM_EINVAL, "pointer not 16-byte aligned");
+  if (pages_of(bytes) > 0xFFFFFFFFull) return fail(CRUM_EINVAL, "allocation too large");
+  std::lock_guard<std::mutex> lk(s->mu);
+  const uintptr_t lo = reinterpret_cast<uintptr_t>(ptr), hi = lo + bytes;
+  for (const Alloc& a : s->allocs) {
+    const uintptr_t alo = reinterpret_cast<uintptr_t>(a.ptr), ahi = alo + a.bytes;
+    if (lo < ahi && alo < hi) return fail(CRUM_EINVAL, "range overlaps registration %u", a.id);
+  }
+  Alloc a{s->next_id++, static_cast<uint8_t*>(ptr), bytes, pages_of(bytes), s->n_pages};
+  s->allocs.push_back(a);
+  s->n_pages += a.n_pages;
+  s->table_dirty = s->reg_changed = true;
+  if (alloc_id) *alloc_id = a.id;
+  return CRUM_OK;
+}
+
+crum_status crum_unregister(crum_set* s, uint32_t id) {
+  t_err.clear();
+  if (s == nullptr) return fail(CRUM_EINVAL, "null set");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = std::find_if(s->allocs.begin(), s->allocs.end(), [&](const Alloc& a) { return a.id == id; });
+  if (it == s->allocs.end()) return fail(CRUM_EINVAL, "unknown allocation id %u", id);
+  s->allocs.erase(it);
+  uint64_t first = 0;
+  for (Alloc& a : s->allocs) {
+    a.first_page = first;
+    first += a.n_pages;
+  }
+  s->n_pages = first;
+  s->table_dirty = s->reg_changed = true;
+  return CRUM_OK;
+}
+
+crum_status crum_set_info(const crum_set* s, uint32_t* n_allocs, uint64_t* n_pages) {
+  if (s == nullptr) return fail(CRUM_EINVAL, "null set");
+  std::lock_guard<std::mutex> lk(const_cast<crum_set*>(s)->mu);
+  if (n_allocs) *n_allocs = static_cast<uint32_t>(s->allocs.size());
+  if (n_pages) *n_pages = s->n_pages;
+  return CRUM_OK;
+}
+
+crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, crum_image** out) {
+  t_err.clear();
+  if (s == nullptr || out == nullptr) return fail(CRUM_EINVAL, "null set or out");
+  *out = nullptr;
+  const bool verify = (flags & CRUM_VERIFY) != 0;
+  if (verify && !s->cfg.verify) return fail(CRUM_EINVAL, "CRUM_VERIFY needs a set created with verify=1");
+  cudaStream_t app = static_cast<cudaStream_t>(app_stream);
+  DeviceGuard dg(s->device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  if (s->allocs.empty()) return fail(CRUM_EINVAL, "no registered allocations");
+  crum_status st = ensure_capacity(s, lk);
+  if (st != CRUM_OK) return st;
+  const int h = s->next_half;
+  Half& H = s->half[h];
+  if (!s->cv.wait_for(lk, std::chrono::seconds(600), [&] { return H.drain_enqueued; }))
+    return fail(CRUM_ETIMEOUT, "timed out waiting for a staging half");
+
+  const bool full = (flags & CRUM_FULL) || s->needs_full || s->reg_changed;
+  auto* img = new crum_image();
+  img->pool = s->pool;
+  img->device = s->device;
+  img->seq = s->seq;
+  img->full = full;
+  img->parent = full ? nullptr : s->last;
+  img->parent_seq = full ? CRUM_NO_PARENT : s->last->seq;
+  image_ref(img->parent);
+  img->n_allocs = static_cast<uint32_t>(s->allocs.size());
+  img->n_pages = s->n_pages;
+  for (const Alloc& a : s->allocs) img->table.emplace_back(a.id, a.bytes);
+  img->half = h;
+  img->t_submit = std::chrono::steady_clock::now();
+  img->drop_payload = s->cfg.sink == CRUM_SINK_NULL;
+  img->do_fsync = s->cfg.fsync != 0;
+  if (s->cfg.sink == CRUM_SINK_FILE) {
+    char name[96];
+    snprintf(name, sizeof name, "/crum_%u_%llu.img", s->set_id, (unsigned long long)img->seq);
+    img->sink_path = s->sink_dir + name;
+  }
+  st = new_image_events(img);
+  if (st != CRUM_OK) {
+    image_unref(img);
+    return st;
+  }
+
+  auto bail = [&](crum_status e) {
+    // leave the set consistent: the next checkpoint starts a new full chain
+    s->needs_full = true;
+    image_unref(img);
+    return e;
+  };
+  if (cudaEventRecord(s->ev_app, app) != cudaSuccess ||
+      cudaStreamWaitEvent(s->cap_stream, s->ev_app, 0) != cudaSuccess ||
+      cudaEventRecord(img->ev_submit, s->cap_stream) != cudaSuccess)
+    return bail(fail(CRUM_ECUDA, "cannot order capture after the application stream: %s",
+                     cudaGetErrorString(cudaGetLastError())));
+  if ((st = upload_table(s)) != CRUM_OK) return bail(st);
+  const uint64_t words = (s->n_pages + 31) / 32;
+  if (cudaMemsetAsync(s->d_mask, 0, words * sizeof(uint32_t), s->cap_stream) != cudaSuccess ||
+      (verify && cudaMemsetAsync(s->d_collisions, 0, sizeof(unsigned long long), s->cap_stream) != cudaSuccess))
+    return bail(fail(CRUM_ECUDA, "memset failed: %s", cudaGetErrorString(cudaGetLastError())));
+
+  crum::HashArgs ha{};
+  ha.allocs = s->d_allocs;
+  ha.first_page = s->d_first_page;
+  ha.n_allocs = img->n_allocs;
+  ha.n_pages = s->n_pages;
+  ha.h_table = s->d_h;
+  ha.dirty_mask = s->d_mask;
+  ha.full = full;
+  ha.shadow = s->d_shadow;
+  ha.collisions = s->d_collisions;
+  cudaError_t ce = crum::launch_hash_dirty(ha, s->map_hash, verify, s->cap_stream);
+  if (ce != cudaSuccess) return bail(fail(CRUM_ECUDA, "hash launch: %s", cudaGetErrorString(ce)));
+
+  // this half's previous drain must be done before its metadata is rewritten
+  if (cudaStreamWaitEvent(s->cap_stream, H.ev_drained, 0) != cudaSuccess)
+    return bail(fail(CRUM_ECUDA, "stream wait failed"));
+  crum::ScanArgs sa{};
+  sa.mask = s->d_mask;
+  sa.n_words = words;
+  sa.word_offset = s->d_word_offset;
+  sa.n_dirty_out = H.scalars;
+  sa.mailbox = H.mailbox_dev;
+  sa.collisions = verify ? s->d_collisions : nullptr;
+  sa.allocs = s->d_allocs;
+  sa.n_allocs = img->n_allocs;
+  sa.meta = H.meta;
+  sa.trailer = H.scalars + 1;
+  sa.seq = img->seq;
+  sa.parent_seq = img->parent_seq;
+  sa.flags = full ? 1u : 0u;
+  ce = crum::launch_scan(sa, s->cap_stream);
+  if (ce != cudaSuccess) return bail(fail(CRUM_ECUDA, "scan launch: %s", cudaGetErrorString(ce)));
+  if (cudaEventRecord(H.ev_scanned, s->cap_stream) != cudaSuccess)
+    return bail(fail(CRUM_ECUDA, "event record failed"));
+
+  crum::GatherArgs ga{};
+  ga.allocs = s->d_allocs;
+  ga.first_page = s->d_first_page;
+  ga.n_allocs = img->n_allocs;
+  ga.mask = s->d_mask;
+  ga.word_offset = s->d_word_offset;
+  ga.n_words = words;
+  ga.n_pages = s->n_pages;
+  ga.n_dirty = H.scalars;
+  ga.h_table = s->d_h;
+  ga.meta = H.meta;
+  ga.trailer = H.scalars + 1;
+  // with verify enabled the shadow follows every capture, so a later
+  // CRUM_VERIFY checkpoint compares against the last checkpointed bytes
+  ga.shadow = s->cfg.verify ? s->d_shadow : nullptr;
+  const bool gather_shadow = ga.shadow != nullptr;
+
+  image_ref(img);  // in-flight reference, dropped by the writer
+  s->inflight++;
+  H.drain_enqueued = false;
+  if (s->n_pages <= s->half_slots) {
+    ga.payload = H.payload;
+    ga.s_begin = 0;
+    ga.s_end = s->n_pages;
+    ce = crum::launch_gather(ga, s->n_pages, s->map_gather, gather_shadow, s->cap_stream);
+    if (ce == cudaSuccess) ce = cudaEventRecord(img->ev_captured, s->cap_stream);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(app, img->ev_captured, 0);
+    if (ce != cudaSuccess) {
+      cudaEventRecord(H.ev_drained, s->cap_stream);
+      H.drain_enqueued = true;
+      s->inflight--;
+      image_unref(img);
+      return bail(fail(CRUM_ECUDA, "gather: %s", cudaGetErrorString(ce)));
+    }
+    s->next_half = h ^ 1;
+    s->plan_q.push_back(img);
+    s->plan_cv.notify_one();
+  } else {
+    if (gather_shadow) {
+      H.drain_enqueued = true;
+      s->inflight--;
+      image_unref(img);
+      return bail(fail(CRUM_EINVAL, "verify mode needs staging that holds every page"));
+    }
+    st = checkpoint_chunked(s, img, app, lk, ga);
+    H.drain_enqueued = true;
+    s->cv.notify_all();
+    if (st != CRUM_OK) {
+      s->inflight--;
+      image_unref(img);
+      return bail(st);
+    }
+    s->write_q.push_back(img);
+    s->write_cv.notify_one();
+  }
+  image_ref(img);  // the set's reference as the newest chain link
+  image_unref(s->last);
+  s->last = img;
+  s->seq++;
+  s->needs_full = false;
+  s->reg_changed = false;
+  *out = img;
+  return CRUM_OK;
+}
+
+crum_status crum_image_wait(crum_image* img, int what, int64_t timeout_ns) {
+  t_err.clear();
+  if (img == nullptr || what < CRUM_WAIT_CAPTURED || what > CRUM_WAIT_PERSISTED)
+    return fail(CRUM_EINVAL, "bad image or stage");
+  if (what == CRUM_WAIT_CAPTURED && img->ev_captured != nullptr) {
+    {
+      std::lock_guard<std::mutex> lk(img->mu);
+      if (img->stage >= CRUM_WAIT_CAPTURED) return img->status == CRUM_ECOLLISION ? CRUM_OK : img->status;
+    }
+    DeviceGuard dg(img->device);
+    crum_status st = wait_event(img->ev_captured, timeout_ns);
+    if (st == CRUM_OK) image_set_stage(img, CRUM_WAIT_CAPTURED, CRUM_OK, "");
+    return st;
+  }
+  std::unique_lock<std::mutex> lk(img->mu);
+  auto done = [&] { return img->stage >= what || (img->status != CRUM_OK && img->status != CRUM_ECOLLISION); };
+  if (timeout_ns < 0) {
+    img->cv.wait(lk, done);
+  } else if (!img->cv.wait_for(lk, std::chrono::nanoseconds(timeout_ns), done)) {
+    return fail(CRUM_ETIMEOUT, "image %llu did not reach stage %d in time", (unsigned long long)img->seq, what);
+  }
+  if (img->status != CRUM_OK) {
+    if (!img->err.empty()) t_err = img->err;
+    else if (img->status == CRUM_ECOLLISION) t_err = "verify mode found hash collisions";
+  }
+  return img->status;
+}
+
+crum_status crum_image_info_get(const crum_image* cimg, crum_image_info* info) {
+  if (cimg == nullptr || info == nullptr) return fail(CRUM_EINVAL, "null image or info");
+  crum_image* img = const_cast<crum_image*>(cimg);
+  std::lock_guard<std::mutex> lk(img->mu);
+  std::memset(info, 0, sizeof *info);
+  info->seq = img->seq;
+  info->parent_seq = img->parent_seq;
+  info->n_pages = img->n_pages;
+  info->n_allocs = img->n_allocs;
+  info->full = img->full ? 1 : 0;
+  info->stage = img->stage;
+  info->status = img->status;
+  if (img->stage >= CRUM_WAIT_DRAINED) {
+    info->n_dirty = img->n_dirty;
+    info->image_bytes = img->image_bytes;
+    info->checksum = img->checksum;
+    info->collisions = img->collisions;
+    info->t_captured_ms = img->t_captured_ms;
+    info->t_drained_ms = img->t_drained_ms;
+  }
+  if (img->stage >= CRUM_WAIT_PERSISTED) info->t_persisted_ms = img->t_persisted_ms;
+  return CRUM_OK;
+}
+
+crum_status crum_image_copy(crum_image* img, void* dst, uint64_t dst_bytes) {
+  t_err.clear();
+  if (img == nullptr || dst == nullptr) return fail(CRUM_EINVAL, "null image or destination");
+  crum_status st = crum_image_wait(img, CRUM_WAIT_DRAINED, -1);
+  if (st != CRUM_OK && st != CRUM_ECOLLISION) return st;
+  std::lock_guard<std::mutex> lk(img->mu);
+  if (img->host == nullptr) return fail(CRUM_EIO, "image payload was dropped (null sink)");
+  if (dst_bytes < img->image_bytes) return fail(CRUM_EINVAL, "destination holds %llu of %llu bytes",
+                                                (unsigned long long)dst_bytes, (unsigned long long)img->image_bytes);
+  std::memcpy(dst, img->host, img->image_bytes);
+  return CRUM_OK;
+}
+
+crum_status crum_image_save(crum_image* img, const char* path) {
+  t_err.clear();
+  if (img == nullptr || path == nullptr) return fail(CRUM_EINVAL, "null image or path");
+  crum_status st = crum_image_wait(img, CRUM_WAIT_DRAINED, -1);
+  if (st != CRUM_OK && st != CRUM_ECOLLISION) return st;
+  if (img->host == nullptr) return fail(CRUM_EIO, "image payload was dropped (null sink)");
+  return write_file(img->host, img->image_bytes, path, false);
+}
+
+crum_status crum_image_release(crum_image* img) {
+  if (img == nullptr) return CRUM_OK;
+  DeviceGuard dg(img->device);
+  image_unref(img);
+  return CRUM_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------- image loading ---
+
+namespace {
+
+uint32_t rd32(const uint8_t* p) {
+  uint32_t v;
+  std::memcpy(&v, p, 4);
+  return v;
+}
+uint64_t rd64(const uint8_t* p) {
+  uint64_t v;
+  std::memcpy(&v, p, 8);
+  return v;
+}
+
+// Structural check of a serialized image held in host memory.
+crum_status parse_image(const uint8_t* b, uint64_t n, crum_image* img) {
+  if (n < kHeaderBytes + 8 || std::memcmp(b, "CRUMIMG1", 8) != 0) return fail(CRUM_ECORRUPT, "bad magic");
+  if (rd32(b + 8) != 1 || rd32(b + 32) != kPage) return fail(CRUM_ECORRUPT, "bad version or page size");
+  const uint64_t A = rd32(b + 36), nd = rd64(b + 40);
+  if (nd > n / kPage || A > n / 16) return fail(CRUM_ECORRUPT, "counts exceed the image size");
+  if (rd64(b + 56) != n || image_size(A, nd) != n || rd64(b + 48) != meta_bytes(A, nd))
+    return fail(CRUM_ECORRUPT, "size fields disagree with the image length");
+  img->full = (rd32(b + 12) & 1u) != 0;
+  img->seq = rd64(b + 16);
+  img->parent_seq = rd64(b + 24);
+  img->n_allocs = static_cast<uint32_t>(A);
+  img->n_dirty = nd;
+  img->image_bytes = n;
+  img->table.clear();
+  uint64_t pages = 0;
+  for (uint64_t a = 0; a < A; ++a) {
+    const uint64_t bytes = rd64(b + kHeaderBytes + 16 * a + 8);
+    if (bytes == 0) return fail(CRUM_ECORRUPT, "zero-sized allocation in table");
+    img->table.emplace_back(rd32(b + kHeaderBytes + 16 * a), bytes);
+    pages += pages_of(bytes);
+  }
+  img->n_pages = pages;
+  const uint8_t* pt = b + kHeaderBytes + 16 * A;
+  uint64_t prev = 0;
+  for (uint64_t s = 0; s < nd; ++s) {
+    const uint32_t a = rd32(pt + 8 * s), p = rd32(pt + 8 * s + 4);
+    if (a >= A || p >= pages_of(img->table[a].second)) return fail(CRUM_ECORRUPT, "page table entry out of range");
+    const uint64_t key = (static_cast<uint64_t>(a) << 32) | p;
+    if (s > 0 && key <= prev) return fail(CRUM_ECORRUPT, "page table not ascending");
+    prev = key;
+  }
+  img->checksum = rd64(b + n - 8);
+  return CRUM_OK;
+}
+
+// Checksum of a host image computed on the device through staging half 0.
+crum_status device_checksum(crum_set* s, const uint8_t* host, uint64_t n, uint64_t* out) {
+  Half& H = s->half[0];
+  const uint64_t chunk = s->half_slots * kPage;
+  CK(cudaMemsetAsync(H.scalars + 1, 0, 8, s->cap_stream));
+  for (uint64_t off = 0; off < n; off += chunk) {
+    const uint64_t len = std::min(chunk, n - off);
+    CK(cudaMemcpyAsync(H.payload, host + off, len, cudaMemcpyHostToDevice, s->cap_stream));
+    CK(crum::launch_hash_bytes(H.payload, len, off / 8, H.scalars + 1, s->cap_stream));
+  }
+  CK(cudaMemcpyAsync(out, H.scalars + 1, 8, cudaMemcpyDeviceToHost, s->cap_stream));
+  CK(cudaStreamSynchronize(s->cap_stream));
+  return CRUM_OK;
+}
+
+crum_status load_common(crum_set* s, crum_image* parent, crum_image** out,
+                        const std::function<crum_status(uint8_t*, uint64_t)>& fill, uint64_t n) {
+  if ((n & 7) != 0 || n < kHeaderBytes + 8) return fail(CRUM_ECORRUPT, "image length %llu is not a valid size", (unsigned long long)n);
+  DeviceGuard dg(s->device);
+  auto* img = new crum_image();
+  img->pool = s->pool;
+  img->device = s->device;
+  img->host_len = n;
+  img->host = s->pool->alloc(n);
+  if (img->host == nullptr) {
+    image_unref(img);
+    return fail(CRUM_ENOMEM, "pinned host pool exhausted");
+  }
+  crum_status st = fill(img->host, n);
+  if (st == CRUM_OK) st = parse_image(img->host, n, img);
+  if (st == CRUM_OK) {
+    std::unique_lock<std::mutex> lk(s->mu);
+    st = quiesce(s, lk);
+    uint64_t cks = 0;
+    if (st == CRUM_OK) st = device_checksum(s, img->host, n - 8, &cks);
+    if (st == CRUM_OK && cks != img->checksum) st = fail(CRUM_ECORRUPT, "checksum mismatch");
+    if (st == CRUM_OK) {
+      // staging half 0 was overwritten: keep the two-halves protocol intact
+      cudaEventRecord(s->half[0].ev_drained, s->cap_stream);
+    }
+  }
+  if (st == CRUM_OK) {
+    if (img->full) {
+      img->parent_seq = CRUM_NO_PARENT;
+    } else if (parent == nullptr || parent->seq != img->parent_seq) {
+      st = fail(CRUM_EMISMATCH, "incremental image %llu needs parent %llu", (unsigned long long)img->seq,
+                (unsigned long long)img->parent_seq);
+    } else {
+      img->parent = parent;
+      image_ref(parent);
+    }
+  }
+  if (st != CRUM_OK) {
+    image_unref(img);
+    return st;
+  }
+  img->stage = CRUM_WAIT_PERSISTED;
+  *out = img;
+  return CRUM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+crum_status crum_image_load(crum_set* s, const char* path, crum_image* parent, crum_image** out) {
+  t_err.clear();
+  if (s == nullptr || path == nullptr || out == nullptr) return fail(CRUM_EINVAL, "null argument");
+  *out = nullptr;
+  const int fd = ::open(path, O_RDONLY);
+  if (fd < 0) return fail(CRUM_EIO, "open %s: %s", path, strerror(errno));
+  struct stat stt;
+  if (fstat(fd, &stt) != 0) {
+    ::close(fd);
+    return fail(CRUM_EIO, "stat %s: %s", path, strerror(errno));
+  }
+  const uint64_t n = static_cast<uint64_t>(stt.st_size);
+  crum_status st = load_common(
+      s, parent, out,
+      [&](uint8_t* dst, uint64_t len) -> crum_status {
+        uint64_t off = 0;
+        while (off < len) {
+          const ssize_t r = ::read(fd, dst + off, static_cast<size_t>(std::min<uint64_t>(len - off, 1ull << 30)));
+          if (r <= 0) return fail(CRUM_EIO, "read %s: %s", path, r == 0 ? "short file" : strerror(errno));
+          off += static_cast<uint64_t>(r);
+        }
+        return CRUM_OK;
+      },
+      n);
+  ::close(fd);
+  return st;
+}
+
+crum_status crum_image_from_bytes(crum_set* s, const void* bytes, uint64_t n, crum_image* parent,
+                                  crum_image** out) {
+  t_err.clear();
+  if (s == nullptr || bytes == nullptr || out == nullptr) return fail(CRUM_EINVAL, "null argument");
+  *out = nullptr;
+  return load_common(
+      s, parent, out,
+      [&](uint8_t* dst, uint64_t len) -> crum_status {
+        std::memcpy(dst, bytes, len);
+        return CRUM_OK;
+      },
+      n);
+}
+
+crum_status crum_restore(crum_set* s, const crum_image* chain_end, crum_stream_t stream) {
+  t_err.clear();
+  if (s == nullptr || chain_end == nullptr) return fail(CRUM_EINVAL, "null set or image");
+  cudaStream_t us = static_cast<cudaStream_t>(stream);
+  std::vector<crum_image*> chain;
+  for (crum_image* p = const_cast<crum_image*>(chain_end); p != nullptr; p = p->parent) {
+    chain.push_back(p);
+    if (p->full) break;
+  }
+  std::reverse(chain.begin(), chain.end());
+  if (!chain.front()->full) return fail(CRUM_ECORRUPT, "chain has no full base image");
+  for (crum_image* img : chain) {
+    const crum_status st = crum_image_wait(img, CRUM_WAIT_DRAINED, -1);
+    if (st != CRUM_OK && st != CRUM_ECOLLISION) return st;
+    if (img->host == nullptr) return fail(CRUM_EIO, "image %llu has no payload (null sink)", (unsigned long long)img->seq);
+  }
+  DeviceGuard dg(s->device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  for (crum_image* img : chain) {
+    if (img->table.size() != s->allocs.size()) return fail(CRUM_EMISMATCH, "image has %zu allocations, set has %zu", img->table.size(), s->allocs.size());
+    for (size_t a = 0; a < s->allocs.size(); ++a)
+      if (img->table[a].second != s->allocs[a].bytes)
+        return fail(CRUM_EMISMATCH, "allocation %zu: image %llu bytes, set %llu bytes", a,
+                    (unsigned long long)img->table[a].second, (unsigned long long)s->allocs[a].bytes);
+  }
+  crum_status st = ensure_capacity(s, lk);
+  if (st != CRUM_OK) return st;
+  CK(cudaEventRecord(s->ev_app, us));
+  CK(cudaStreamWaitEvent(s->cap_stream, s->ev_app, 0));
+  if ((st = upload_table(s)) != CRUM_OK) return st;
+  const uint64_t A = s->allocs.size();
+  int h = s->next_half;
+  for (crum_image* img : chain) {
+    const uint64_t n = img->n_dirty;
+    const uint8_t* ptab = img->host + kHeaderBytes + 16 * A;
+    const uint8_t* hashes = ptab + 8 * n;
+    const uint8_t* payload = img->host + meta_bytes(A, n);
+    for (uint64_t s0 = 0; s0 < n; s0 += s->half_slots) {
+      const uint64_t s1 = std::min(n, s0 + s->half_slots);
+      Half& H = s->half[h];
+      if (!s->cv.wait_for(lk, std::chrono::seconds(600), [&] { return H.drain_enqueued; }))
+        return fail(CRUM_ETIMEOUT, "timed out waiting for a staging half");
+      CK(cudaStreamWaitEvent(s->cap_stream, H.ev_drained, 0));
+      const uint64_t m = s1 - s0;
+      CK(cudaMemcpyAsync(H.meta, ptab + 8 * s0, 8 * m, cudaMemcpyHostToDevice, s->cap_stream));
+      CK(cudaMemcpyAsync(H.meta + 8 * m, hashes + 8 * s0, 8 * m, cudaMemcpyHostToDevice, s->cap_stream));
+      CK(cudaMemcpyAsync(H.payload, payload + kPage * s0, kPage * m, cudaMemcpyHostToDevice, s->cap_stream));
+      crum::RestoreArgs ra{};
+      ra.allocs = s->d_allocs;
+      ra.n_allocs = static_cast<uint32_t>(A);
+      ra.ptab = reinterpret_cast<const uint32_t*>(H.meta);
+      ra.hashes = reinterpret_cast<const uint64_t*>(H.meta + 8 * m);
+      ra.payload = H.payload;
+      ra.n_slots = m;
+      ra.h_table = s->d_h;
+      CK(crum::launch_restore(ra, s->cap_stream));
+      CK(cudaEventRecord(H.ev_drained, s->cap_stream));
+      h ^= 1;
+    }
+  }
+  s->next_half = h;
+  CK(cudaEventRecord(s->ev_done, s->cap_stream));
+  CK(cudaStreamWaitEvent(us, s->ev_done, 0));
+  crum_image* end = const_cast<crum_image*>(chain_end);
+  image_ref(end);
+  image_unref(s->last);
+  s->last = end;
+  s->seq = end->seq + 1;
+  s->needs_full = s->cfg.verify != 0;  // the verify shadow does not hold the restored bytes
+  s->reg_changed = false;
+  return CRUM_OK;
+}
+
+crum_status crum_hash_pages(const void* ptr, uint64_t bytes, uint64_t* out, crum_stream_t stream) {
+  t_err.clear();
+  if (ptr == nullptr || out == nullptr || bytes == 0) return fail(CRUM_EINVAL, "null pointer or zero size");
+  if (reinterpret_cast<uintptr_t>(ptr) % 16 != 0) return fail(CRUM_EINVAL, "pointer not 16-byte aligned");
+  crum::HashArgs ha{};
+  ha.allocs = nullptr;
+  ha.one = DevAlloc{static_cast<uint8_t*>(const_cast<void*>(ptr)), bytes, 0, 0,
+                    static_cast<uint32_t>(pages_of(bytes))};
+  ha.n_allocs = 1;
+  ha.n_pages = pages_of(bytes);
+  ha.h_out = out;
+  CK(crum::launch_hash_dirty(ha, 1, false, static_cast<cudaStream_t>(stream)));
+  return CRUM_OK;
+}
+
+crum_status crum_hash_bytes(const void* ptr, uint64_t bytes, uint64_t first_index, uint64_t* out,
+                            crum_stream_t stream) {
+  t_err.clear();
+  if (out == nullptr || (bytes > 0 && ptr == nullptr)) return fail(CRUM_EINVAL, "null pointer");
+  if (reinterpret_cast<uintptr_t>(ptr) % 16 != 0) return fail(CRUM_EINVAL, "pointer not 16-byte aligned");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CK(cudaMemsetAsync(out, 0, 8, st));
+  CK(crum::launch_hash_bytes(static_cast<const uint8_t*>(ptr), bytes, first_index, out, st));
+  return CRUM_OK;
+}
+
+crum_status crum_get_hashes(crum_set* s, uint64_t* host_out, uint64_t n) {
+  t_err.clear();
+  if (s == nullptr || host_out == nullptr) return fail(CRUM_EINVAL, "null argument");
+  DeviceGuard dg(s->device);
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (n > s->n_pages || n > s->h_cap) return fail(CRUM_EINVAL, "asked for %llu hashes, table holds %llu", (unsigned long long)n, (unsigned long long)std::min<uint64_t>(s->n_pages, s->h_cap));
+  CK(cudaStreamSynchronize(s->cap_stream));
+  if (n) CK(cudaMemcpy(host_out, s->d_h, n * 8, cudaMemcpyDeviceToHost));
+  return CRUM_OK;
+}
+
+crum_status crum_poke_hash(crum_set* s, uint64_t g, uint64_t value) {
+  t_err.clear();
+  if (s == nullptr) return fail(CRUM_EINVAL, "null set");
+  DeviceGuard dg(s->device);
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (g >= s->n_pages || g >= s->h_cap) return fail(CRUM_EINVAL, "page %llu out of range", (unsigned long long)g);
+  CK(cudaStreamSynchronize(s->cap_stream));
+  CK(cudaMemcpy(s->d_h + g, &value, 8, cudaMemcpyHostToDevice));
+  return CRUM_OK;
+}
+
+}  // extern "C"

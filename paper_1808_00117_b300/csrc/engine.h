@@ -1,0 +1,147 @@
+// Host-side state of registration sets and images (internal).
+//
+// The paper's checkpoint (Section 3.4) copies every region device -> host
+// after draining the device, and its forked checkpoint (Section 3.3) lets a
+// child process write the image while the application continues.  Here the
+// "child" is a pair of host threads per set:
+//   planner  learns each capture's dirty count from a mapped pinned mailbox,
+//            sizes the image and queues the device->host drain on the drain
+//            stream;
+//   writer   waits for the drain, then hands the image to its sink.
+// The application's stream only waits for the device-side capture (hash,
+// scan, gather into staging); the staging buffer is split in two halves
+// that alternate between consecutive checkpoints so a capture never waits
+// for the previous checkpoint's drain unless both halves are busy.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "crum.h"
+#include "device.cuh"
+
+namespace crum {
+
+// First-fit allocator over cudaHostAlloc arenas (pinning is slow: about
+// 0.35 s per GiB, so images draw from a pool instead of pinning per image).
+class PinnedPool {
+ public:
+  explicit PinnedPool(size_t initial);
+  ~PinnedPool();
+  uint8_t* alloc(size_t n);  // nullptr on failure
+  void free(uint8_t* p, size_t n);
+  size_t reserved() const { return reserved_; }
+
+ private:
+  struct Arena {
+    uint8_t* base;
+    size_t size;
+    std::map<size_t, size_t> free_list;  // offset -> length
+  };
+  std::mutex mu_;
+  std::vector<Arena> arenas_;
+  size_t reserved_ = 0;
+  size_t initial_;
+};
+
+struct Alloc {
+  uint32_t id;
+  uint8_t* ptr;
+  uint64_t bytes;
+  uint64_t n_pages;
+  uint64_t first_page;
+};
+
+struct Half {
+  uint8_t* meta = nullptr;     // header, allocation table, page table, hashes
+  size_t meta_cap = 0;
+  uint8_t* payload = nullptr;  // half_slots pages
+  uint64_t* scalars = nullptr; // device: [0] n_dirty, [1] trailer
+  uint64_t* mailbox = nullptr; // mapped pinned host: [0] n_dirty
+  uint64_t* mailbox_dev = nullptr;
+  cudaEvent_t ev_scanned = nullptr;
+  cudaEvent_t ev_drained = nullptr;  // last device->host copy out of this half
+  bool drain_enqueued = true;        // host: ev_drained is recorded for its last user
+};
+
+}  // namespace crum
+
+struct crum_image {
+  std::atomic<int> refs{1};
+  std::shared_ptr<crum::PinnedPool> pool;
+  crum_image* parent = nullptr;  // holds a reference
+  int device = 0;
+  uint64_t seq = 0, parent_seq = CRUM_NO_PARENT;
+  bool full = false;
+  uint32_t n_allocs = 0;
+  uint64_t n_pages = 0;
+  std::vector<std::pair<uint32_t, uint64_t>> table;  // (id, bytes) per allocation
+  uint64_t n_dirty = 0, image_bytes = 0, checksum = 0, collisions = 0;
+  uint8_t* host = nullptr;  // serialized image in pinned host memory
+  size_t host_len = 0;
+  std::mutex mu;
+  std::condition_variable cv;
+  int stage = 0;
+  crum_status status = CRUM_OK;
+  std::string err;
+  cudaEvent_t ev_submit = nullptr, ev_captured = nullptr, ev_drained = nullptr;
+  std::chrono::steady_clock::time_point t_submit;
+  double t_captured_ms = 0, t_drained_ms = 0, t_persisted_ms = 0;
+  int half = 0;
+  bool drop_payload = false;  // null sink
+  std::string sink_path;
+  bool do_fsync = false;
+};
+
+struct crum_set {
+  crum_config cfg{};
+  std::string sink_dir;
+  int device = 0;
+  uint32_t set_id = 0;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::vector<crum::Alloc> allocs;
+  uint32_t next_id = 0;
+  uint64_t n_pages = 0;
+  bool table_dirty = true;
+  bool reg_changed = true;
+  // device state
+  crum::DevAlloc* d_allocs = nullptr;
+  uint64_t* d_first_page = nullptr;
+  size_t alloc_cap = 0;
+  uint64_t* d_h = nullptr;
+  size_t h_cap = 0;
+  uint32_t* d_mask = nullptr;
+  uint32_t* d_word_offset = nullptr;
+  size_t words_cap = 0;
+  unsigned long long* d_collisions = nullptr;
+  uint8_t* d_shadow = nullptr;
+  size_t shadow_cap = 0;  // pages
+  crum::Half half[2];
+  int next_half = 0;
+  uint64_t half_slots = 0;
+  cudaStream_t cap_stream = nullptr, drain_stream = nullptr;
+  cudaEvent_t ev_app = nullptr, ev_done = nullptr;
+  int map_hash = 1, map_gather = 1;
+  // chain state
+  uint64_t seq = 0;
+  crum_image* last = nullptr;
+  bool needs_full = true;
+  // background threads
+  std::shared_ptr<crum::PinnedPool> pool;
+  std::deque<crum_image*> plan_q, write_q;
+  std::condition_variable plan_cv, write_cv;
+  std::thread planner, writer;
+  bool stop = false;
+  int inflight = 0;
+};

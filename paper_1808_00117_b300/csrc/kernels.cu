@@ -1,0 +1,514 @@
+// Kernels of the capture/restore path and their host-side launchers.
+//
+//   k_hash_dirty  hash every page of the flattened work-list, compare with
+//                 the committed hash, commit the new one, set dirty bits
+//                 (the dirty test standing in for Algorithm 1's write faults)
+//   k_scan        one CTA: prefix sum of the dirty bitmap (ballot-free, since
+//                 the bitmap already packs 32 pages a word) -> slot of every
+//                 dirty page, dirty count, image header and allocation table
+//   k_gather      one group per dirty slot: page table entry, hash entry and
+//                 the page's bytes into staging ("drain the device", Sections
+//                 3.3-3.4), plus the image checksum of everything it writes
+//   k_restore     inverse scatter of image slots onto the allocations and
+//                 installation of the image hashes (Section 3.4 restart)
+//   k_hash_bytes  the hash over an arbitrary byte string (image checksum)
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+
+#include "device.cuh"
+#include "kernels.h"
+
+namespace crum {
+
+std::atomic<uint64_t> g_kernel_launches{0};
+
+namespace {
+
+using dev::hash_vec;
+using dev::ld_stream;
+using dev::mix;
+
+// ---------------------------------------------------------------- groups ---
+// A "group" of G threads owns one page at a time.  G == 32: a warp, several
+// groups per CTA.  G > 32: the whole CTA (blockDim.x == G).
+
+template <int G>
+struct GroupShared {
+  uint64_t red[G > 32 ? G / 32 : 1];
+  int flag;
+};
+
+template <int G>
+__device__ __forceinline__ uint64_t group_sum(uint64_t v, GroupShared<G>& sh) {
+  v = dev::warp_sum(v);
+  if constexpr (G == 32) {
+    return v;
+  } else {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();  // previous readers of sh.red are done
+    if (lane == 0) sh.red[warp] = v;
+    __syncthreads();
+    return dev::warp_sum(lane < G / 32 ? sh.red[lane] : 0ull);
+  }
+}
+
+// Value of thread 0 of the group, in every thread of the group.
+template <int G>
+__device__ __forceinline__ int group_bcast0(int v, GroupShared<G>& sh) {
+  if constexpr (G == 32) {
+    return __shfl_sync(0xffffffffu, v, 0);
+  } else {
+    __syncthreads();
+    if (threadIdx.x == 0) sh.flag = v;
+    __syncthreads();
+    return sh.flag;
+  }
+}
+
+template <int G>
+__device__ __forceinline__ bool group_any(bool v, GroupShared<G>& sh) {
+  if constexpr (G == 32) {
+    return __any_sync(0xffffffffu, v);
+  } else {
+    return __syncthreads_or(v) != 0;
+  }
+}
+
+// ------------------------------------------------------------- page hash ---
+
+// Full 64 KiB page; thread t of G hashes vectors t, t+G, ...  U loads are
+// issued before their arithmetic so each thread keeps U*16 bytes in flight.
+template <int G, int U>
+__device__ __forceinline__ uint64_t hash_full_page(const uint8_t* src, int t) {
+  constexpr int kPer = kPageVecs / G;
+  static_assert(kPer % U == 0, "unroll must divide the per-thread vector count");
+  constexpr uint64_t kStep = static_cast<uint64_t>(2 * G) * kPhi;
+  const uint4* v4 = reinterpret_cast<const uint4*>(src) + t;
+  uint64_t c = static_cast<uint64_t>(2 * t) * kPhi;
+  uint64_t h = 0;
+#pragma unroll 1
+  for (int k = 0; k < kPer; k += U) {
+    uint4 v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = ld_stream(v4 + (k + u) * G);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      h += hash_vec(v[u], c);
+      c += kStep;
+    }
+  }
+  return h;
+}
+
+// Page with valid < 64 KiB bytes: whole vectors, then the partial vector.
+template <int G>
+__device__ __forceinline__ uint64_t hash_tail_page(const uint8_t* src, uint32_t valid, int t) {
+  const uint32_t nvec = valid >> 4;
+  uint64_t h = 0;
+  for (uint32_t v = t; v < nvec; v += G)
+    h += hash_vec(ld_stream(src + 16ull * v), static_cast<uint64_t>(2 * v) * kPhi);
+  const uint32_t rem = valid & 15u;
+  if (rem != 0 && static_cast<uint32_t>(t) == nvec % G)
+    h += dev::hash_partial(dev::ld_partial(src + 16ull * nvec, rem), rem, 2ull * nvec);
+  return h;
+}
+
+// Verify mode: does any valid byte differ from the shadow copy?
+template <int G>
+__device__ __forceinline__ bool page_differs(const uint8_t* src, const uint8_t* shadow,
+                                             uint32_t valid, int t, GroupShared<G>& sh) {
+  const uint32_t nvec = valid >> 4;
+  bool diff = false;
+  for (uint32_t v = t; v < nvec; v += G) {
+    const uint4 x = ld_stream(src + 16ull * v);
+    const uint4 y = ld_stream(shadow + 16ull * v);
+    diff |= (x.x != y.x) | (x.y != y.y) | (x.z != y.z) | (x.w != y.w);
+  }
+  const uint32_t rem = valid & 15u;
+  if (rem != 0 && t == 0)
+    for (uint32_t b = 0; b < rem; ++b) diff |= src[16ull * nvec + b] != shadow[16ull * nvec + b];
+  return group_any<G>(diff, sh);
+}
+
+template <int G, int U, bool VERIFY>
+__global__ void __launch_bounds__(256) k_hash_dirty(HashArgs a) {
+  __shared__ GroupShared<G> sh;
+  constexpr int kGroupsPerCta = (G == 32) ? 256 / 32 : 1;
+  const int t = threadIdx.x % G;
+  const uint64_t group = static_cast<uint64_t>(blockIdx.x) * kGroupsPerCta + threadIdx.x / G;
+  const uint64_t n_groups = static_cast<uint64_t>(gridDim.x) * kGroupsPerCta;
+  for (uint64_t g = group; g < a.n_pages; g += n_groups) {
+    uint8_t* base;
+    uint64_t bytes, first;
+    if (a.allocs != nullptr) {
+      const uint32_t k = dev::find_alloc(a.first_page, a.n_allocs, g);
+      base = a.allocs[k].base;
+      bytes = a.allocs[k].bytes;
+      first = a.allocs[k].first_page;
+    } else {
+      base = a.one.base;
+      bytes = a.one.bytes;
+      first = 0;
+    }
+    const uint64_t p = g - first;
+    const uint8_t* src = base + p * kPage;
+    const uint32_t valid = dev::valid_bytes(bytes, p);
+    uint64_t h = (valid == kPage) ? hash_full_page<G, U>(src, t) : hash_tail_page<G>(src, valid, t);
+    h = group_sum<G>(h, sh);
+    if (a.h_out != nullptr) {
+      if (t == 0) a.h_out[g] = h;
+      continue;
+    }
+    int d = 0;
+    if (t == 0) d = a.full || h != a.h_table[g];
+    if constexpr (VERIFY) {
+      d = group_bcast0<G>(d, sh);
+      if (!d && page_differs<G>(src, a.shadow + g * kPage, valid, t, sh)) {
+        d = 1;
+        if (t == 0) atomicAdd(a.collisions, 1ull);
+      }
+    }
+    if (t == 0) {
+      a.h_table[g] = h;
+      if (d) atomicOr(a.dirty_mask + (g >> 5), 1u << (g & 31));
+    }
+  }
+}
+
+// ------------------------------------------------------------------ scan ---
+
+constexpr int kScanThreads = 1024;
+constexpr uint64_t kMagic = 0x31474D494D555243ull;  // "CRUMIMG1" little-endian
+
+__global__ void __launch_bounds__(kScanThreads) k_scan(ScanArgs a) {
+  __shared__ uint32_t wsum[32];
+  __shared__ uint64_t red[32];
+  __shared__ uint32_t total_sh;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint64_t per = (a.n_words + kScanThreads - 1) / kScanThreads;
+  const uint64_t w0 = min(static_cast<uint64_t>(tid) * per, a.n_words);
+  const uint64_t w1 = min(w0 + per, a.n_words);
+  uint32_t cnt = 0;
+  for (uint64_t w = w0; w < w1; ++w) cnt += __popc(a.mask[w]);
+  uint32_t incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t x = wsum[lane];
+    uint32_t s = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    wsum[lane] = s - x;  // exclusive prefix of warp totals
+  }
+  __syncthreads();
+  uint32_t run = wsum[warp] + incl - cnt;
+  for (uint64_t w = w0; w < w1; ++w) {
+    a.word_offset[w] = run;
+    run += __popc(a.mask[w]);
+  }
+  if (tid == kScanThreads - 1) {
+    a.word_offset[a.n_words] = run;
+    *a.n_dirty_out = run;
+    total_sh = run;
+    if (a.mailbox != nullptr) {
+      a.mailbox[0] = run;
+      a.mailbox[1] = a.collisions != nullptr ? *a.collisions : 0ull;
+      __threadfence_system();
+    }
+  }
+  __syncthreads();
+  const uint64_t n = total_sh;
+  const uint64_t A = a.n_allocs;
+  const uint64_t payload_off = kHeaderBytes + 16 * A + 16 * n;
+  const uint64_t image_bytes = payload_off + n * kPage + 8;
+  // header words 0..7, then allocation-table words 8 .. 8+2A-1
+  uint64_t* meta = reinterpret_cast<uint64_t*>(a.meta);
+  uint64_t cks = 0;
+  for (uint64_t k = tid; k < 8 + 2 * A; k += kScanThreads) {
+    uint64_t w;
+    if (k < 8) {
+      switch (k) {
+        case 0: w = kMagic; break;
+        case 1: w = 1ull | (static_cast<uint64_t>(a.flags) << 32); break;
+        case 2: w = a.seq; break;
+        case 3: w = a.parent_seq; break;
+        case 4: w = static_cast<uint64_t>(kPage) | (A << 32); break;
+        case 5: w = n; break;
+        case 6: w = payload_off; break;
+        default: w = image_bytes; break;
+      }
+    } else {
+      const uint64_t e = (k - 8) >> 1;
+      w = ((k - 8) & 1) ? a.allocs[e].bytes : static_cast<uint64_t>(a.allocs[e].id);
+    }
+    meta[k] = w;
+    cks += mix(w ^ (k * kPhi));
+  }
+  cks = dev::warp_sum(cks);
+  if (lane == 0) red[warp] = cks;
+  __syncthreads();
+  if (warp == 0) {
+    cks = dev::warp_sum(red[lane]);
+    if (lane == 0) *a.trailer = cks;
+  }
+}
+
+// ---------------------------------------------------------------- gather ---
+
+// Global page of dirty slot s: the word w holding it, then the r-th set bit.
+__device__ __forceinline__ uint64_t slot_to_page(const uint32_t* mask, const uint32_t* word_offset,
+                                                 uint64_t n_words, uint64_t s) {
+  uint64_t lo = 0, hi = n_words;  // last w with word_offset[w] <= s
+  while (hi - lo > 1) {
+    const uint64_t mid = (lo + hi) >> 1;
+    if (word_offset[mid] <= s)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  uint32_t m = mask[lo];
+  for (uint32_t r = static_cast<uint32_t>(s - word_offset[lo]); r > 0 && m != 0; --r) m &= m - 1;
+  if (m == 0) return ~0ull;  // inconsistent bitmap: the caller skips the slot
+  return lo * 32 + static_cast<uint64_t>(__ffs(m) - 1);
+}
+
+template <int G, int U, bool VERIFY>
+__global__ void __launch_bounds__(256) k_gather(GatherArgs a) {
+  __shared__ GroupShared<G> sh;
+  constexpr int kGroupsPerCta = (G == 32) ? 256 / 32 : 1;
+  const int t = threadIdx.x % G;
+  const uint64_t group = static_cast<uint64_t>(blockIdx.x) * kGroupsPerCta + threadIdx.x / G;
+  const uint64_t n_groups = static_cast<uint64_t>(gridDim.x) * kGroupsPerCta;
+  const uint64_t n = *a.n_dirty;
+  const uint64_t end = min(a.s_end, n);
+  const uint64_t A = a.n_allocs;
+  const uint64_t pt_w0 = (kHeaderBytes + 16 * A) / 8;           // first page-table word
+  const uint64_t pay_w0 = (kHeaderBytes + 16 * A + 16 * n) / 8;  // first payload word
+  uint64_t* meta = reinterpret_cast<uint64_t*>(a.meta);
+  for (uint64_t s = a.s_begin + group; s < end; s += n_groups) {
+    const uint64_t g = slot_to_page(a.mask, a.word_offset, a.n_words, s);
+    if (g >= a.n_pages) continue;  // never taken when the scan is consistent
+    const uint32_t k = dev::find_alloc(a.first_page, a.n_allocs, g);
+    const uint64_t p = g - a.allocs[k].first_page;
+    const uint8_t* src = a.allocs[k].base + p * kPage;
+    const uint32_t valid = dev::valid_bytes(a.allocs[k].bytes, p);
+    uint8_t* dst = a.payload + (s - a.s_begin) * kPage;
+    uint64_t cks = 0;
+    if (t == 0) {
+      const uint64_t pte = static_cast<uint64_t>(k) | (p << 32);
+      const uint64_t hv = a.h_table[g];
+      meta[pt_w0 + s] = pte;
+      meta[pt_w0 + n + s] = hv;
+      cks = mix(pte ^ ((pt_w0 + s) * kPhi)) + mix(hv ^ ((pt_w0 + n + s) * kPhi));
+    }
+    uint64_t c = (pay_w0 + s * (kPage / 8) + 2ull * t) * kPhi;
+    constexpr uint64_t kStep = static_cast<uint64_t>(2 * G) * kPhi;
+    if (valid == kPage) {
+      constexpr int kPer = kPageVecs / G;
+#pragma unroll 1
+      for (int j = 0; j < kPer; j += U) {
+        uint4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = ld_stream(src + 16ull * (t + (j + u) * G));
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const uint64_t off = 16ull * (t + (j + u) * G);
+          dev::st_stream(dst + off, v[u]);
+          if constexpr (VERIFY) dev::st_stream(a.shadow + g * kPage + off, v[u]);
+          cks += hash_vec(v[u], c);
+          c += kStep;
+        }
+      }
+    } else {
+      for (uint32_t v = t; v < kPageVecs; v += G) {
+        const uint32_t lo = 16u * v;
+        uint4 x = make_uint4(0u, 0u, 0u, 0u);
+        if (lo + 16 <= valid)
+          x = ld_stream(src + lo);
+        else if (lo < valid)
+          x = dev::ld_partial(src + lo, valid - lo);
+        dev::st_stream(dst + lo, x);
+        if constexpr (VERIFY) dev::st_stream(a.shadow + g * kPage + lo, x);
+        cks += hash_vec(x, c);
+        c += kStep;
+      }
+    }
+    cks = group_sum<G>(cks, sh);
+    if (t == 0) atomicAdd(reinterpret_cast<unsigned long long*>(a.trailer),
+                          static_cast<unsigned long long>(cks));
+  }
+}
+
+// --------------------------------------------------------------- restore ---
+
+template <int G>
+__global__ void __launch_bounds__(256) k_restore(RestoreArgs a) {
+  constexpr int kGroupsPerCta = (G == 32) ? 256 / 32 : 1;
+  const int t = threadIdx.x % G;
+  const uint64_t group = static_cast<uint64_t>(blockIdx.x) * kGroupsPerCta + threadIdx.x / G;
+  const uint64_t n_groups = static_cast<uint64_t>(gridDim.x) * kGroupsPerCta;
+  for (uint64_t s = group; s < a.n_slots; s += n_groups) {
+    const uint32_t k = a.ptab[2 * s];
+    const uint64_t p = a.ptab[2 * s + 1];
+    if (k >= a.n_allocs || p >= a.allocs[k].n_pages) continue;  // rejected on the host already
+    uint8_t* dst = a.allocs[k].base + p * kPage;
+    const uint32_t valid = dev::valid_bytes(a.allocs[k].bytes, p);
+    const uint8_t* src = a.payload + s * kPage;
+    const uint32_t nvec = valid >> 4;
+    for (uint32_t v = t; v < nvec; v += G)
+      *reinterpret_cast<uint4*>(dst + 16ull * v) = ld_stream(src + 16ull * v);
+    const uint32_t rem = valid & 15u;
+    if (rem != 0 && t == 0)
+      for (uint32_t b = 0; b < rem; ++b) dst[16ull * nvec + b] = src[16ull * nvec + b];
+    if (t == 0) a.h_table[a.allocs[k].first_page + p] = a.hashes[s];
+  }
+}
+
+// ------------------------------------------------------------ hash bytes ---
+
+__global__ void __launch_bounds__(256) k_hash_bytes(const uint8_t* p, uint64_t n,
+                                                    uint64_t first_index,
+                                                    unsigned long long* out) {
+  const uint64_t nvec = n >> 4;
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  uint64_t h = 0;
+  for (uint64_t v = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < nvec;
+       v += stride)
+    h += hash_vec(ld_stream(p + 16 * v), (first_index + 2 * v) * kPhi);
+  const uint32_t rem = static_cast<uint32_t>(n & 15u);
+  if (rem != 0 && blockIdx.x == 0 && threadIdx.x == 0)
+    h += dev::hash_partial(dev::ld_partial(p + 16 * nvec, rem), rem, first_index + 2 * nvec);
+  h = dev::warp_sum(h);
+  if ((threadIdx.x & 31) == 0 && h != 0) atomicAdd(out, static_cast<unsigned long long>(h));
+}
+
+int g_num_sms = 0;
+
+int num_sms() {
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 1;
+  }
+  return g_num_sms;
+}
+
+template <typename K>
+int resident_ctas(K kernel, int threads) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+  return std::max(1, per_sm) * num_sms();
+}
+
+// Grid for `units` groups of a kernel with `groups_per_cta` groups per CTA:
+// enough CTAs for every unit, at most what is resident at once.
+template <typename K>
+unsigned grid_for(K kernel, uint64_t units, int groups_per_cta) {
+  const uint64_t need = (units + groups_per_cta - 1) / groups_per_cta;
+  const uint64_t cap = static_cast<uint64_t>(resident_ctas(kernel, 256));
+  return static_cast<unsigned>(std::max<uint64_t>(1, std::min(need, cap)));
+}
+
+template <int G, int U, bool V>
+cudaError_t launch_hash_t(const HashArgs& a, cudaStream_t st) {
+  auto kern = k_hash_dirty<G, U, V>;
+  const unsigned grid = grid_for(kern, a.n_pages, G == 32 ? 8 : 1);
+  kern<<<grid, 256, 0, st>>>(a);
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+template <int G, int U, bool V>
+cudaError_t launch_gather_t(const GatherArgs& a, uint64_t max_slots, cudaStream_t st) {
+  auto kern = k_gather<G, U, V>;
+  const unsigned grid = grid_for(kern, max_slots, G == 32 ? 8 : 1);
+  kern<<<grid, 256, 0, st>>>(a);
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+const Mapping kMappings[] = {
+    {32, 4}, {32, 8}, {32, 16}, {256, 2}, {256, 4}, {256, 8},
+};
+const int kNumMappings = sizeof(kMappings) / sizeof(kMappings[0]);
+
+cudaError_t launch_hash_dirty(const HashArgs& a, int mapping, bool verify, cudaStream_t st) {
+  if (a.n_pages == 0) return cudaSuccess;
+#define CRUM_HASH_CASE(i, G, U)                                               \
+  case i:                                                                     \
+    return verify ? launch_hash_t<G, U, true>(a, st) : launch_hash_t<G, U, false>(a, st);
+  switch (mapping) {
+    CRUM_HASH_CASE(0, 32, 4)
+    CRUM_HASH_CASE(1, 32, 8)
+    CRUM_HASH_CASE(2, 32, 16)
+    CRUM_HASH_CASE(3, 256, 2)
+    CRUM_HASH_CASE(4, 256, 4)
+    CRUM_HASH_CASE(5, 256, 8)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef CRUM_HASH_CASE
+}
+
+cudaError_t launch_scan(const ScanArgs& a, cudaStream_t st) {
+  k_scan<<<1, kScanThreads, 0, st>>>(a);
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const GatherArgs& a, uint64_t max_slots, int mapping, bool verify,
+                          cudaStream_t st) {
+  if (max_slots == 0) return cudaSuccess;
+#define CRUM_GATHER_CASE(i, G, U)                                                     \
+  case i:                                                                             \
+    return verify ? launch_gather_t<G, U, true>(a, max_slots, st)                     \
+                  : launch_gather_t<G, U, false>(a, max_slots, st);
+  switch (mapping) {
+    CRUM_GATHER_CASE(0, 32, 4)
+    CRUM_GATHER_CASE(1, 32, 8)
+    CRUM_GATHER_CASE(2, 32, 16)
+    CRUM_GATHER_CASE(3, 256, 2)
+    CRUM_GATHER_CASE(4, 256, 4)
+    CRUM_GATHER_CASE(5, 256, 8)
+    default:
+      return cudaErrorInvalidValue;
+  }
+#undef CRUM_GATHER_CASE
+}
+
+cudaError_t launch_restore(const RestoreArgs& a, cudaStream_t st) {
+  if (a.n_slots == 0) return cudaSuccess;
+  auto kern = k_restore<32>;
+  const unsigned grid = grid_for(kern, a.n_slots, 8);
+  kern<<<grid, 256, 0, st>>>(a);
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hash_bytes(const uint8_t* p, uint64_t n, uint64_t first_index, uint64_t* out,
+                              cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const uint64_t nvec = (n + 15) / 16;
+  const uint64_t cap = static_cast<uint64_t>(resident_ctas(k_hash_bytes, 256));
+  const unsigned grid =
+      static_cast<unsigned>(std::max<uint64_t>(1, std::min((nvec + 255) / 256, cap)));
+  k_hash_bytes<<<grid, 256, 0, st>>>(p, n, first_index, reinterpret_cast<unsigned long long*>(out));
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+}  // namespace crum

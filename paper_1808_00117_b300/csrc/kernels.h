@@ -1,0 +1,88 @@
+// Launch interface of the capture/restore kernels (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+
+#include "device.cuh"
+
+namespace crum {
+
+extern std::atomic<uint64_t> g_kernel_launches;
+
+// Thread mapping of the page kernels: G threads per page (32: one warp per
+// page, several pages per CTA; 256: one CTA per page) and U 16-byte loads
+// in flight per thread.  Chosen per set by the autotuner.
+struct Mapping {
+  int group;
+  int unroll;
+};
+extern const Mapping kMappings[];
+extern const int kNumMappings;
+
+struct HashArgs {
+  const DevAlloc* allocs;      // device table, or nullptr to use `one`
+  const uint64_t* first_page;  // device, n_allocs entries (first page of each)
+  DevAlloc one;                // single allocation (allocs == nullptr)
+  uint32_t n_allocs;
+  uint64_t n_pages;
+  uint64_t* h_table;      // committed hashes: read as previous, overwritten with new
+  uint64_t* h_out;        // if set: write hashes here and skip the dirty logic
+  uint32_t* dirty_mask;   // bit g%32 of word g/32 set for dirty page g (pre-zeroed)
+  int full;               // every page dirty
+  const uint8_t* shadow;  // verify mode: last checkpointed bytes, page g at g*64 KiB
+  unsigned long long* collisions;
+};
+
+struct ScanArgs {
+  const uint32_t* mask;
+  uint64_t n_words;          // ceil(n_pages / 32)
+  uint32_t* word_offset;     // n_words + 1: dirty pages before each word; last = total
+  uint64_t* n_dirty_out;     // device
+  volatile uint64_t* mailbox;  // mapped pinned host: [0] dirty count, [1] collisions (optional)
+  const unsigned long long* collisions;  // verify-mode collision counter (optional)
+  const DevAlloc* allocs;
+  uint32_t n_allocs;
+  uint8_t* meta;             // header + allocation table + page table + hashes
+  uint64_t* trailer;         // set to the checksum of header + allocation table
+  uint64_t seq, parent_seq;
+  uint32_t flags;
+};
+
+struct GatherArgs {
+  const DevAlloc* allocs;
+  const uint64_t* first_page;
+  uint32_t n_allocs;
+  const uint32_t* mask;
+  const uint32_t* word_offset;
+  uint64_t n_words;
+  uint64_t n_pages;
+  const uint64_t* n_dirty;   // device
+  const uint64_t* h_table;
+  uint8_t* meta;
+  uint8_t* payload;          // slot s goes to payload + (s - s_begin) * 64 KiB
+  uint64_t* trailer;         // checksum accumulator
+  uint64_t s_begin, s_end;   // slot range of this launch (clipped to n_dirty)
+  uint8_t* shadow;           // verify mode: copy of each gathered page
+};
+
+struct RestoreArgs {
+  const DevAlloc* allocs;
+  uint32_t n_allocs;
+  const uint32_t* ptab;      // 2 u32 per slot: allocation index, page index
+  const uint64_t* hashes;    // per slot
+  const uint8_t* payload;    // slot s at payload + s * 64 KiB
+  uint64_t n_slots;
+  uint64_t* h_table;
+};
+
+cudaError_t launch_hash_dirty(const HashArgs& a, int mapping, bool verify, cudaStream_t st);
+cudaError_t launch_scan(const ScanArgs& a, cudaStream_t st);
+cudaError_t launch_gather(const GatherArgs& a, uint64_t max_slots, int mapping, bool verify,
+                          cudaStream_t st);
+cudaError_t launch_restore(const RestoreArgs& a, cudaStream_t st);
+cudaError_t launch_hash_bytes(const uint8_t* p, uint64_t n, uint64_t first_index, uint64_t* out,
+                              cudaStream_t st);
+
+}  // namespace crum

@@ -1,0 +1,173 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module draws random numbers and nothing else: it holds none of the
+method's arithmetic (no page hash, no dirty rule, no image format).  Both
+the CUDA path and the CPU oracle consume what it produces: device tensors
+filled here are copied to the host for the oracle.
+
+Workload recipes (the paper's own applications and data are not used;
+synthetic data of the same shape stands in for them):
+
+* ``small16m``  one 16 MiB fp32 allocation, uniform in [-1, 1) (the synthetic
+  single-GPU benchmark's random-float vectors, Section 4.5, scaled down);
+  10 % of pages rewritten, chosen uniformly without replacement.
+* ``uint32_8g`` one 8 GiB allocation of random 32-bit words; 5 % of pages
+  (6,554) dirtied per step in clustered runs: run starts uniform, run
+  lengths geometric with p = 1/16 truncated to [1, 64], runs merged until
+  the union reaches the target, the last run trimmed to hit it exactly.
+* ``stencil``   200 fp64 fields with log-uniform sizes (4 KiB .. 512 MiB,
+  rounded to 4 KiB, rescaled to a target total), the many-regions-of-uneven-
+  size shape of the HPGMG/HYPRE runs (Section 4.2-4.3).
+* ``large``     4,096 allocations, log-uniform 64 KiB .. 2 GiB rescaled to a
+  target total, fp32 or bf16 bit patterns, 2 % of pages per step.
+
+A "mutation" xors every 64-bit word of a chosen page with one nonzero
+per-page mask, so every chosen page really changes.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import List
+
+import numpy as np
+
+PAGE = 65536
+KiB, MiB, GiB = 1 << 10, 1 << 20, 1 << 30
+
+
+def pages_of(nbytes: int) -> int:
+    return -(-nbytes // PAGE)
+
+
+@dataclass
+class Workload:
+    name: str
+    sizes: List[int]
+    kind: str
+    dirty_frac: float
+    steps: int
+    dirty_mode: str = "uniform"  # uniform | runs
+    seed: int = 0x5EED
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def total_bytes(self) -> int:
+        return sum(self.sizes)
+
+    @property
+    def n_pages(self) -> int:
+        return sum(pages_of(s) for s in self.sizes)
+
+
+def loguniform_sizes(seed: int, n: int, lo: int, hi: int, total: int, round_to: int = 4 * KiB,
+                     tol: float = 0.005) -> List[int]:
+    """n sizes log-uniform in [lo, hi], rounded to `round_to`, then rescaled
+    by a common factor (clamped to [lo, hi]) until the total is within `tol`
+    of `total`."""
+    rng = np.random.default_rng(seed)
+    x = np.exp(rng.uniform(math.log(lo), math.log(hi), size=n))
+    for _ in range(200):
+        s = np.clip(np.round(x / round_to) * round_to, lo, hi)
+        t = float(s.sum())
+        if abs(t - total) <= tol * total:
+            break
+        x = np.clip(x * (total / t), lo, hi)
+    return [int(v) for v in s]
+
+
+def workload(name: str) -> Workload:
+    if name == "small16m":
+        return Workload(name, [16 * MiB], "fp32", 0.10, 1, "uniform", 0x5EED + 0)
+    if name == "uint32_8g":
+        return Workload(name, [8 * GiB], "u32", 0.05, 10, "runs", 0x5EED + 1)
+    if name == "stencil":
+        sizes = loguniform_sizes(0x5EED + 2, 200, 4 * KiB, 512 * MiB, 24 * GiB)
+        return Workload(name, sizes, "fp64", 0.30, 20, "uniform", 0x5EED + 2)
+    if name == "large":
+        sizes = loguniform_sizes(0x5EED + 4, 4096, 64 * KiB, 2 * GiB, 140 * GiB)
+        return Workload(name, sizes, "fp32", 0.02, 50, "uniform", 0x5EED + 4)
+    raise KeyError(name)
+
+
+# ------------------------------------------------------------- selections ---
+
+def choose_uniform(seed: int, n_pages: int, k: int) -> np.ndarray:
+    """k distinct page indices in [0, n_pages), sorted."""
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(n_pages, size=min(k, n_pages), replace=False)).astype(np.int64)
+
+
+def choose_runs(seed: int, n_pages: int, target: int, p: float = 1 / 16, max_len: int = 64) -> np.ndarray:
+    """Clustered dirty runs: uniform starts, geometric(p) lengths truncated to
+    [1, max_len], merged until `target` distinct pages; sorted."""
+    rng = np.random.default_rng(seed)
+    target = min(target, n_pages)
+    chosen = np.zeros(n_pages, dtype=bool)
+    count = 0
+    while count < target:
+        start = int(rng.integers(0, n_pages))
+        length = int(min(max(rng.geometric(p), 1), max_len))
+        seg = chosen[start:start + length]
+        new = np.flatnonzero(~seg)
+        if count + new.size > target:
+            new = new[: target - count]
+        seg[new] = True
+        count += new.size
+    return np.flatnonzero(chosen).astype(np.int64)
+
+
+def choose_step(wl: Workload, step: int, n_pages: int) -> np.ndarray:
+    k = max(1, int(round(wl.dirty_frac * n_pages)))
+    seed = wl.seed * 1_000_003 + step
+    if wl.dirty_mode == "runs":
+        return choose_runs(seed, n_pages, k)
+    return choose_uniform(seed, n_pages, k)
+
+
+# ------------------------------------------------------------ device fills ---
+
+def _torch():
+    import torch
+    return torch
+
+
+def fill_(buf, seed: int, kind: str) -> None:
+    """Fill a uint8 tensor in place from a seeded torch generator."""
+    torch = _torch()
+    g = torch.Generator(device=buf.device)
+    g.manual_seed(seed)
+    n = buf.numel()
+    n8 = n // 8 * 8
+    if kind in ("fp32", "fp64") and n8:
+        dt = torch.float32 if kind == "fp32" else torch.float64
+        buf[:n8].view(dt).uniform_(-1.0, 1.0, generator=g)
+    elif kind == "bf16" and n8:
+        buf[:n8].view(torch.bfloat16).normal_(generator=g)
+    elif n8:
+        buf[:n8].view(torch.int64).random_(generator=g)
+    if n > n8:
+        buf[n8:] = torch.randint(0, 256, (n - n8,), dtype=torch.uint8, device=buf.device, generator=g)
+
+
+def mutate_pages_(buf, pages, seed: int) -> None:
+    """xor every word of each listed page (page indices within `buf`) with a
+    per-page nonzero 64-bit mask; a partial last page gets a nonzero byte mask."""
+    torch = _torch()
+    pages = torch.as_tensor(np.asarray(pages, dtype=np.int64), device=buf.device)
+    if pages.numel() == 0:
+        return
+    g = torch.Generator(device=buf.device)
+    g.manual_seed(seed)
+    n = buf.numel()
+    n_full = n // PAGE
+    full = pages[pages < n_full]
+    if full.numel():
+        v = buf[: n_full * PAGE].view(torch.int64).view(n_full, PAGE // 8)
+        masks = torch.randint(1, 2**62, (full.numel(), 1), dtype=torch.int64, device=buf.device,
+                              generator=g) | 1
+        v[full] = v[full] ^ masks
+    if (pages == n_full).any() and n > n_full * PAGE:
+        tail = buf[n_full * PAGE:]
+        m = torch.randint(1, 256, (1,), dtype=torch.int64, device=buf.device, generator=g).to(torch.uint8)
+        tail.bitwise_xor_(m)

@@ -1,0 +1,318 @@
+"""GPU parity: the CUDA library, called through its C ABI, against the CPU
+oracle on the same seeded inputs.  Integer and byte work, so the bar is
+bit-exact: hashes, dirty sets, page tables, whole images and restored
+memory."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1808_00117_b300 as crum
+from paper_1808_00117_b300 import workloads as W
+
+from helpers import (device_buffers, first_diff, host_copies, make_set, mutate, page_offsets,
+                     page_table, parse_header, stream_handle, torch)
+
+pytestmark = pytest.mark.gpu
+
+P = 65536
+# sizes that exercise full pages, every kind of tail and several tiles
+RAGGED = [1, 7, 8, 9, 15, 16, 17, 24, 4096 + 3, P - 8, P, P + 24, 3 * P - 5, 300 * P + 4104]
+
+
+@pytest.fixture(autouse=True)
+def _cuda():
+    t = torch()
+    if not t.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    crum.load()
+    yield
+    t.cuda.synchronize()
+
+
+def test_hash_pages_matches_oracle():
+    t = torch()
+    bufs = device_buffers(RAGGED, seed=1)
+    for b, h in zip(bufs, host_copies(bufs)):
+        n = W.pages_of(b.numel())
+        out = t.zeros(n, dtype=t.int64, device="cuda")
+        crum.hash_pages(b.data_ptr(), b.numel(), out.data_ptr(), stream_handle())
+        got = out.cpu().numpy().view(np.uint64)
+        exp = oracle.hash_all([h])
+        assert np.array_equal(got, exp), f"size {b.numel()}"
+
+
+def test_hash_pages_special_contents():
+    t = torch()
+    for fill in [0, 255]:
+        b = t.full((5 * P + 100,), fill, dtype=t.uint8, device="cuda")
+        out = t.zeros(6, dtype=t.int64, device="cuda")
+        crum.hash_pages(b.data_ptr(), b.numel(), out.data_ptr(), stream_handle())
+        assert np.array_equal(out.cpu().numpy().view(np.uint64), oracle.hash_all([b.cpu().numpy()]))
+    # the all-zero full page has the value pinned from the published sequence
+    z = t.zeros(P, dtype=t.uint8, device="cuda")
+    out = t.zeros(1, dtype=t.int64, device="cuda")
+    crum.hash_pages(z.data_ptr(), P, out.data_ptr(), stream_handle())
+    assert int(out.cpu().numpy().view(np.uint64)[0]) == 0xA19D4D208D42E336
+
+
+@pytest.mark.parametrize("first", [0, 3, 8191, 2**33 + 1])
+def test_hash_bytes_matches_oracle(first):
+    t = torch()
+    for n in [1, 8, 15, 16, 17, 100, 4096, 65536 + 8, 3_000_000 + 3]:
+        b = device_buffers([n], seed=n)[0]
+        out = t.zeros(1, dtype=t.int64, device="cuda")
+        crum.hash_bytes(b.data_ptr(), n, first, out.data_ptr(), stream_handle())
+        got = int(out.cpu().numpy().view(np.uint64)[0])
+        assert got == oracle.hash_bytes(b.cpu().numpy(), first), n
+
+
+def _checkpoint_bytes(s, flags=crum.INCR):
+    img = s.checkpoint(stream_handle(), flags)
+    img.wait(crum.WAIT_PERSISTED)
+    return img, img.to_bytes()
+
+
+def test_small16m_full_incremental_restore():
+    """16 MiB fp32, full checkpoint, 10 % of pages rewritten, incremental
+    checkpoint, restore of the chain onto garbage."""
+    wl = W.workload("small16m")
+    bufs = device_buffers(wl.sizes, seed=wl.seed, kind=wl.kind)
+    s = make_set(bufs)
+    o = oracle.OracleSet(wl.sizes)
+    img0, b0 = _checkpoint_bytes(s)
+    e0, d0, h0, _ = o.checkpoint(host_copies(bufs))
+    assert first_diff(b0, e0) is None
+    assert np.array_equal(s.hashes(), h0)
+    pages = W.choose_step(wl, 1, wl.n_pages)
+    assert pages.size == 26
+    W.mutate_pages_(bufs[0], pages, wl.seed + 1)
+    img1, b1 = _checkpoint_bytes(s)
+    state1 = host_copies(bufs)
+    e1, d1, h1, _ = o.checkpoint(state1)
+    assert set(np.flatnonzero(d1).tolist()) == set(pages.tolist())
+    assert first_diff(b1, e1) is None
+    info = img1.info()
+    assert info["n_dirty"] == 26 and info["parent_seq"] == 0 and info["full"] == 0
+    assert info["checksum"] == int(np.frombuffer(e1[-8:], dtype=np.uint64)[0])
+    # restore onto garbage
+    W.fill_(bufs[0], 12345, "u32")
+    s.restore(img1, stream_handle())
+    torch().cuda.synchronize()
+    assert np.array_equal(host_copies(bufs)[0], state1[0])
+    assert np.array_equal(s.hashes(), h1)
+    # after restore, an unchanged state checkpoints empty with the right parent
+    img2, b2 = _checkpoint_bytes(s)
+    assert parse_header(b2)["n"] == 0 and parse_header(b2)["parent"] == 1
+    for i in (img0, img1, img2):
+        i.release()
+    s.destroy()
+
+
+def test_ragged_allocations_chain():
+    sizes = RAGGED
+    bufs = device_buffers(sizes, seed=3)
+    s = make_set(bufs)
+    o = oracle.OracleSet(sizes)
+    chain_dev, states = [], []
+    for step in range(4):
+        if step:
+            touched = mutate(bufs, sizes, 0.3, seed=100 + step)
+        img, got = _checkpoint_bytes(s)
+        state = host_copies(bufs)
+        exp, d, h, _ = o.checkpoint(state)
+        if step:
+            assert set(np.flatnonzero(d).tolist()) == touched
+        assert first_diff(got, exp) is None, f"step {step}"
+        chain_dev.append(img)
+        states.append(state)
+    # restore every prefix of the chain onto garbage
+    for k in range(len(chain_dev)):
+        for i, b in enumerate(bufs):
+            W.fill_(b, 999 + i + k, "u32")
+        s.restore(chain_dev[k], stream_handle())
+        torch().cuda.synchronize()
+        for got, exp in zip(host_copies(bufs), states[k]):
+            assert np.array_equal(got, exp), f"prefix {k}"
+        assert np.array_equal(s.hashes(), oracle.hash_all(states[k]))
+    s.destroy()
+
+
+def test_empty_and_all_dirty():
+    sizes = [5 * P + 3, 2 * P]
+    bufs = device_buffers(sizes, seed=5)
+    s = make_set(bufs)
+    o = oracle.OracleSet(sizes)
+    _, b0 = _checkpoint_bytes(s)
+    e0, *_ = o.checkpoint(host_copies(bufs))
+    assert first_diff(b0, e0) is None
+    _, b1 = _checkpoint_bytes(s)
+    e1, d1, *_ = o.checkpoint(host_copies(bufs))
+    assert d1.sum() == 0 and first_diff(b1, e1) is None
+    # explicit FULL: every page, no parent
+    _, b2 = _checkpoint_bytes(s, crum.FULL)
+    e2, *_ = o.checkpoint(host_copies(bufs), full=True)
+    assert first_diff(b2, e2) is None and parse_header(b2)["flags"] == 1
+    s.destroy()
+
+
+def test_chunked_capture_small_staging():
+    """Staging halves of 3 pages: captures run chunk by chunk."""
+    sizes = [17 * P + 5, 4 * P]
+    bufs = device_buffers(sizes, seed=7)
+    s = make_set(bufs, staging_bytes=6 * P)
+    o = oracle.OracleSet(sizes)
+    for step in range(3):
+        if step:
+            mutate(bufs, sizes, 0.5, seed=70 + step)
+        _, got = _checkpoint_bytes(s)
+        exp, *_ = o.checkpoint(host_copies(bufs))
+        assert first_diff(got, exp) is None, f"step {step}"
+    s.destroy()
+
+
+def test_registration_change_forces_full():
+    sizes = [3 * P, P + 1]
+    bufs = device_buffers(sizes, seed=9)
+    s = crum.CheckpointSet()
+    s.register(bufs[0].data_ptr(), sizes[0])
+    _, b0 = _checkpoint_bytes(s)
+    s.register(bufs[1].data_ptr(), sizes[1])
+    _, b1 = _checkpoint_bytes(s)
+    h = parse_header(b1)
+    assert h["flags"] == 1 and h["n"] == 5 and h["A"] == 2
+    exp, *_ = oracle.OracleSet(sizes).checkpoint(host_copies(bufs))
+    # same bytes as a fresh set's first image except seq
+    assert first_diff(b1[32:-8], exp[32:-8]) is None
+    s.destroy()
+
+
+def test_verify_mode_reports_injected_collision():
+    sizes = [4 * P]
+    bufs = device_buffers(sizes, seed=11)
+    s = make_set(bufs, verify=1)
+    o = oracle.OracleSet(sizes)
+    _, _ = _checkpoint_bytes(s, crum.VERIFY)
+    prev = host_copies(bufs)
+    o.checkpoint(prev)
+    # change page 2, then make the committed hash equal the new one
+    W.mutate_pages_(bufs[0], [2], 77)
+    now = host_copies(bufs)
+    new_h = int(oracle.hash_all(now)[2])
+    s.poke_hash(2, new_h)
+    o.h_prev[2] = new_h
+    img = s.checkpoint(stream_handle(), crum.VERIFY)
+    st = img.wait(crum.WAIT_PERSISTED)
+    assert st == crum.ECOLLISION and img.info()["collisions"] == 1
+    exp, d, _, coll = o.checkpoint(now, verify_prev=prev)
+    assert coll == 1
+    assert first_diff(img.to_bytes(), exp) is None
+    assert page_table(img.to_bytes()).tolist() == [[0, 2]]
+    s.destroy()
+
+
+def test_save_load_corrupt_mismatch(tmp_path):
+    sizes = [6 * P + 17]
+    bufs = device_buffers(sizes, seed=13)
+    s = make_set(bufs)
+    img0, b0 = _checkpoint_bytes(s)
+    mutate(bufs, sizes, 0.4, seed=5)
+    img1, b1 = _checkpoint_bytes(s)
+    state = host_copies(bufs)
+    p0, p1 = str(tmp_path / "a.img"), str(tmp_path / "b.img")
+    img0.save(p0)
+    img1.save(p1)
+    s2 = make_set(bufs)
+    l0 = s2.load_image(p0)
+    l1 = s2.load_image(p1, parent=l0)
+    assert l1.info()["n_dirty"] == parse_header(b1)["n"]
+    W.fill_(bufs[0], 4242, "u32")
+    s2.restore(l1, stream_handle())
+    torch().cuda.synchronize()
+    assert np.array_equal(host_copies(bufs)[0], state[0])
+    # a flipped payload byte, a flipped header byte, a truncated file
+    for pos in [len(b1) // 2, 20, len(b1) - 3]:
+        bad = bytearray(b1)
+        bad[pos] ^= 0x40
+        with pytest.raises(crum.CrumError) as e:
+            s2.image_from_bytes(bytes(bad), parent=l0)
+        assert e.value.status == crum.ECORRUPT
+    with pytest.raises(crum.CrumError) as e:
+        s2.image_from_bytes(b1[:-16], parent=l0)
+    assert e.value.status == crum.ECORRUPT
+    # wrong parent
+    with pytest.raises(crum.CrumError) as e:
+        s2.image_from_bytes(b1, parent=None)
+    assert e.value.status == crum.EMISMATCH
+    # restore onto a set with a different registration table
+    other = device_buffers([6 * P + 16], seed=1)
+    s3 = make_set(other)
+    with pytest.raises(crum.CrumError) as e:
+        s3.restore(img0, stream_handle())
+    assert e.value.status == crum.EMISMATCH
+    for x in (s, s2, s3):
+        x.destroy()
+
+
+def test_file_sink_writes_each_image(tmp_path):
+    sizes = [3 * P + 11]
+    bufs = device_buffers(sizes, seed=15)
+    s = make_set(bufs, sink=crum.SINK_FILE, sink_dir=str(tmp_path), fsync=1)
+    o = oracle.OracleSet(sizes)
+    for step in range(3):
+        if step:
+            mutate(bufs, sizes, 0.5, seed=step)
+        img, got = _checkpoint_bytes(s)
+        exp, *_ = o.checkpoint(host_copies(bufs))
+        files = sorted(os.listdir(tmp_path))
+        assert len(files) == step + 1
+        name = [f for f in files if f.endswith(f"_{step}.img")][0]
+        with open(os.path.join(tmp_path, name), "rb") as f:
+            on_disk = f.read()
+        assert on_disk == exp == got
+    s.destroy()
+
+
+def test_null_sink_still_counts_pages():
+    sizes = [4 * P]
+    bufs = device_buffers(sizes, seed=17)
+    s = make_set(bufs, sink=crum.SINK_NULL)
+    img = s.checkpoint(stream_handle())
+    img.wait()
+    assert img.info()["n_dirty"] == 4
+    with pytest.raises(crum.CrumError):
+        img.to_bytes()
+    s.destroy()
+
+
+def test_invalid_registrations():
+    t = torch()
+    b = t.empty(4 * P, dtype=t.uint8, device="cuda")
+    s = crum.CheckpointSet()
+    for ptr, n in [(b.data_ptr() + 8, P), (b.data_ptr(), 0), (0, P)]:
+        with pytest.raises(crum.CrumError) as e:
+            s.register(ptr, n)
+        assert e.value.status == crum.EINVAL
+    s.register(b.data_ptr(), 2 * P)
+    with pytest.raises(crum.CrumError) as e:
+        s.register(b.data_ptr() + P, 2 * P)  # overlaps
+    assert e.value.status == crum.EINVAL
+    with pytest.raises(crum.CrumError) as e:
+        s.checkpoint(stream_handle(), crum.VERIFY)  # set made without verify
+    assert e.value.status == crum.EINVAL
+    empty = crum.CheckpointSet()
+    with pytest.raises(crum.CrumError) as e:
+        empty.checkpoint(stream_handle())
+    assert e.value.status == crum.EINVAL
+    s.destroy()
+    empty.destroy()
+
+
+def test_kernels_are_launched():
+    before = crum.kernel_launches()
+    bufs = device_buffers([2 * P], seed=19)
+    s = make_set(bufs)
+    s.checkpoint(stream_handle()).wait()
+    assert crum.kernel_launches() - before == 3  # hash, scan, gather
+    s.destroy()
