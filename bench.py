@@ -1,0 +1,520 @@
+#!/usr/bin/env python
+"""Benchmark of the B300 capture/restore path (one JSON line on rank 0).
+
+Workload (default ``uint32_8g``): one 8 GiB allocation of random 32-bit
+words, 64 KiB pages (131,072), registered with one set.  Setup takes the
+full checkpoint; each step then lets the application's update kernel dirty
+5 % of the pages (6,554, clustered runs) and takes an incremental
+checkpoint on the application's stream.  A step is one pass of the whole
+path: hash every page, detect dirty pages, compact them into staging,
+drain them to pinned host memory and persist the image (memory sink); the
+drain overlaps the next step's application work and capture.  After the
+timed steps the chain (full + every incremental) is restored.
+
+``value`` is the capture throughput: footprint bytes checkpointed per
+second of capture-kernel device time (hash + scan + gather, CUDA events on
+the capture stream), mean over the K timed steps.  ``ms_per_step`` is the
+whole step (application update, capture, drain) bracketed by a barrier and
+a synchronize.  Inputs (8 GiB) are larger than L2 (126 MB), so no flush is
+needed between steps.
+
+``--impl reference`` times the CPU oracle (test infrastructure, single
+thread) on a bounded sample of the same workload: the paper has no code to
+run, so the oracle is the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("checkpoint capture GB/s vs HBM peak; drain GB/s vs host link; "
+          "p50/p99 ckpt latency")
+UNIT = "GB/s"
+FALLBACK_HBM_GBS = 6400.0
+NOMINAL_LINK_GBS = 63.0  # PCIe Gen5 x16 per direction
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="uint32_8g")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-mib", type=int, default=512)
+    return ap.parse_args(argv)
+
+
+# ------------------------------------------------------------ distributed ---
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(world: int, backend: str):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, x: float, device=None) -> float:
+    """Largest value of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, x: float, device=None) -> float:
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- clocks ---
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while work runs."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, period_ms: int = 20):
+        self.gpu = gpu_index
+        self.period = period_ms
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="crum_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", f"-lms={self.period}"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def mark(self, which: str):
+        setattr(self, which, time.time())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        import datetime
+        rows, all_rows = [], []
+        t0, t1 = getattr(self, "t0", None), getattr(self, "t1", None)
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                try:
+                    ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    row = (float(parts[2]), float(parts[3]), parts[5:10])
+                except ValueError:
+                    continue
+                all_rows.append(row)
+                if t0 is None or (t0 - 0.05 <= ts <= (t1 or ts) + 0.05):
+                    rows.append(row)
+        os.unlink(self.path)
+        if not rows:
+            rows = all_rows
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for _, _, r in rows:
+            for n, v in zip(names, r[1:]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        busy = [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            mp = json.load(f)
+        return {"hbm_gbs": float(mp["hbm_gbs"]), "source": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "source": "fallback"}
+
+
+def traffic_from_profile(kernel: str, workload: str):
+    """DRAM bytes per launch recorded from ncu in profiles/, if the recorded
+    kernel source digest still matches the source being benchmarked."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    src = os.path.join(ROOT, "paper_1808_00117_b300", "csrc", "kernels.cu")
+    try:
+        text = open(path).read()
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernels_cu_sha256_16") != digest:
+        return None
+    try:
+        return int(vals["traffic_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+# --------------------------------------------------------------- CPU arm ---
+
+def oracle_sample_run(sample_mib: int, steps: int, warmup: int, wl):
+    """Time the CPU oracle's incremental checkpoint on a bounded sample of the
+    workload: the first `sample_mib` MiB, the same 5 % clustered mutation."""
+    import oracle
+    from paper_1808_00117_b300 import workloads as W
+    nbytes = sample_mib << 20
+    n_pages = W.pages_of(nbytes)
+    rng = np.random.default_rng(wl.seed)
+    data = rng.integers(0, 2**32, size=nbytes // 4, dtype=np.uint32).view(np.uint8)
+    o = oracle.OracleSet([nbytes])
+    o.checkpoint([data])
+    words = data.view(np.uint64).reshape(n_pages, -1)
+    times = []
+    for step in range(warmup + steps):
+        pages = W.choose_step(wl, 1000 + step, n_pages)
+        masks = (rng.integers(1, 2**62, size=(pages.size, 1), dtype=np.uint64) | np.uint64(1))
+        words[pages] ^= masks
+        t0 = time.perf_counter()
+        img, d, _, _ = o.checkpoint([data])
+        dt = time.perf_counter() - t0
+        assert int(d.sum()) == pages.size
+        if step >= warmup:
+            times.append(dt)
+    mean = statistics.mean(times)
+    return {"value": nbytes / mean / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sample_mib} MiB of the {wl.name} workload ({n_pages} pages, "
+                      f"{int(round(wl.dirty_frac * n_pages))} dirty per step), "
+                      f"{steps} incremental checkpoints, single-thread C oracle",
+            "ms_per_checkpoint": mean * 1e3}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1808_00117_b300 import workloads as W
+    wl = W.workload(args.workload)
+    t0 = time.perf_counter()
+    cb = oracle_sample_run(args.cpu_sample_mib, args.steps, args.warmup, wl)
+    wall = time.perf_counter() - t0
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(cb["value"], 4), "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(cb["ms_per_checkpoint"], 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": wl.name, "sample_bytes": args.cpu_sample_mib << 20,
+                   "parallelism": "single host thread"},
+        "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "e2e": {"value": round(cb["value"], 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "wall_s": round(wall, 2),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- GPU arm ---
+
+def pct(xs, q):
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if xs else None
+
+
+def link_d2h_peak(torch, nbytes=2 << 30):
+    """Pinned device->host copy bandwidth, measured with CUDA events."""
+    dev = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    for _ in range(2):
+        host.copy_(dev, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        host.copy_(dev, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    gbs = 3 * nbytes / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    del dev, host
+    return gbs
+
+
+def run_ours(args):
+    import torch
+    import paper_1808_00117_b300 as crum
+    from paper_1808_00117_b300 import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    crum.load()
+    dev = torch.device("cuda", local)
+    wl = W.workload(args.workload)
+    S = wl.total_bytes
+    n_pages = wl.n_pages
+    k_dirty = int(round(wl.dirty_frac * n_pages))
+    incr_image = 64 + 16 * len(wl.sizes) + 16 * k_dirty + 8 + k_dirty * W.PAGE
+    full_image = 64 + 16 * len(wl.sizes) + 16 * n_pages + 8 + n_pages * W.PAGE
+    steps, warmup = args.steps, max(args.warmup, 3)
+
+    link_peak = link_d2h_peak(torch)
+    bufs = []
+    for i, n in enumerate(wl.sizes):
+        b = torch.empty(n, dtype=torch.uint8, device=dev)
+        W.fill_(b, wl.seed * 7919 + i + 1000 * rank, wl.kind)
+        bufs.append(b)
+    torch.cuda.synchronize()
+    staging = 2 * ((n_pages + 1) * W.PAGE)  # two halves that each hold every page
+    pool = full_image + (warmup + steps + 2) * incr_image
+    s = crum.CheckpointSet(device=local, staging_bytes=staging, host_pool_bytes=pool)
+    for b in bufs:
+        s.register(b.data_ptr(), b.numel())
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    full = s.checkpoint(sh, crum.FULL)
+    full.wait()
+    chain = [full]
+    offsets = np.cumsum([0] + [W.pages_of(n) for n in wl.sizes])
+
+    def app_update(step):
+        pages = W.choose_step(wl, step, n_pages)
+        for i, b in enumerate(bufs):
+            lo, hi = offsets[i], offsets[i + 1]
+            local_pages = pages[(pages >= lo) & (pages < hi)] - lo
+            W.mutate_pages_(b, local_pages, wl.seed + 17 * step + i)
+
+    for step in range(warmup):
+        app_update(step + 1)
+        chain.append(s.checkpoint(sh))
+    for img in chain:
+        img.wait()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(dist)
+    torch.cuda.synchronize()
+    launches0 = crum.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.mark("t0")
+    e0.record(stream)
+    timed = []
+    for step in range(steps):
+        app_update(warmup + 1 + step)
+        timed.append(s.checkpoint(sh))
+    for img in timed:
+        img.wait(crum.WAIT_DRAINED)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks.mark("t1")
+    barrier(dist)
+    launches = crum.kernel_launches() - launches0
+    clk = clocks.stop()
+    for img in timed:
+        img.wait()
+    chain.extend(timed)
+    total_ms = max_over_ranks(dist, e0.elapsed_time(e1), dev)
+
+    infos = [img.info() for img in timed]
+    cap_ms = [i["t_hash_ms"] + i["t_compact_ms"] for i in infos]
+    hash_ms = [i["t_hash_ms"] for i in infos]
+    drain_ms = [i["t_drain_ms"] for i in infos]
+    drained_bytes = [i["image_bytes"] for i in infos]
+    mean_cap = max_over_ranks(dist, statistics.mean(cap_ms), dev)
+    mean_hash = max_over_ranks(dist, statistics.mean(hash_ms), dev)
+    value = world * S / (mean_cap * 1e-3) / 1e9
+    peaks = measured_peaks()
+    hash_bytes = S + 16 * n_pages  # read every page, read + write each committed hash
+    achieved = hash_bytes / (mean_hash * 1e-3) / 1e9
+    drain_gbs = statistics.mean(b / (t * 1e-3) / 1e9 for b, t in zip(drained_bytes, drain_ms))
+
+    # restore of the chain end (full image + every incremental) onto garbage
+    for b in bufs:
+        W.fill_(b, 4242, "u32")
+    torch.cuda.synchronize()
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    s.restore(chain[-1], sh)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    restore_ms = r0.elapsed_time(r1)
+    restore_bytes = sum(img.info()["n_dirty"] for img in chain) * W.PAGE
+
+    # plain form P0 (Section 3.4): synchronize, then copy every allocation whole
+    host_plain = torch.empty(S, dtype=torch.uint8, pin_memory=True)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    p0.record(stream)
+    off = 0
+    for b in bufs:
+        host_plain[off:off + b.numel()].copy_(b, non_blocking=True)
+        off += b.numel()
+    p1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = p0.elapsed_time(p1)
+    del host_plain
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(torch, crum, W, s, bufs, wl, steps, sh, stream, warmup + steps + 1, dist, dev, world)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cb = oracle_sample_run(args.cpu_sample_mib, 3, 1, wl)
+        cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+
+    traffic = traffic_from_profile("k_hash_dirty", wl.name)
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": warmup, "ms_per_step": round(total_ms / steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "footprint_bytes": S, "allocations": len(wl.sizes),
+                   "n_pages": n_pages, "dirty_pages_per_step": k_dirty,
+                   "staging_bytes": staging, "parallelism": f"replica per GPU x{world}",
+                   "l2": "inputs (8 GiB) larger than L2 (126 MB); no flush",
+                   "value_def": "footprint bytes / capture-kernel device time (hash+scan+gather)"},
+        "roofline": {"kernel": "k_hash_dirty", "bound": "hbm", "achieved": round(achieved, 1),
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
+                     "peak_source": peaks["source"], "bytes_per_launch": hash_bytes,
+                     "ms_per_launch": round(statistics.mean(hash_ms), 4)},
+        "capture": {"ms_mean": round(statistics.mean(cap_ms), 4),
+                    "hash_ms_mean": round(statistics.mean(hash_ms), 4),
+                    "frac_of_hbm": round(value / world / peaks["hbm_gbs"], 4)},
+        "drain": {"gbs": round(drain_gbs, 2), "link_measured_gbs": round(link_peak, 2),
+                  "frac_measured": round(drain_gbs / link_peak, 4),
+                  "link_nominal_gbs": NOMINAL_LINK_GBS,
+                  "frac_nominal": round(drain_gbs / NOMINAL_LINK_GBS, 4),
+                  "bytes_per_step": int(statistics.mean(drained_bytes))},
+        "latency_ms": {"captured_p50": pct([i["t_captured_ms"] for i in infos], 50),
+                       "captured_p99": pct([i["t_captured_ms"] for i in infos], 99),
+                       "drained_p50": pct([i["t_drained_ms"] for i in infos], 50),
+                       "drained_p99": pct([i["t_drained_ms"] for i in infos], 99),
+                       "persisted_p50": pct([i["t_persisted_ms"] for i in infos], 50),
+                       "persisted_p99": pct([i["t_persisted_ms"] for i in infos], 99),
+                       "n": len(infos)},
+        "restore": {"images": len(chain), "ms": round(restore_ms, 3),
+                    "payload_bytes": restore_bytes,
+                    "gbs": round(restore_bytes / (restore_ms * 1e-3) / 1e9, 2)},
+        "plain_p0": {"ms": round(plain_ms, 3), "gbs": round(S / (plain_ms * 1e-3) / 1e9, 2),
+                     "what": "synchronize + full device->host copy of the footprint"},
+        "clocks": clk,
+        "gpu_launches": int(launches),
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+    }
+    for img in chain:
+        img.release()
+    s.destroy()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_e2e(torch, crum, W, s, bufs, wl, steps, sh, stream, step0, dist, dev, world):
+    """Public API end to end: each step copies the application's new page
+    contents host->device from pinned memory, checkpoints, and waits until
+    the image is persisted in host memory (its bytes crossed device->host)."""
+    n_pages = wl.n_pages
+    k = int(round(wl.dirty_frac * n_pages))
+    gen = torch.Generator(device="cpu")
+    gen.manual_seed(wl.seed + 99)
+    new = torch.randint(0, 256, (k, W.PAGE), dtype=torch.uint8, generator=gen).pin_memory()
+    tmp = torch.empty((k, W.PAGE), dtype=torch.uint8, device=bufs[0].device)
+    view = bufs[0][: (bufs[0].numel() // W.PAGE) * W.PAGE].view(-1, W.PAGE)
+    imgs = []
+    h2d, d2h = [], []
+    for warm in range(2):
+        pages = torch.as_tensor(W.choose_step(wl, step0 + warm, n_pages), device=bufs[0].device)
+        pages = pages[pages < view.shape[0]]
+        tmp[: pages.numel()].copy_(new[: pages.numel()], non_blocking=True)
+        view[pages] = tmp[: pages.numel()]
+        im = s.checkpoint(sh)
+        im.wait()
+        imgs.append(im)
+    barrier(dist)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for step in range(steps):
+        pages_np = W.choose_step(wl, step0 + 2 + step, n_pages)
+        pages = torch.as_tensor(pages_np, device=bufs[0].device)
+        pages = pages[pages < view.shape[0]]
+        m = pages.numel()
+        tmp[:m].copy_(new[:m], non_blocking=True)
+        view[pages] = tmp[:m]
+        im = s.checkpoint(sh)
+        im.wait()
+        imgs.append(im)
+        h2d.append(m * W.PAGE)
+        d2h.append(im.info()["image_bytes"])
+    torch.cuda.synchronize()
+    dt = max_over_ranks(dist, time.perf_counter() - t0, dev)
+    for im in imgs:
+        im.release()
+    return {"value": round(world * wl.total_bytes * steps / dt / 1e9, 2), "unit": UNIT,
+            "h2d_bytes_per_step": int(statistics.mean(h2d)),
+            "d2h_bytes_per_step": int(statistics.mean(d2h)),
+            "ms_per_step": round(dt * 1e3 / steps, 3),
+            "what": "pinned H2D of the step's new pages + crum_checkpoint + wait PERSISTED"}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
