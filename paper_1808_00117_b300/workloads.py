@@ -9,7 +9,7 @@ Workload recipes (the paper's own applications and data are not used;
 synthetic data of the same shape stands in for them):
 
 * ``small16m``  one 16 MiB fp32 allocation, uniform in [-1, 1) (the synthetic
-  single-GPU benchmark's random-float vectors, Section 4.5, scaled down);
+  single-GPU benchmark's random-float vectors, Section 4.4, scaled down);
   10 % of pages rewritten, chosen uniformly without replacement.
 * ``uint32_8g`` one 8 GiB allocation of random 32-bit words; 5 % of pages
   (6,554) dirtied per step in clustered runs: run starts uniform, run
@@ -17,7 +17,7 @@ synthetic data of the same shape stands in for them):
   the union reaches the target, the last run trimmed to hit it exactly.
 * ``stencil``   200 fp64 fields with log-uniform sizes (4 KiB .. 512 MiB,
   rounded to 4 KiB, rescaled to a target total), the many-regions-of-uneven-
-  size shape of the HPGMG/HYPRE runs (Section 4.2-4.3).
+  size shape of the HPGMG/HYPRE runs (Section 4.2).
 * ``large``     4,096 allocations, log-uniform 64 KiB .. 2 GiB rescaled to a
   target total, fp32 or bf16 bit patterns, 2 % of pages per step.
 
