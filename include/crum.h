@@ -181,6 +181,10 @@ typedef struct crum_image_info {
     double t_captured_ms;    /* device time submit->captured (CUDA events) */
     double t_drained_ms;     /* device time submit->drained */
     double t_persisted_ms;   /* host time submit->persisted */
+    double t_hash_ms;        /* device time of the page-hash kernel */
+    double t_compact_ms;     /* device time of scan + gather into staging, from the
+                                moment the staging half was free */
+    double t_drain_ms;       /* device time of the device->host copies */
 } crum_image_info;
 
 /* Fill *info.  Fields past `stage` are zero until the image gets there. */
@@ -249,6 +253,7 @@ crum_status crum_poke_hash(crum_set *set, uint64_t global_page, uint64_t value);
 
 /* Kernel launches the library has issued since load (for launch accounting). */
 uint64_t crum_kernel_launches(void);
+
 
 #ifdef __cplusplus
 }

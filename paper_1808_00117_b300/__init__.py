@@ -50,7 +50,8 @@ class ImageInfo(ctypes.Structure):
                 ("collisions", ctypes.c_uint64), ("n_allocs", ctypes.c_uint32),
                 ("full", ctypes.c_uint32), ("stage", ctypes.c_int), ("status", ctypes.c_int),
                 ("t_captured_ms", ctypes.c_double), ("t_drained_ms", ctypes.c_double),
-                ("t_persisted_ms", ctypes.c_double)]
+                ("t_persisted_ms", ctypes.c_double), ("t_hash_ms", ctypes.c_double),
+                ("t_compact_ms", ctypes.c_double), ("t_drain_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -100,6 +100,8 @@ void image_unref(crum_image* img) {
     if (img->ev_submit) cudaEventDestroy(img->ev_submit);
     if (img->ev_captured) cudaEventDestroy(img->ev_captured);
     if (img->ev_drained) cudaEventDestroy(img->ev_drained);
+    for (cudaEvent_t ev : {img->ev_k0, img->ev_k1, img->ev_k2, img->ev_d0})
+      if (ev) cudaEventDestroy(ev);
     delete img;
     img = parent;
   }
@@ -201,6 +203,7 @@ crum_status upload_table(crum_set* s) {
 crum_status enqueue_drain(crum_set* s, crum_image* img, Half& H) {
   const uint64_t A = img->n_allocs, n = img->n_dirty;
   CK(cudaStreamWaitEvent(s->drain_stream, img->ev_captured, 0));
+  CK(cudaEventRecord(img->ev_d0, s->drain_stream));
   CK(cudaMemcpyAsync(img->host, H.meta, meta_bytes(A, n), cudaMemcpyDeviceToHost, s->drain_stream));
   if (n > 0 && !img->drop_payload)
     CK(cudaMemcpyAsync(img->host + meta_bytes(A, n), H.payload, n * kPage, cudaMemcpyDeviceToHost,
@@ -306,6 +309,11 @@ void writer_main(crum_set* s) {
         img->t_captured_ms = ms;
       if (cudaEventElapsedTime(&ms, img->ev_submit, img->ev_drained) == cudaSuccess)
         img->t_drained_ms = ms;
+      if (cudaEventElapsedTime(&ms, img->ev_k0, img->ev_k1) == cudaSuccess) img->t_hash_ms = ms;
+      if (cudaEventElapsedTime(&ms, img->ev_k2, img->ev_captured) == cudaSuccess)
+        img->t_compact_ms = ms;
+      if (cudaEventElapsedTime(&ms, img->ev_d0, img->ev_drained) == cudaSuccess)
+        img->t_drain_ms = ms;
       std::memcpy(&img->checksum, img->host + img->image_bytes - 8, 8);
       image_set_stage(img, CRUM_WAIT_DRAINED, img->collisions ? CRUM_ECOLLISION : CRUM_OK, "");
       if (img->drop_payload) {
@@ -333,9 +341,9 @@ void writer_main(crum_set* s) {
 }
 
 crum_status new_image_events(crum_image* img) {
-  CK(cudaEventCreate(&img->ev_submit));
-  CK(cudaEventCreate(&img->ev_captured));
-  CK(cudaEventCreate(&img->ev_drained));
+  for (cudaEvent_t* ev : {&img->ev_submit, &img->ev_captured, &img->ev_drained, &img->ev_k0,
+                          &img->ev_k1, &img->ev_k2, &img->ev_d0})
+    CK(cudaEventCreate(ev));
   return CRUM_OK;
 }
 
@@ -380,6 +388,7 @@ crum_status checkpoint_chunked(crum_set* s, crum_image* img, cudaStream_t app,
   CK(cudaEventRecord(img->ev_captured, s->cap_stream));
   CK(cudaStreamWaitEvent(app, img->ev_captured, 0));
   CK(cudaStreamWaitEvent(s->drain_stream, img->ev_captured, 0));
+  CK(cudaEventRecord(img->ev_d0, s->drain_stream));
   CK(cudaMemcpyAsync(img->host, H0.meta, meta_bytes(A, n), cudaMemcpyDeviceToHost, s->drain_stream));
   CK(cudaMemcpyAsync(img->host + img->image_bytes - 8, H0.scalars + 1, 8, cudaMemcpyDeviceToHost,
                      s->drain_stream));
@@ -686,11 +695,14 @@ crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, cr
   ha.full = full;
   ha.shadow = s->d_shadow;
   ha.collisions = s->d_collisions;
-  cudaError_t ce = crum::launch_hash_dirty(ha, s->map_hash, verify, s->cap_stream);
+  cudaError_t ce = cudaEventRecord(img->ev_k0, s->cap_stream);
+  if (ce == cudaSuccess) ce = crum::launch_hash_dirty(ha, s->map_hash, verify, s->cap_stream);
+  if (ce == cudaSuccess) ce = cudaEventRecord(img->ev_k1, s->cap_stream);
   if (ce != cudaSuccess) return bail(fail(CRUM_ECUDA, "hash launch: %s", cudaGetErrorString(ce)));
 
   // this half's previous drain must be done before its metadata is rewritten
-  if (cudaStreamWaitEvent(s->cap_stream, H.ev_drained, 0) != cudaSuccess)
+  if (cudaStreamWaitEvent(s->cap_stream, H.ev_drained, 0) != cudaSuccess ||
+      cudaEventRecord(img->ev_k2, s->cap_stream) != cudaSuccess)
     return bail(fail(CRUM_ECUDA, "stream wait failed"));
   crum::ScanArgs sa{};
   sa.mask = s->d_mask;
@@ -823,6 +835,9 @@ crum_status crum_image_info_get(const crum_image* cimg, crum_image_info* info) {
     info->collisions = img->collisions;
     info->t_captured_ms = img->t_captured_ms;
     info->t_drained_ms = img->t_drained_ms;
+    info->t_hash_ms = img->t_hash_ms;
+    info->t_compact_ms = img->t_compact_ms;
+    info->t_drain_ms = img->t_drain_ms;
   }
   if (img->stage >= CRUM_WAIT_PERSISTED) info->t_persisted_ms = img->t_persisted_ms;
   return CRUM_OK;

@@ -95,8 +95,12 @@ struct crum_image {
   crum_status status = CRUM_OK;
   std::string err;
   cudaEvent_t ev_submit = nullptr, ev_captured = nullptr, ev_drained = nullptr;
+  // phase timing: hash kernel [ev_k0, ev_k1], compaction [ev_k2, ev_captured]
+  // (ev_k2 is taken once the staging half is free), drain [ev_d0, ev_drained]
+  cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr, ev_k2 = nullptr, ev_d0 = nullptr;
   std::chrono::steady_clock::time_point t_submit;
   double t_captured_ms = 0, t_drained_ms = 0, t_persisted_ms = 0;
+  double t_hash_ms = 0, t_compact_ms = 0, t_drain_ms = 0;
   int half = 0;
   bool drop_payload = false;  // null sink
   std::string sink_path;
