@@ -254,6 +254,34 @@ crum_status crum_poke_hash(crum_set *set, uint64_t global_page, uint64_t value);
 /* Kernel launches the library has issued since load (for launch accounting). */
 uint64_t crum_kernel_launches(void);
 
+/* ---- allocation-free dirty-page detection (the paper has no counterpart;
+        this exists for callers that cannot allocate device memory) ---- */
+
+#define CRUM_STATIC_MAX_PAGES 4194304u /* 256 GiB of 64 KiB pages */
+
+/* Which pages of one allocation changed, without allocating any memory.
+   For callers that cannot call cudaMalloc when they need the answer: an
+   out-of-memory handler that wants a last checkpoint before freeing
+   anything (where cudaMalloc is what fails), or an allocator hook or
+   CUDA-call interposer in which a nested cudaMalloc would re-enter the
+   allocator being served.
+   ptr/bytes: the allocation (16-byte aligned device pointer, bytes > 0,
+   at most CRUM_STATIC_MAX_PAGES pages, else EINVAL).  hashes: device array
+   of ceil(bytes/65536) u64 holding the previous page hashes; overwritten
+   with the current ones.  full != 0 lists every page.  pages_out: device
+   array with room for ceil(bytes/65536) u32; receives the changed page
+   indices in ascending order.  count_out: device u64, receives their number.
+   Stream ordered on `stream`; returns once the work is queued.
+   Scratch: a 512 KiB dirty bitmap in a fixed device array inside the
+   library, which every GPU that loads the library keeps until exit.  The
+   first call on a device looks up that array's address with the device
+   current; make that first call before any stream capture and before
+   memory runs short.  All calls on a device share the bitmap, so calls
+   that overlap on the GPU (unordered streams) race; each call clears what
+   it uses first.  Errors: EINVAL, ECUDA. */
+crum_status crum_dirty_pages_static(const void *ptr, uint64_t bytes, uint64_t *hashes, int full,
+                                    uint32_t *pages_out, uint64_t *count_out,
+                                    crum_stream_t stream);
 
 #ifdef __cplusplus
 }

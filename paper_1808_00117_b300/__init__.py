@@ -82,6 +82,7 @@ SIGNATURES = {
     "crum_get_hashes": ([_VP, _VP, _U64], _I),
     "crum_poke_hash": ([_VP, _U64, _U64], _I),
     "crum_kernel_launches": ([], _U64),
+    "crum_dirty_pages_static": ([_VP, _U64, _VP, _I, _VP, _VP, _VP], _I),
 }
 
 _lib = None
@@ -140,6 +141,14 @@ def hash_pages(ptr: int, nbytes: int, out_ptr: int, stream: int = 0) -> None:
 
 def hash_bytes(ptr: int, nbytes: int, first_index: int, out_ptr: int, stream: int = 0) -> None:
     _check(load().crum_hash_bytes(ptr, nbytes, first_index, out_ptr, stream), "crum_hash_bytes")
+
+
+def dirty_pages_static(ptr: int, nbytes: int, hashes_ptr: int, full: bool, pages_out_ptr: int,
+                       count_out_ptr: int, stream: int = 0) -> None:
+    """Changed pages of one allocation with no memory allocated by the
+    library (its scratch is a fixed device array; see include/crum.h)."""
+    _check(load().crum_dirty_pages_static(ptr, nbytes, hashes_ptr, int(bool(full)), pages_out_ptr,
+                                          count_out_ptr, stream), "crum_dirty_pages_static")
 
 
 class Image:

@@ -1154,3 +1154,9 @@ crum_status crum_poke_hash(crum_set* s, uint64_t g, uint64_t value) {
 }
 
 }  // extern "C"
+
+namespace crum {
+// Lets other translation units of the library report a message through
+// crum_last_error().
+void set_last_error(const char* msg) { t_err = msg; }
+}  // namespace crum
