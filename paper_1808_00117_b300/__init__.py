@@ -40,7 +40,8 @@ class Config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("staging_bytes", ctypes.c_uint64),
                 ("chunk_bytes", ctypes.c_uint64), ("host_pool_bytes", ctypes.c_uint64),
                 ("sink", ctypes.c_int), ("sink_dir", ctypes.c_char_p),
-                ("verify", ctypes.c_int), ("fsync", ctypes.c_int)]
+                ("verify", ctypes.c_int), ("fsync", ctypes.c_int),
+                ("hash_mapping", ctypes.c_int), ("gather_mapping", ctypes.c_int)]
 
 
 class ImageInfo(ctypes.Structure):
@@ -68,6 +69,8 @@ SIGNATURES = {
     "crum_register": ([_VP, _VP, ctypes.c_size_t, ctypes.POINTER(_U32)], _I),
     "crum_unregister": ([_VP, _U32], _I),
     "crum_set_info": ([_VP, ctypes.POINTER(_U32), ctypes.POINTER(_U64)], _I),
+    "crum_autotune": ([_VP, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double),
+                       ctypes.POINTER(ctypes.c_double)], _I),
     "crum_checkpoint": ([_VP, _VP, _I, ctypes.POINTER(_VP)], _I),
     "crum_image_wait": ([_VP, _I, _I64], _I),
     "crum_image_info_get": ([_VP, ctypes.POINTER(ImageInfo)], _I),
@@ -214,6 +217,15 @@ class CheckpointSet:
         a, p = _U32(), _U64()
         _check(load().crum_set_info(self.handle, ctypes.byref(a), ctypes.byref(p)), "crum_set_info")
         return a.value, p.value
+
+    def autotune(self) -> dict:
+        """Pick the fastest hash and gather mappings for the registrations."""
+        hm, gm = _I(), _I()
+        ht, gt = (ctypes.c_double * 9)(), (ctypes.c_double * 6)()
+        _check(load().crum_autotune(self.handle, ctypes.byref(hm), ctypes.byref(gm), ht, gt),
+               "crum_autotune")
+        return {"hash_mapping": hm.value, "gather_mapping": gm.value,
+                "hash_ms": list(ht), "gather_ms": list(gt)}
 
     def checkpoint(self, stream: int = 0, flags: int = INCR) -> Image:
         h = _VP()

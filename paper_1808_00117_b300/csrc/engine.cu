@@ -242,7 +242,9 @@ void planner_main(crum_set* s) {
     if (st == CRUM_OK) {
       img->n_dirty = reinterpret_cast<volatile uint64_t*>(H.mailbox)[0];
       img->collisions = reinterpret_cast<volatile uint64_t*>(H.mailbox)[1];
-      st = alloc_image_host(s, img);
+      if (reinterpret_cast<volatile uint64_t*>(H.mailbox)[2] != 0)
+        st = fail(CRUM_ETIMEOUT, "hash kernel: a bounded device wait ran out");
+      if (st == CRUM_OK) st = alloc_image_host(s, img);
       if (st == CRUM_OK) st = enqueue_drain(s, img, H);
       if (st != CRUM_OK) err = t_err;
     }
@@ -474,6 +476,8 @@ void crum_config_default(crum_config* cfg) {
   cfg->staging_bytes = kDefaultStaging;
   cfg->chunk_bytes = kDefaultChunk;
   cfg->sink = CRUM_SINK_MEMORY;
+  cfg->hash_mapping = -1;
+  cfg->gather_mapping = -1;
 }
 
 const char* crum_last_error(void) { return t_err.c_str(); }
@@ -496,6 +500,9 @@ crum_status crum_set_create(const crum_config* cfg_in, crum_set** out) {
   if (cfg.sink < CRUM_SINK_MEMORY || cfg.sink > CRUM_SINK_NULL) return fail(CRUM_EINVAL, "bad sink");
   if (cfg.sink == CRUM_SINK_FILE && (cfg.sink_dir == nullptr || cfg.sink_dir[0] == 0))
     return fail(CRUM_EINVAL, "file sink needs sink_dir");
+  if (cfg.hash_mapping < -1 || cfg.hash_mapping >= crum::kNumMappings ||
+      cfg.gather_mapping < -1 || cfg.gather_mapping > 5)
+    return fail(CRUM_EINVAL, "mapping out of range");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg.device < 0 || cfg.device >= ndev) {
     cudaGetLastError();
@@ -509,6 +516,8 @@ crum_status crum_set_create(const crum_config* cfg_in, crum_set** out) {
   s->device = cfg.device;
   s->set_id = g_set_ids.fetch_add(1);
   s->half_slots = cfg.staging_bytes / 2 / kPage;
+  if (cfg.hash_mapping >= 0) s->map_hash = cfg.hash_mapping;
+  if (cfg.gather_mapping >= 0) s->map_gather = cfg.gather_mapping;
   s->pool = std::make_shared<crum::PinnedPool>(cfg.host_pool_bytes);
   if (cfg.host_pool_bytes) {
     uint8_t* p = s->pool->alloc(cfg.host_pool_bytes);
@@ -519,7 +528,7 @@ crum_status crum_set_create(const crum_config* cfg_in, crum_set** out) {
   CK(cudaStreamCreateWithFlags(&s->drain_stream, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&s->ev_app, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&s->ev_done, cudaEventDisableTiming));
-  CK(cudaMalloc(&s->d_collisions, sizeof(unsigned long long)));
+  CK(cudaMalloc(&s->d_collisions, 2 * sizeof(unsigned long long)));  // [0] collisions, [1] error
   for (Half& H : s->half) {
     if (cudaMalloc(&H.payload, s->half_slots * kPage) != cudaSuccess) {
       cudaGetLastError();
@@ -527,7 +536,7 @@ crum_status crum_set_create(const crum_config* cfg_in, crum_set** out) {
                   (unsigned long long)(s->half_slots * kPage));
     }
     CK(cudaMalloc(&H.scalars, 2 * sizeof(uint64_t)));
-    CK(cudaHostAlloc(reinterpret_cast<void**>(&H.mailbox), 2 * sizeof(uint64_t), cudaHostAllocMapped));
+    CK(cudaHostAlloc(reinterpret_cast<void**>(&H.mailbox), 4 * sizeof(uint64_t), cudaHostAllocMapped));
     CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&H.mailbox_dev), H.mailbox, 0));
     CK(cudaEventCreateWithFlags(&H.ev_scanned, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&H.ev_drained, cudaEventDisableTiming));
@@ -624,6 +633,134 @@ crum_status crum_set_info(const crum_set* s, uint32_t* n_allocs, uint64_t* n_pag
   return CRUM_OK;
 }
 
+crum_status crum_autotune(crum_set* s, int* hash_mapping, int* gather_mapping, double* hash_ms,
+                          double* gather_ms) {
+  t_err.clear();
+  if (s == nullptr) return fail(CRUM_EINVAL, "null set");
+  DeviceGuard dg(s->device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  if (s->allocs.empty()) return fail(CRUM_EINVAL, "no registered allocations");
+  crum_status st = ensure_capacity(s, lk);
+  if (st == CRUM_OK) st = quiesce(s, lk);
+  if (st != CRUM_OK) return st;
+  if ((st = upload_table(s)) != CRUM_OK) return st;
+  const uint64_t n = s->n_pages;
+  const uint64_t words = (n + 31) / 32;
+  constexpr int kReps = 3;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  uint64_t* d_out = nullptr;
+  CK(cudaMalloc(&d_out, n * sizeof(uint64_t)));
+  std::vector<uint64_t> ref(n), got(n);
+  double best = 1e30;
+  int best_h = s->map_hash;
+  crum::HashArgs ha{};
+  ha.allocs = s->d_allocs;
+  ha.first_page = s->d_first_page;
+  ha.n_allocs = static_cast<uint32_t>(s->allocs.size());
+  ha.n_pages = n;
+  ha.h_out = d_out;
+  auto cleanup = [&]() {
+    cudaFree(d_out);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  };
+  for (int m = 0; m < crum::kNumMappings && st == CRUM_OK; ++m) {
+    cudaError_t ce = crum::launch_hash_dirty(ha, m, false, s->cap_stream);  // warm-up
+    if (ce == cudaSuccess) ce = cudaEventRecord(e0, s->cap_stream);
+    for (int r = 0; r < kReps && ce == cudaSuccess; ++r)
+      ce = crum::launch_hash_dirty(ha, m, false, s->cap_stream);
+    if (ce == cudaSuccess) ce = cudaEventRecord(e1, s->cap_stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->cap_stream);
+    float ms = 0;
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpy(m == 0 ? ref.data() : got.data(), d_out, n * 8, cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) {
+      st = fail(CRUM_ECUDA, "autotune hash mapping %d: %s", m, cudaGetErrorString(ce));
+      break;
+    }
+    if (m > 0 && got != ref) {
+      st = fail(CRUM_ECORRUPT, "hash mapping %d disagrees with mapping 0", m);
+      break;
+    }
+    const double mean = ms / kReps;
+    if (hash_ms) hash_ms[m] = mean;
+    if (mean < best) {
+      best = mean;
+      best_h = m;
+    }
+  }
+  // gather: a synthetic dirty set (bit 0 of every bitmap byte, 1 page in 8)
+  // scanned into staging half 0, then each mapping gathers it
+  int best_g = s->map_gather;
+  Half& H = s->half[0];
+  const uint64_t slots = std::min<uint64_t>((n + 7) / 8, s->half_slots);
+  if (st == CRUM_OK && slots == (n + 7) / 8) {
+    cudaError_t ce = cudaMemsetAsync(s->d_mask, 0x01, words * sizeof(uint32_t), s->cap_stream);
+    crum::ScanArgs sa{};
+    sa.mask = s->d_mask;
+    sa.n_words = words;
+    sa.word_offset = s->d_word_offset;
+    sa.n_dirty_out = H.scalars;
+    sa.allocs = s->d_allocs;
+    sa.n_allocs = ha.n_allocs;
+    sa.meta = H.meta;
+    sa.trailer = H.scalars + 1;
+    sa.parent_seq = CRUM_NO_PARENT;
+    // bits past the last page may be set by the pattern: clear that word's tail
+    if (ce == cudaSuccess && (n & 31) != 0) {
+      const uint32_t last = 0x01010101u & ((1u << (n & 31)) - 1u);
+      ce = cudaMemcpyAsync(s->d_mask + words - 1, &last, 4, cudaMemcpyHostToDevice, s->cap_stream);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->cap_stream);
+    }
+    if (ce == cudaSuccess) ce = crum::launch_scan(sa, s->cap_stream);
+    crum::GatherArgs ga{};
+    ga.allocs = s->d_allocs;
+    ga.first_page = s->d_first_page;
+    ga.n_allocs = ha.n_allocs;
+    ga.mask = s->d_mask;
+    ga.word_offset = s->d_word_offset;
+    ga.n_words = words;
+    ga.n_pages = n;
+    ga.n_dirty = H.scalars;
+    ga.h_table = s->d_h;
+    ga.meta = H.meta;
+    ga.payload = H.payload;
+    ga.trailer = H.scalars + 1;
+    ga.s_begin = 0;
+    ga.s_end = slots;
+    best = 1e30;
+    for (int m = 0; m <= 5 && ce == cudaSuccess; ++m) {
+      ce = crum::launch_gather(ga, slots, m, false, s->cap_stream);
+      if (ce == cudaSuccess) ce = cudaEventRecord(e0, s->cap_stream);
+      for (int r = 0; r < kReps && ce == cudaSuccess; ++r)
+        ce = crum::launch_gather(ga, slots, m, false, s->cap_stream);
+      if (ce == cudaSuccess) ce = cudaEventRecord(e1, s->cap_stream);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->cap_stream);
+      float ms = 0;
+      if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+      if (ce != cudaSuccess) break;
+      const double mean = ms / kReps;
+      if (gather_ms) gather_ms[m] = mean;
+      if (mean < best) {
+        best = mean;
+        best_g = m;
+      }
+    }
+    if (ce == cudaSuccess) ce = cudaEventRecord(H.ev_drained, s->cap_stream);
+    if (ce != cudaSuccess) st = fail(CRUM_ECUDA, "autotune gather: %s", cudaGetErrorString(ce));
+  }
+  cleanup();
+  if (st != CRUM_OK) return st;
+  s->map_hash = best_h;
+  s->map_gather = best_g;
+  if (hash_mapping) *hash_mapping = best_h;
+  if (gather_mapping) *gather_mapping = best_g;
+  return CRUM_OK;
+}
+
 crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, crum_image** out) {
   t_err.clear();
   if (s == nullptr || out == nullptr) return fail(CRUM_EINVAL, "null set or out");
@@ -682,7 +819,7 @@ crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, cr
   if ((st = upload_table(s)) != CRUM_OK) return bail(st);
   const uint64_t words = (s->n_pages + 31) / 32;
   if (cudaMemsetAsync(s->d_mask, 0, words * sizeof(uint32_t), s->cap_stream) != cudaSuccess ||
-      (verify && cudaMemsetAsync(s->d_collisions, 0, sizeof(unsigned long long), s->cap_stream) != cudaSuccess))
+      cudaMemsetAsync(s->d_collisions, 0, 2 * sizeof(unsigned long long), s->cap_stream) != cudaSuccess)
     return bail(fail(CRUM_ECUDA, "memset failed: %s", cudaGetErrorString(cudaGetLastError())));
 
   crum::HashArgs ha{};
@@ -695,6 +832,7 @@ crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, cr
   ha.full = full;
   ha.shadow = s->d_shadow;
   ha.collisions = s->d_collisions;
+  ha.error = reinterpret_cast<unsigned int*>(s->d_collisions + 1);
   cudaError_t ce = cudaEventRecord(img->ev_k0, s->cap_stream);
   if (ce == cudaSuccess) ce = crum::launch_hash_dirty(ha, s->map_hash, verify, s->cap_stream);
   if (ce == cudaSuccess) ce = cudaEventRecord(img->ev_k1, s->cap_stream);
@@ -711,6 +849,7 @@ crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, cr
   sa.n_dirty_out = H.scalars;
   sa.mailbox = H.mailbox_dev;
   sa.collisions = verify ? s->d_collisions : nullptr;
+  sa.error = reinterpret_cast<const unsigned int*>(s->d_collisions + 1);
   sa.allocs = s->d_allocs;
   sa.n_allocs = img->n_allocs;
   sa.meta = H.meta;

@@ -136,7 +136,7 @@ struct crum_set {
   uint64_t half_slots = 0;
   cudaStream_t cap_stream = nullptr, drain_stream = nullptr;
   cudaEvent_t ev_app = nullptr, ev_done = nullptr;
-  int map_hash = 1, map_gather = 1;
+  int map_hash = 1, map_gather = 4;  // defaults until crum_autotune or the config
   // chain state
   uint64_t seq = 0;
   crum_image* last = nullptr;

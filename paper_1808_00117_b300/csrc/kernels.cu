@@ -224,6 +224,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(ScanArgs a) {
     if (a.mailbox != nullptr) {
       a.mailbox[0] = run;
       a.mailbox[1] = a.collisions != nullptr ? *a.collisions : 0ull;
+      a.mailbox[2] = a.error != nullptr ? *a.error : 0u;
       __threadfence_system();
     }
   }
@@ -393,6 +394,203 @@ __global__ void __launch_bounds__(256) k_hash_bytes(const uint8_t* p, uint64_t n
   if ((threadIdx.x & 31) == 0 && h != 0) atomicAdd(out, static_cast<unsigned long long>(h));
 }
 
+// ------------------------------------------------- bulk-copy page hashing ---
+//
+// Warp-specialised variant of k_hash_dirty for sm_90+ bulk copies: lane 0 of
+// warp 0 streams every full page of the CTA's share, as four 16 KiB
+// quarters, into a ring of STAGES shared-memory buffers with
+// cp.async.bulk (completion counted on a "full" mbarrier per buffer); CW
+// consumer warps hash each buffer from shared memory and release it on an
+// "empty" mbarrier.  Bytes in flight per CTA = STAGES * 16 KiB, independent
+// of register allocation.  Tail pages (valid < 64 KiB) are hashed by the
+// consumers straight from global memory.  Every wait is bounded; a wait that
+// runs out sets *error and `stop`: the producer stops issuing and waits
+// (bounded) for its copies in flight, consumers stop waiting and hashing but
+// keep meeting at their per-page barrier, so every thread still exits.
+
+constexpr uint32_t kQuarter = kPage / 4;
+constexpr uint32_t kWaitLimit = 1u << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// true once the barrier's phase with this parity has completed; false if the
+// bounded number of polls ran out or *stop became nonzero.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          const volatile int* stop) {
+  const uint32_t addr = smem_u32(bar);
+  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((i & 1023u) == 1023u && stop != nullptr && *stop) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void bulk_load(void* dst_smem, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst_smem)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void consumer_sync(int threads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(threads) : "memory");
+}
+
+template <int STAGES, int CW>
+__global__ void __launch_bounds__(32 * (CW + 1)) k_hash_dirty_bulk(HashArgs a) {
+  extern __shared__ __align__(128) uint8_t ring[];
+  __shared__ __align__(8) uint64_t full_bar[STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ uint64_t red[CW];
+  __shared__ int stop;
+  constexpr int kConsumers = 32 * CW;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], CW);
+    }
+    stop = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (warp == 0) {
+    // ---- producer ----
+    if (lane != 0) return;
+    uint32_t chunk = 0, issued = 0;
+    bool ok = true;
+    for (uint64_t g = blockIdx.x; ok && g < a.n_pages; g += gridDim.x) {
+      const uint8_t* base;
+      uint64_t bytes, first;
+      if (a.allocs != nullptr) {
+        const uint32_t k = dev::find_alloc(a.first_page, a.n_allocs, g);
+        base = a.allocs[k].base;
+        bytes = a.allocs[k].bytes;
+        first = a.allocs[k].first_page;
+      } else {
+        base = a.one.base;
+        bytes = a.one.bytes;
+        first = 0;
+      }
+      const uint64_t p = g - first;
+      if (dev::valid_bytes(bytes, p) != kPage) continue;
+      const uint8_t* src = base + p * kPage;
+      for (uint32_t q = 0; q < 4; ++q, ++chunk) {
+        const uint32_t s = chunk % STAGES, k = chunk / STAGES;
+        if (k > 0 && !mbar_wait(&empty_bar[s], (k - 1) & 1, &stop)) {
+          ok = false;
+          break;
+        }
+        mbar_arrive_expect_tx(&full_bar[s], kQuarter);
+        bulk_load(ring + s * kQuarter, src + q * kQuarter, kQuarter, &full_bar[s]);
+        ++issued;
+      }
+    }
+    if (!ok) {
+      if (a.error) atomicExch(a.error, 1u);
+      stop = 1;
+      // let the copies already issued land before the CTA can retire
+      for (uint32_t c = (issued > STAGES ? issued - STAGES : 0); c < issued; ++c)
+        mbar_wait(&full_bar[c % STAGES], (c / STAGES) & 1, nullptr);
+    }
+    return;
+  }
+
+  // ---- consumers ----
+  const int ct = threadIdx.x - 32, cw = warp - 1;
+  uint32_t chunk = 0;
+  bool bad = false;
+  const uint64_t c_base = static_cast<uint64_t>(2 * ct) * kPhi;
+  constexpr uint64_t kStepU = static_cast<uint64_t>(2 * kConsumers) * kPhi;
+  constexpr uint64_t kStepQ = static_cast<uint64_t>(2 * (kQuarter / 16)) * kPhi;
+  for (uint64_t g = blockIdx.x; g < a.n_pages; g += gridDim.x) {
+    const uint8_t* base;
+    uint64_t bytes, first;
+    if (a.allocs != nullptr) {
+      const uint32_t k = dev::find_alloc(a.first_page, a.n_allocs, g);
+      base = a.allocs[k].base;
+      bytes = a.allocs[k].bytes;
+      first = a.allocs[k].first_page;
+    } else {
+      base = a.one.base;
+      bytes = a.one.bytes;
+      first = 0;
+    }
+    const uint64_t p = g - first;
+    const uint32_t valid = dev::valid_bytes(bytes, p);
+    uint64_t h = 0;
+    if (valid == kPage) {
+      for (uint32_t q = 0; q < 4; ++q, ++chunk) {
+        const uint32_t s = chunk % STAGES, k = chunk / STAGES;
+        if (bad || !mbar_wait(&full_bar[s], k & 1, &stop)) {
+          bad = true;
+          stop = 1;  // the producer stops issuing at its next poll
+          continue;
+        }
+        const uint4* buf = reinterpret_cast<const uint4*>(ring + s * kQuarter);
+        uint64_t c = c_base + q * kStepQ;
+#pragma unroll
+        for (int u = 0; u < static_cast<int>(kQuarter / 16) / kConsumers; ++u) {
+          h += hash_vec(buf[ct + u * kConsumers], c);
+          c += kStepU;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty_bar[s]);
+      }
+    } else if (!bad) {
+      h = hash_tail_page<kConsumers>(base + p * kPage, valid, ct);
+    }
+    h = dev::warp_sum(h);
+    consumer_sync(kConsumers);
+    if (lane == 0) red[cw] = h;
+    consumer_sync(kConsumers);
+    if (ct == 0 && !bad) {
+      uint64_t total = 0;
+#pragma unroll
+      for (int w = 0; w < CW; ++w) total += red[w];
+      if (a.h_out != nullptr) {
+        a.h_out[g] = total;
+      } else {
+        const bool d = a.full || total != a.h_table[g];
+        a.h_table[g] = total;
+        if (d) atomicOr(a.dirty_mask + (g >> 5), 1u << (g & 31));
+      }
+    }
+  }
+  if (bad) {
+    stop = 1;
+    if (a.error) atomicExch(a.error, 1u);
+  }
+}
+
 int g_num_sms = 0;
 
 int num_sms() {
@@ -441,13 +639,40 @@ cudaError_t launch_gather_t(const GatherArgs& a, uint64_t max_slots, cudaStream_
 
 }  // namespace
 
+namespace {
+
+template <int STAGES, int CW>
+cudaError_t launch_hash_bulk_t(const HashArgs& a, cudaStream_t st) {
+  auto kern = k_hash_dirty_bulk<STAGES, CW>;
+  constexpr int kThreads = 32 * (CW + 1);
+  constexpr int kSmem = STAGES * static_cast<int>(kQuarter);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, kSmem);
+  if (e != cudaSuccess) return e;
+  const uint64_t cap = static_cast<uint64_t>(std::max(1, per_sm)) * num_sms();
+  const unsigned grid = static_cast<unsigned>(std::max<uint64_t>(1, std::min(a.n_pages, cap)));
+  kern<<<grid, kThreads, kSmem, st>>>(a);
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Hash mappings 0-5 are register mappings, 6-8 bulk-copy mappings; gather
+// and restore use the register mappings 0-5 only.
 const Mapping kMappings[] = {
-    {32, 4}, {32, 8}, {32, 16}, {256, 2}, {256, 4}, {256, 8},
+    {32, 4, 0},  {32, 8, 0},  {32, 16, 0},  {256, 2, 0}, {256, 4, 0},
+    {256, 8, 0}, {256, 0, 4}, {256, 0, 6},  {512, 0, 4},
 };
 const int kNumMappings = sizeof(kMappings) / sizeof(kMappings[0]);
 
 cudaError_t launch_hash_dirty(const HashArgs& a, int mapping, bool verify, cudaStream_t st) {
   if (a.n_pages == 0) return cudaSuccess;
+  // verify mode compares pages against the shadow copy, which only the
+  // register mappings do; bulk-copy mappings fall back to mapping 1 there
+  if (verify && mapping >= 6) mapping = 1;
 #define CRUM_HASH_CASE(i, G, U)                                               \
   case i:                                                                     \
     return verify ? launch_hash_t<G, U, true>(a, st) : launch_hash_t<G, U, false>(a, st);
@@ -458,6 +683,12 @@ cudaError_t launch_hash_dirty(const HashArgs& a, int mapping, bool verify, cudaS
     CRUM_HASH_CASE(3, 256, 2)
     CRUM_HASH_CASE(4, 256, 4)
     CRUM_HASH_CASE(5, 256, 8)
+    case 6:
+      return launch_hash_bulk_t<4, 8>(a, st);
+    case 7:
+      return launch_hash_bulk_t<6, 8>(a, st);
+    case 8:
+      return launch_hash_bulk_t<4, 16>(a, st);
     default:
       return cudaErrorInvalidValue;
   }

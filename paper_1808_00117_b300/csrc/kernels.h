@@ -11,12 +11,16 @@ namespace crum {
 
 extern std::atomic<uint64_t> g_kernel_launches;
 
-// Thread mapping of the page kernels: G threads per page (32: one warp per
-// page, several pages per CTA; 256: one CTA per page) and U 16-byte loads
-// in flight per thread.  Chosen per set by the autotuner.
+// Thread mapping of the page kernels.  Register mappings: G threads per page
+// (32: one warp per page, several pages per CTA; 256: one CTA per page) and
+// U 16-byte loads in flight per thread.  Bulk-copy mappings (hash only):
+// one producer thread streams 16 KiB quarter-pages into a ring of `stages`
+// shared-memory buffers with cp.async.bulk, `group` consumer threads hash
+// them.  Chosen per set by the autotuner.
 struct Mapping {
   int group;
   int unroll;
+  int stages;  // 0: register mapping
 };
 extern const Mapping kMappings[];
 extern const int kNumMappings;
@@ -33,6 +37,7 @@ struct HashArgs {
   int full;               // every page dirty
   const uint8_t* shadow;  // verify mode: last checkpointed bytes, page g at g*64 KiB
   unsigned long long* collisions;
+  unsigned int* error;    // bulk-copy mappings: set to 1 if a bounded wait ran out (optional)
 };
 
 struct ScanArgs {
@@ -40,8 +45,10 @@ struct ScanArgs {
   uint64_t n_words;          // ceil(n_pages / 32)
   uint32_t* word_offset;     // n_words + 1: dirty pages before each word; last = total
   uint64_t* n_dirty_out;     // device
-  volatile uint64_t* mailbox;  // mapped pinned host: [0] dirty count, [1] collisions (optional)
+  volatile uint64_t* mailbox;  // mapped pinned host: [0] dirty count, [1] collisions,
+                               // [2] hash timeout flag (optional)
   const unsigned long long* collisions;  // verify-mode collision counter (optional)
+  const unsigned int* error;             // hash-kernel wait-timeout flag (optional)
   const DevAlloc* allocs;
   uint32_t n_allocs;
   uint8_t* meta;             // header + allocation table + page table + hashes

@@ -150,24 +150,30 @@ def fill_(buf, seed: int, kind: str) -> None:
         buf[n8:] = torch.randint(0, 256, (n - n8,), dtype=torch.uint8, device=buf.device, generator=g)
 
 
-def mutate_pages_(buf, pages, seed: int) -> None:
+def mutate_pages_(buf, pages, seed: int, has_tail=None) -> None:
     """xor every word of each listed page (page indices within `buf`) with a
-    per-page nonzero 64-bit mask; a partial last page gets a nonzero byte mask."""
+    per-page nonzero 64-bit mask; a partial last page gets a nonzero byte mask.
+
+    `pages` is a host sequence, or a device tensor of whole-page indices with
+    `has_tail` saying whether the partial last page is also chosen (this form
+    never waits for the device)."""
     torch = _torch()
-    pages = torch.as_tensor(np.asarray(pages, dtype=np.int64), device=buf.device)
-    if pages.numel() == 0:
-        return
-    g = torch.Generator(device=buf.device)
-    g.manual_seed(seed)
     n = buf.numel()
     n_full = n // PAGE
-    full = pages[pages < n_full]
+    if isinstance(pages, torch.Tensor):
+        full = pages.to(device=buf.device, dtype=torch.int64)
+        tail = bool(has_tail) and n > n_full * PAGE
+    else:
+        p = np.asarray(pages, dtype=np.int64)
+        tail = bool((p == n_full).any()) and n > n_full * PAGE
+        full = torch.as_tensor(p[p < n_full], device=buf.device)
+    g = torch.Generator(device=buf.device)
+    g.manual_seed(seed)
     if full.numel():
         v = buf[: n_full * PAGE].view(torch.int64).view(n_full, PAGE // 8)
         masks = torch.randint(1, 2**62, (full.numel(), 1), dtype=torch.int64, device=buf.device,
                               generator=g) | 1
         v[full] = v[full] ^ masks
-    if (pages == n_full).any() and n > n_full * PAGE:
-        tail = buf[n_full * PAGE:]
+    if tail:
         m = torch.randint(1, 256, (1,), dtype=torch.int64, device=buf.device, generator=g).to(torch.uint8)
-        tail.bitwise_xor_(m)
+        buf[n_full * PAGE:].bitwise_xor_(m)

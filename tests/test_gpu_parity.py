@@ -316,3 +316,41 @@ def test_kernels_are_launched():
     s.checkpoint(stream_handle()).wait()
     assert crum.kernel_launches() - before == 3  # hash, scan, gather
     s.destroy()
+
+
+@pytest.mark.parametrize("hm", range(9))
+def test_every_mapping_is_bit_exact(hm):
+    """Every autotuner candidate (hash mappings 0-8, gather mappings 0-5)
+    gives the oracle's images bit for bit, over ragged allocations."""
+    gm = hm % 6
+    sizes = RAGGED + [9 * P, 2 * P + 16]
+    bufs = device_buffers(sizes, seed=40 + hm)
+    s = make_set(bufs, hash_mapping=hm, gather_mapping=gm)
+    o = oracle.OracleSet(sizes)
+    for step in range(3):
+        if step:
+            mutate(bufs, sizes, 0.35, seed=400 + 10 * hm + step)
+        _, got = _checkpoint_bytes(s)
+        exp, *_ = o.checkpoint(host_copies(bufs))
+        assert first_diff(got, exp) is None, f"hash {hm} gather {gm} step {step}"
+    s.destroy()
+
+
+def test_autotune_keeps_parity():
+    sizes = [40 * P, 3 * P + 8, 17 * P]
+    bufs = device_buffers(sizes, seed=51)
+    s = make_set(bufs)
+    o = oracle.OracleSet(sizes)
+    _, b0 = _checkpoint_bytes(s)
+    e0, *_ = o.checkpoint(host_copies(bufs))
+    assert first_diff(b0, e0) is None
+    t = s.autotune()
+    assert 0 <= t["hash_mapping"] < 9 and 0 <= t["gather_mapping"] < 6
+    assert all(x > 0 for x in t["hash_ms"]) and all(x > 0 for x in t["gather_ms"])
+    # autotuning hashed into scratch: the committed hashes are untouched
+    assert np.array_equal(s.hashes(), oracle.hash_all(host_copies(bufs)))
+    mutate(bufs, sizes, 0.25, seed=52)
+    _, b1 = _checkpoint_bytes(s)
+    e1, *_ = o.checkpoint(host_copies(bufs))
+    assert first_diff(b1, e1) is None
+    s.destroy()
