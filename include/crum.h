@@ -94,6 +94,8 @@ typedef struct crum_config {
                                   0-5: register mappings (one warp or one CTA per
                                   page), 6-8: shared-memory bulk-copy mappings */
     int gather_mapping;        /* thread mapping of the gather kernel, 0..5; -1 default */
+    int external_staging;      /* 1: allocate no staging; a crum_server lends staging
+                                  to the set for each request it admits */
 } crum_config;
 
 /* Fill *cfg with defaults (device 0, 1 GiB staging, 64 MiB chunks, memory sink). */
@@ -269,6 +271,88 @@ crum_status crum_poke_hash(crum_set *set, uint64_t global_page, uint64_t value);
 
 /* Kernel launches the library has issued since load (for launch accounting). */
 uint64_t crum_kernel_launches(void);
+
+/* ---- serving: checkpoint/restore requests from many clients ----
+   The paper checkpoints each MPI rank's process (Sections 3.3-3.4); here a
+   server takes checkpoint and restore requests from many clients as they
+   arrive and keeps several on the device at once ("continuous batching"):
+   a request is admitted when a slot is free and the staging it needs fits
+   the remaining staging budget, so requests that arrive while others run
+   join as soon as memory frees up.  Each client is a crum_set created with
+   external_staging = 1 (its hash table and page tables stay resident on the
+   device between requests) plus the stream its application runs on.  One
+   request per client is on the device at a time; a client's requests run
+   in arrival order.  A client must not enqueue further work that writes
+   its registered memory on its stream until its checkpoint request has
+   reached CRUM_WAIT_CAPTURED (the consistency point is the capture). */
+
+typedef struct crum_server crum_server;
+
+typedef struct crum_server_config {
+    int device;
+    uint64_t staging_budget;  /* device bytes lent to admitted requests; 0: 16 GiB */
+    int max_inflight;         /* requests on the device at once; 0: 8 */
+} crum_server_config;
+
+#define CRUM_REQ_CHECKPOINT 0      /* incremental checkpoint of the client's set */
+#define CRUM_REQ_CHECKPOINT_FULL 1 /* full checkpoint (starts a new chain) */
+#define CRUM_REQ_RESTORE 2         /* restore the client's newest persisted image chain */
+
+typedef struct crum_request_info {
+    uint64_t id;
+    uint32_t client;
+    int kind;
+    int status;               /* crum_status; CRUM_ETIMEOUT while still running */
+    int done;                 /* 1 once complete */
+    uint64_t n_dirty;         /* checkpoint: pages in the image; restore: pages written */
+    uint64_t bytes;           /* image bytes drained (checkpoint) or restored payload */
+    uint64_t image_seq;       /* checkpoint: seq of the new image; restore: chain end seq */
+    uint64_t checksum;        /* checkpoint: the new image's trailer checksum */
+    double t_queue_ms;        /* submit -> admitted */
+    double t_total_ms;        /* submit -> complete (checkpoint: persisted) */
+} crum_request_info;
+
+typedef struct crum_server_stats {
+    uint64_t submitted, completed, failed;
+    uint64_t bytes_checkpointed;  /* footprint bytes of completed checkpoint requests */
+    uint64_t bytes_restored;
+    double p50_ms, p99_ms;        /* submit -> complete over completed requests */
+    double p50_ckpt_ms, p99_ckpt_ms, p50_restore_ms, p99_restore_ms;
+    double wall_ms;               /* first submit -> last completion */
+    uint32_t peak_inflight;
+    uint64_t peak_staging;        /* most staging bytes lent at once */
+} crum_server_stats;
+
+/* Create a server (allocates the staging budget on the device and starts its
+   admission thread).  Errors: EINVAL, ENOMEM, ECUDA. */
+crum_status crum_server_create(const crum_server_config *cfg, crum_server **out);
+
+/* Wait for every submitted request, stop the thread, free the staging. */
+crum_status crum_server_destroy(crum_server *srv);
+
+/* Add a client: a set made with external_staging = 1 and registered
+   allocations, and the stream its application uses.  The server does not
+   own the set.  Errors: EINVAL (set without external staging, or larger
+   than the whole budget). */
+crum_status crum_server_add_client(crum_server *srv, crum_set *set, crum_stream_t app_stream,
+                                   uint32_t *client_id);
+
+/* Queue a request (CRUM_REQ_*); returns at once with its id. */
+crum_status crum_server_submit(crum_server *srv, uint32_t client, int kind, uint64_t *request_id);
+
+/* Wait until a request completes (timeout_ns < 0: no limit) and fill *info.
+   CRUM_WAIT_CAPTURED-like early return: stage = 1 waits only until a
+   checkpoint request's pages are captured.  Returns the request's status,
+   or ETIMEOUT. */
+crum_status crum_server_wait(crum_server *srv, uint64_t request_id, int stage, int64_t timeout_ns,
+                             crum_request_info *info);
+
+/* Wait for every submitted request, then fill *stats (latencies over all
+   completed requests since create or the last reset). */
+crum_status crum_server_drain(crum_server *srv, crum_server_stats *stats);
+
+/* Forget completed requests and their latencies (for a fresh measurement). */
+crum_status crum_server_reset_stats(crum_server *srv);
 
 /* ---- allocation-free dirty-page detection (the paper has no counterpart;
         this exists for callers that cannot allocate device memory) ---- */

@@ -41,7 +41,40 @@ class Config(ctypes.Structure):
                 ("chunk_bytes", ctypes.c_uint64), ("host_pool_bytes", ctypes.c_uint64),
                 ("sink", ctypes.c_int), ("sink_dir", ctypes.c_char_p),
                 ("verify", ctypes.c_int), ("fsync", ctypes.c_int),
-                ("hash_mapping", ctypes.c_int), ("gather_mapping", ctypes.c_int)]
+                ("hash_mapping", ctypes.c_int), ("gather_mapping", ctypes.c_int),
+                ("external_staging", ctypes.c_int)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("staging_budget", ctypes.c_uint64),
+                ("max_inflight", ctypes.c_int)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("client", ctypes.c_uint32), ("kind", ctypes.c_int),
+                ("status", ctypes.c_int), ("done", ctypes.c_int), ("n_dirty", ctypes.c_uint64),
+                ("bytes", ctypes.c_uint64), ("image_seq", ctypes.c_uint64),
+                ("checksum", ctypes.c_uint64),
+                ("t_queue_ms", ctypes.c_double), ("t_total_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("bytes_checkpointed", ctypes.c_uint64),
+                ("bytes_restored", ctypes.c_uint64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("p50_ckpt_ms", ctypes.c_double),
+                ("p99_ckpt_ms", ctypes.c_double), ("p50_restore_ms", ctypes.c_double),
+                ("p99_restore_ms", ctypes.c_double), ("wall_ms", ctypes.c_double),
+                ("peak_inflight", ctypes.c_uint32), ("peak_staging", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+REQ_CHECKPOINT, REQ_CHECKPOINT_FULL, REQ_RESTORE = 0, 1, 2
 
 
 class ImageInfo(ctypes.Structure):
@@ -86,6 +119,13 @@ SIGNATURES = {
     "crum_poke_hash": ([_VP, _U64, _U64], _I),
     "crum_kernel_launches": ([], _U64),
     "crum_dirty_pages_static": ([_VP, _U64, _VP, _I, _VP, _VP, _VP], _I),
+    "crum_server_create": ([ctypes.POINTER(ServerConfig), ctypes.POINTER(_VP)], _I),
+    "crum_server_destroy": ([_VP], _I),
+    "crum_server_add_client": ([_VP, _VP, _VP, ctypes.POINTER(_U32)], _I),
+    "crum_server_submit": ([_VP, _U32, _I, ctypes.POINTER(_U64)], _I),
+    "crum_server_wait": ([_VP, _U64, _I, _I64, ctypes.POINTER(RequestInfo)], _I),
+    "crum_server_drain": ([_VP, ctypes.POINTER(ServerStats)], _I),
+    "crum_server_reset_stats": ([_VP], _I),
 }
 
 _lib = None
@@ -262,6 +302,55 @@ class CheckpointSet:
     def destroy(self) -> None:
         if self.handle:
             load().crum_set_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class Server:
+    """Checkpoint/restore request server (``crum_server``)."""
+
+    def __init__(self, device: int = 0, staging_budget: int = 16 << 30, max_inflight: int = 8):
+        cfg = ServerConfig(device, staging_budget, max_inflight)
+        h = _VP()
+        _check(load().crum_server_create(ctypes.byref(cfg), ctypes.byref(h)), "crum_server_create")
+        self.handle = h.value
+
+    def add_client(self, cset: "CheckpointSet", stream: int) -> int:
+        i = _U32()
+        _check(load().crum_server_add_client(self.handle, cset.handle, stream, ctypes.byref(i)),
+               "crum_server_add_client")
+        return i.value
+
+    def submit(self, client: int, kind: int = REQ_CHECKPOINT) -> int:
+        rid = _U64()
+        _check(load().crum_server_submit(self.handle, client, kind, ctypes.byref(rid)),
+               "crum_server_submit")
+        return rid.value
+
+    def wait(self, request_id: int, stage: int = WAIT_PERSISTED, timeout_s: Optional[float] = None,
+             allow=(OK, ECOLLISION)) -> dict:
+        info = RequestInfo()
+        t = -1 if timeout_s is None else int(timeout_s * 1e9)
+        _check(load().crum_server_wait(self.handle, request_id, stage, t, ctypes.byref(info)),
+               "crum_server_wait", allow)
+        return info.as_dict()
+
+    def drain(self) -> dict:
+        st = ServerStats()
+        _check(load().crum_server_drain(self.handle, ctypes.byref(st)), "crum_server_drain")
+        return st.as_dict()
+
+    def reset_stats(self) -> None:
+        _check(load().crum_server_reset_stats(self.handle), "crum_server_reset_stats")
+
+    def destroy(self) -> None:
+        if self.handle:
+            load().crum_server_destroy(self.handle)
             self.handle = 0
 
     def __del__(self):

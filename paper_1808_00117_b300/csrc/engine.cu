@@ -205,7 +205,8 @@ crum_status enqueue_drain(crum_set* s, crum_image* img, Half& H) {
   CK(cudaStreamWaitEvent(s->drain_stream, img->ev_captured, 0));
   CK(cudaEventRecord(img->ev_d0, s->drain_stream));
   CK(cudaMemcpyAsync(img->host, H.meta, meta_bytes(A, n), cudaMemcpyDeviceToHost, s->drain_stream));
-  if (n > 0 && !img->drop_payload)
+  // the null sink drains too (the bytes cross the link); the writer drops them
+  if (n > 0)
     CK(cudaMemcpyAsync(img->host + meta_bytes(A, n), H.payload, n * kPage, cudaMemcpyDeviceToHost,
                        s->drain_stream));
   CK(cudaMemcpyAsync(img->host + img->image_bytes - 8, H.scalars + 1, 8, cudaMemcpyDeviceToHost,
@@ -358,6 +359,8 @@ crum_status checkpoint_chunked(crum_set* s, crum_image* img, cudaStream_t app,
   if (st != CRUM_OK) return st;
   img->n_dirty = reinterpret_cast<volatile uint64_t*>(H0.mailbox)[0];
   img->collisions = reinterpret_cast<volatile uint64_t*>(H0.mailbox)[1];
+  if (reinterpret_cast<volatile uint64_t*>(H0.mailbox)[2] != 0)
+    return fail(CRUM_ETIMEOUT, "hash kernel: a bounded device wait ran out");
   st = alloc_image_host(s, img);
   if (st != CRUM_OK) return st;
   const uint64_t n = img->n_dirty, A = img->n_allocs, hs = s->half_slots;
@@ -381,9 +384,8 @@ crum_status checkpoint_chunked(crum_set* s, crum_image* img, cudaStream_t app,
     CK(cudaEventRecord(ev, s->cap_stream));
     CK(cudaStreamWaitEvent(s->drain_stream, ev, 0));
     CK(cudaEventDestroy(ev));  // released once the recorded work completes
-    if (!img->drop_payload)
-      CK(cudaMemcpyAsync(img->host + meta_bytes(A, n) + s0 * kPage, H.payload, (s1 - s0) * kPage,
-                         cudaMemcpyDeviceToHost, s->drain_stream));
+    CK(cudaMemcpyAsync(img->host + meta_bytes(A, n) + s0 * kPage, H.payload, (s1 - s0) * kPage,
+                       cudaMemcpyDeviceToHost, s->drain_stream));
     CK(cudaEventRecord(H.ev_drained, s->drain_stream));
     h ^= 1;
   }
@@ -424,8 +426,11 @@ uint8_t* PinnedPool::alloc(size_t n) {
         if (len > n) a.free_list.emplace(off + n, len - n);
         return a.base + off;
       }
+  // grow geometrically (at least 4 MiB, at most 256 MiB beyond the request)
+  // so small sets pin little and large ones pin rarely
   size_t size = std::max(n, arenas_.empty() ? initial_ : size_t(0));
-  size = std::max(size, size_t(256) << 20);
+  size = std::max(size, std::min(std::max(reserved_, size_t(4) << 20), size_t(256) << 20));
+  size = (size + (size_t(2) << 20) - 1) & ~((size_t(2) << 20) - 1);
   uint8_t* p = nullptr;
   if (cudaHostAlloc(reinterpret_cast<void**>(&p), size, cudaHostAllocPortable) != cudaSuccess) {
     cudaGetLastError();
@@ -515,7 +520,7 @@ crum_status crum_set_create(const crum_config* cfg_in, crum_set** out) {
   s->cfg.sink_dir = nullptr;
   s->device = cfg.device;
   s->set_id = g_set_ids.fetch_add(1);
-  s->half_slots = cfg.staging_bytes / 2 / kPage;
+  s->half_slots = cfg.external_staging ? 0 : cfg.staging_bytes / 2 / kPage;
   if (cfg.hash_mapping >= 0) s->map_hash = cfg.hash_mapping;
   if (cfg.gather_mapping >= 0) s->map_gather = cfg.gather_mapping;
   s->pool = std::make_shared<crum::PinnedPool>(cfg.host_pool_bytes);
@@ -530,7 +535,7 @@ crum_status crum_set_create(const crum_config* cfg_in, crum_set** out) {
   CK(cudaEventCreateWithFlags(&s->ev_done, cudaEventDisableTiming));
   CK(cudaMalloc(&s->d_collisions, 2 * sizeof(unsigned long long)));  // [0] collisions, [1] error
   for (Half& H : s->half) {
-    if (cudaMalloc(&H.payload, s->half_slots * kPage) != cudaSuccess) {
+    if (!cfg.external_staging && cudaMalloc(&H.payload, s->half_slots * kPage) != cudaSuccess) {
       cudaGetLastError();
       return fail(CRUM_ENOMEM, "cannot allocate %llu bytes of staging",
                   (unsigned long long)(s->half_slots * kPage));
@@ -567,7 +572,7 @@ crum_status crum_set_destroy(crum_set* s) {
   image_unref(s->last);
   for (Half& H : s->half) {
     cudaFree(H.meta);
-    cudaFree(H.payload);
+    if (!s->cfg.external_staging) cudaFree(H.payload);
     cudaFree(H.scalars);
     cudaFreeHost(H.mailbox);
     cudaEventDestroy(H.ev_scanned);
@@ -771,6 +776,7 @@ crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, cr
   DeviceGuard dg(s->device);
   std::unique_lock<std::mutex> lk(s->mu);
   if (s->allocs.empty()) return fail(CRUM_EINVAL, "no registered allocations");
+  if (s->half_slots == 0) return fail(CRUM_EINVAL, "no staging bound to this set");
   crum_status st = ensure_capacity(s, lk);
   if (st != CRUM_OK) return st;
   const int h = s->next_half;
@@ -1196,6 +1202,7 @@ crum_status crum_restore(crum_set* s, const crum_image* chain_end, crum_stream_t
         return fail(CRUM_EMISMATCH, "allocation %zu: image %llu bytes, set %llu bytes", a,
                     (unsigned long long)img->table[a].second, (unsigned long long)s->allocs[a].bytes);
   }
+  if (s->half_slots == 0) return fail(CRUM_EINVAL, "no staging bound to this set");
   crum_status st = ensure_capacity(s, lk);
   if (st != CRUM_OK) return st;
   CK(cudaEventRecord(s->ev_app, us));
@@ -1298,4 +1305,19 @@ namespace crum {
 // Lets other translation units of the library report a message through
 // crum_last_error().
 void set_last_error(const char* msg) { t_err = msg; }
+}  // namespace crum
+
+namespace crum {
+// Point both staging halves of an external-staging set at `payload`
+// (`slots` pages), or detach them (payload == nullptr).  The caller (the
+// server) guarantees the set has nothing in flight.
+crum_status bind_staging(crum_set* s, uint8_t* payload, uint64_t slots) {
+  std::unique_lock<std::mutex> lk(s->mu);
+  if (!s->cfg.external_staging) return fail(CRUM_EINVAL, "set owns its staging");
+  if (!(s->half[0].drain_enqueued && s->half[1].drain_enqueued))
+    return fail(CRUM_EBUSY, "set has a capture in flight");
+  for (Half& H : s->half) H.payload = payload;
+  s->half_slots = payload != nullptr ? slots : 0;
+  return CRUM_OK;
+}
 }  // namespace crum

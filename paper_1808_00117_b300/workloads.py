@@ -83,7 +83,7 @@ def workload(name: str) -> Workload:
         return Workload(name, [8 * GiB], "u32", 0.05, 10, "runs", 0x5EED + 1)
     if name == "stencil":
         sizes = loguniform_sizes(0x5EED + 2, 200, 4 * KiB, 512 * MiB, 24 * GiB)
-        return Workload(name, sizes, "fp64", 0.30, 20, "uniform", 0x5EED + 2)
+        return Workload(name, sizes, "fp64", 0.30, 20, "stencil", 0x5EED + 2)
     if name == "large":
         sizes = loguniform_sizes(0x5EED + 4, 4096, 64 * KiB, 2 * GiB, 140 * GiB)
         return Workload(name, sizes, "fp32", 0.02, 50, "uniform", 0x5EED + 4)
@@ -148,6 +148,35 @@ def fill_(buf, seed: int, kind: str) -> None:
         buf[:n8].view(torch.int64).random_(generator=g)
     if n > n8:
         buf[n8:] = torch.randint(0, 256, (n - n8,), dtype=torch.uint8, device=buf.device, generator=g)
+
+
+STENCIL_NX = STENCIL_NY = 64  # fp64 box planes of 64 x 64 (32 KiB, two per page)
+
+
+def stencil_plan(nbytes: int, frac: float, seed: int):
+    """Interior z-range [z0, z0 + L) of an fp64 (nz, 64, 64) box so that about
+    `frac` of the box's planes are rewritten; None if the box is too thin."""
+    nz = nbytes // (8 * STENCIL_NX * STENCIL_NY)
+    if nz < 3:
+        return None
+    L = max(1, min(nz - 2, int(round(frac * nz))))
+    rng = np.random.default_rng(seed)
+    z0 = int(rng.integers(1, nz - L)) if nz - L > 1 else 1
+    return nz, z0, L
+
+
+def stencil_step_(buf, plan) -> None:
+    """27-point average (3x3x3 box mean) over the interior sub-box
+    z in [z0, z0+L), y, x in [1, 63) of an fp64 (nz, 64, 64) field, written
+    in place: the synthetic stencil application's update."""
+    if plan is None:
+        return
+    torch = _torch()
+    nz, z0, L = plan
+    box = buf[: nz * 8 * STENCIL_NX * STENCIL_NY].view(torch.float64).view(nz, STENCIL_NY, STENCIL_NX)
+    src = box[z0 - 1: z0 + L + 1].unsqueeze(0).unsqueeze(0)
+    avg = torch.nn.functional.avg_pool3d(src, kernel_size=3, stride=1)
+    box[z0: z0 + L, 1: STENCIL_NY - 1, 1: STENCIL_NX - 1] = avg[0, 0]
 
 
 def mutate_pages_(buf, pages, seed: int, has_tail=None) -> None:

@@ -1,0 +1,136 @@
+"""Serving: checkpoint/restore requests from several clients through
+crum_server, several on the device at once.  Each client's results must be
+the same alone and in the mix (exact: integer work), and equal the oracle's
+images; admission must respect the staging budget."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1808_00117_b300 as crum
+from paper_1808_00117_b300 import workloads as W
+
+from helpers import torch
+
+pytestmark = pytest.mark.gpu
+P = 65536
+SIZES = [3 * P + 5, 40 * P, 7 * P + 100, 16 * P]
+
+
+@pytest.fixture(autouse=True)
+def _cuda():
+    if not torch().cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    crum.load()
+
+
+class Client:
+    def __init__(self, server, idx, size):
+        t = torch()
+        self.idx, self.size = idx, size
+        self.stream = t.cuda.Stream()
+        self.buf = t.empty(size, dtype=t.uint8, device="cuda")
+        W.fill_(self.buf, 600 + idx, "fp32")
+        t.cuda.synchronize()
+        self.set = crum.CheckpointSet(external_staging=1)
+        self.set.register(self.buf.data_ptr(), size)
+        self.cid = server.add_client(self.set, self.stream.cuda_stream)
+        self.oracle = oracle.OracleSet([size])
+        self.step = 0
+        self.states = []
+
+    def host(self):
+        self.stream.synchronize()
+        return self.buf.cpu().numpy().copy()
+
+    def mutate(self):
+        self.step += 1
+        n = W.pages_of(self.size)
+        pages = W.choose_uniform(self.idx * 1000 + self.step, n, max(1, n // 3))
+        with torch().cuda.stream(self.stream):
+            W.mutate_pages_(self.buf, pages, self.idx * 77 + self.step)
+
+
+def run_sequence(server, clients, rounds, restore_at):
+    """Each round: every client mutates and submits a checkpoint; the
+    client waits for its capture before touching its memory again.  At
+    round `restore_at` every client also asks for a restore.  Returns per
+    client the checksums of its checkpoint images and the oracle's."""
+    got = {c.idx: [] for c in clients}
+    exp = {c.idx: [] for c in clients}
+    pending = []
+    for rnd in range(rounds):
+        round_ids = []
+        for c in clients:
+            if rnd:
+                c.mutate()
+            round_ids.append((c, server.submit(c.cid, crum.REQ_CHECKPOINT)))
+        for c, rid in round_ids:
+            server.wait(rid, crum.WAIT_CAPTURED)
+            state = c.host()
+            c.states.append(state)
+            img, *_ = c.oracle.checkpoint([state])
+            exp[c.idx].append(int(np.frombuffer(img[-8:], dtype=np.uint64)[0]))
+            pending.append((c, rid))
+        if rnd == restore_at:
+            for c in clients:
+                # scribble, then restore the newest chain: memory must come back
+                with torch().cuda.stream(c.stream):
+                    W.fill_(c.buf, 999, "u32")
+                rid = server.submit(c.cid, crum.REQ_RESTORE)
+                info = server.wait(rid)
+                assert info["done"] and info["status"] == crum.OK
+                assert np.array_equal(c.host(), c.states[-1])
+    for c, rid in pending:
+        info = server.wait(rid)
+        assert info["status"] == crum.OK
+        got[c.idx].append(info["checksum"])
+    return got, exp
+
+
+def test_same_alone_and_in_the_mix():
+    srv = crum.Server(staging_budget=1 << 30, max_inflight=3)
+    mix = [Client(srv, i, s) for i, s in enumerate(SIZES)]
+    got_mix, exp = run_sequence(srv, mix, rounds=4, restore_at=2)
+    stats = srv.drain()
+    assert stats["failed"] == 0 and stats["completed"] == 4 * len(SIZES) + len(SIZES)
+    assert stats["peak_inflight"] >= 2  # requests of different clients overlapped
+    for i in range(len(SIZES)):
+        assert got_mix[i] == exp[i], f"client {i} in the mix differs from the oracle"
+    srv.destroy()
+    # each client alone, same seeds: same images
+    for i, s in enumerate(SIZES):
+        srv1 = crum.Server(staging_budget=1 << 30, max_inflight=3)
+        alone = Client(srv1, i, s)
+        got_alone, _ = run_sequence(srv1, [alone], rounds=4, restore_at=2)
+        assert got_alone[i] == got_mix[i], f"client {i} alone differs from the mix"
+        srv1.destroy()
+
+
+def test_admission_respects_the_budget():
+    # budget holds the 40-page client or two small ones, never all at once
+    budget = 48 * P
+    srv = crum.Server(staging_budget=budget, max_inflight=8)
+    clients = [Client(srv, 10 + i, s) for i, s in enumerate(SIZES)]
+    ids = []
+    for rnd in range(3):
+        for c in clients:
+            if rnd:
+                c.mutate()
+            ids.append(srv.submit(c.cid, crum.REQ_CHECKPOINT_FULL if rnd == 0 else crum.REQ_CHECKPOINT))
+            srv.wait(ids[-1], crum.WAIT_CAPTURED)
+    stats = srv.drain()
+    assert stats["failed"] == 0 and stats["completed"] == len(ids)
+    assert stats["peak_staging"] <= budget
+    srv.destroy()
+
+
+def test_client_larger_than_budget_is_rejected():
+    srv = crum.Server(staging_budget=4 * P, max_inflight=2)
+    t = torch()
+    buf = t.empty(8 * P, dtype=t.uint8, device="cuda")
+    s = crum.CheckpointSet(external_staging=1)
+    s.register(buf.data_ptr(), buf.numel())
+    with pytest.raises(crum.CrumError) as e:
+        srv.add_client(s, t.cuda.current_stream().cuda_stream)
+    assert e.value.status == crum.EINVAL
+    srv.destroy()
