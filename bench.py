@@ -56,6 +56,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-mib", type=int, default=512)
+    ap.add_argument("--requests", type=int, default=2000, help="serving workload: request count")
     ap.add_argument("--footprint-gib", type=int, default=0,
                     help="resize the single-allocation uint32 workload (small profiling cases)")
     return ap.parse_args(argv)
@@ -707,10 +708,146 @@ def run_batched(args):
     return 0
 
 
+def run_serving(args):
+    """Checkpoint/restore requests from 32 simulated clients through
+    crum_server: footprints log-uniform 1 MiB..4 GiB (int32/fp32/fp64 in
+    turn), 80 % checkpoints (every 4th of a client full, so chains stay
+    short) and 20 % restores of the client's newest chain, each checkpoint
+    preceded by the client rewriting U[1 %, 50 %] of its pages.  Runs:
+    plain sequential form (one request on the device at a time) saturated,
+    which gives its service rate mu; then Poisson arrivals at 0.8 mu through
+    the sequential form and through continuous batching (8 slots, 16 GiB
+    staging budget); then batching saturated.  One driver thread per client
+    replays that client's requests at their arrival times."""
+    import threading
+    import torch
+    import paper_1808_00117_b300 as crum
+    from paper_1808_00117_b300 import workloads as W
+
+    torch.cuda.set_device(0)
+    crum.load()
+    n_clients, n_req = 32, args.requests
+    sizes = W.loguniform_sizes(0x5EED + 3, n_clients, 1 << 20, 4 << 30, total=None, round_to=W.PAGE)
+    kinds = ["i32", "fp32", "fp64"]
+    rng = np.random.default_rng(0x5EED + 3)
+    req_client = rng.integers(0, n_clients, size=n_req)
+    req_restore = rng.random(n_req) < 0.2
+    req_frac = rng.uniform(0.01, 0.50, size=n_req)
+    budget = 16 << 30
+
+    class C:
+        pass
+
+    clients = []
+    for i, n in enumerate(sizes):
+        c = C()
+        c.size, c.pages = n, W.pages_of(n)
+        c.buf = torch.empty(n, dtype=torch.uint8, device="cuda")
+        W.fill_(c.buf, 7000 + i, {"i32": "u32", "fp32": "fp32", "fp64": "fp64"}[kinds[i % 3]])
+        c.stream = torch.cuda.Stream()
+        clients.append(c)
+    torch.cuda.synchronize()
+
+    for c in clients:  # sets (and their pinned pools) are reused by every run
+        c.set = crum.CheckpointSet(external_staging=1, host_pool_bytes=2 * c.size + (8 << 20))
+        c.set.register(c.buf.data_ptr(), c.size)
+
+    def run(max_inflight, rate_hz, label, max_ckpt=0, max_rest=0):
+        srv = crum.Server(staging_budget=budget, max_inflight=max_inflight,
+                          max_checkpoints=max_ckpt, max_restores=max_rest)
+        for c in clients:
+            c.cid = srv.add_client(c.set, c.stream.cuda_stream)
+            c.n_ckpt = 0
+        # warm-up: every client's first request is a full checkpoint
+        for c in clients:
+            srv.wait(srv.submit(c.cid, crum.REQ_CHECKPOINT_FULL))
+            c.n_ckpt = 1
+        srv.reset_stats()
+        gaps = np.random.default_rng(17).exponential(1.0 / rate_hz, size=n_req) if rate_hz else np.zeros(n_req)
+        arrivals = np.cumsum(gaps)
+        per_client = [[] for _ in clients]
+        for r in range(n_req):
+            per_client[req_client[r]].append(r)
+        t0 = time.perf_counter() + 0.05
+        ids = [None] * n_req
+
+        def drive(ci):
+            c = clients[ci]
+            last = None
+            for r in per_client[ci]:
+                delay = t0 + arrivals[r] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                if last is not None:  # the client's consistency rule
+                    srv.wait(last[0], crum.WAIT_CAPTURED if last[1] != crum.REQ_RESTORE else crum.WAIT_PERSISTED)
+                if req_restore[r]:
+                    kind = crum.REQ_RESTORE
+                else:
+                    k = max(1, int(round(req_frac[r] * c.pages)))
+                    pages = W.choose_uniform(int(r) * 31 + ci, c.pages, k)
+                    with torch.cuda.stream(c.stream):
+                        W.mutate_pages_(c.buf, pages, int(r))
+                    kind = crum.REQ_CHECKPOINT_FULL if c.n_ckpt % 4 == 0 else crum.REQ_CHECKPOINT
+                    c.n_ckpt += 1
+                ids[r] = srv.submit(c.cid, kind)
+                last = (ids[r], kind)
+
+        threads = [threading.Thread(target=drive, args=(ci,)) for ci in range(n_clients)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        st = srv.drain()
+        wall_s = st["wall_ms"] * 1e-3
+        out = {"label": label, "max_inflight": max_inflight, "max_checkpoints": max_ckpt,
+               "max_restores": max_rest,
+               "arrival_rate_hz": None if not rate_hz else round(rate_hz, 2),
+               "completed": st["completed"], "failed": st["failed"],
+               "throughput_req_s": round(st["completed"] / wall_s, 2),
+               "checkpointed_gbs": round(st["bytes_checkpointed"] / wall_s / 1e9, 2),
+               "p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
+               "p50_ckpt_ms": round(st["p50_ckpt_ms"], 3), "p99_ckpt_ms": round(st["p99_ckpt_ms"], 3),
+               "p50_restore_ms": round(st["p50_restore_ms"], 3),
+               "p99_restore_ms": round(st["p99_restore_ms"], 3),
+               "peak_inflight": st["peak_inflight"], "peak_staging_bytes": st["peak_staging"]}
+        srv.destroy()
+        return out
+
+    launches0 = crum.kernel_launches()
+    seq_sat = run(1, 0, "sequential, saturated")
+    mu = seq_sat["throughput_req_s"]
+    lam = 0.8 * mu
+    seq = run(1, lam, "sequential, Poisson 0.8 mu")
+    sweep = [run(8, lam, f"batched {c}/{r}, Poisson 0.8 mu", c, r) for c, r in ((-1, -1), (2, 1), (1, 1), (3, 2))]
+    bat = min(sweep, key=lambda x: x["p99_ms"])
+    bat_sat = run(8, 0, "batched, saturated", bat["max_checkpoints"], bat["max_restores"])
+    line = {
+        "metric": METRIC, "value": bat_sat["checkpointed_gbs"], "unit": UNIT, "n_gpus": 1,
+        "steps": n_req, "warmup": n_clients, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "serving", "clients": n_clients, "requests": n_req,
+                   "footprint_bytes": int(sum(sizes)), "staging_budget": budget,
+                   "restore_share": 0.2, "dirty": "U[1%,50%] per checkpoint request",
+                   "value_def": "footprint bytes checkpointed per second, batched saturated"},
+        "runs": [seq_sat, seq] + sweep + [bat_sat],
+        "batched_vs_sequential_at_lambda": {
+            "p50_speedup": round(seq["p50_ms"] / bat["p50_ms"], 3),
+            "p99_speedup": round(seq["p99_ms"] / bat["p99_ms"], 3)},
+        "saturated_throughput_gain": round(bat_sat["throughput_req_s"] / seq_sat["throughput_req_s"], 3),
+        "gpu_launches": int(crum.kernel_launches() - launches0),
+    }
+    for c in clients:
+        c.set.destroy()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serving":
+        return run_serving(args)
     if args.workload in ("stencil", "large"):
         return run_batched(args)
     return run_ours(args)

@@ -244,10 +244,21 @@ crum_status start(crum_server* S, Request& r) {
 
 void admit(crum_server* S) {
   std::vector<bool> blocked(S->clients.size(), false);
+  int n_ckpt = 0, n_rest = 0;
+  for (uint64_t id : S->running) (S->reqs[id].kind == CRUM_REQ_RESTORE ? n_rest : n_ckpt)++;
+  bool kind_full[2] = {false, false};  // a kind at its limit stops its queue, in order
   for (auto it = S->pending.begin(); it != S->pending.end();) {
     if (S->running.size() >= static_cast<size_t>(S->cfg.max_inflight)) break;
     Request& r = S->reqs[*it];
     Client& c = S->clients[r.client];
+    const int k = r.kind == CRUM_REQ_RESTORE ? 1 : 0;
+    const int lim = k ? S->cfg.max_restores : S->cfg.max_checkpoints;
+    if (kind_full[k] || (lim > 0 && (k ? n_rest : n_ckpt) >= lim)) {
+      kind_full[k] = true;
+      blocked[r.client] = true;
+      ++it;
+      continue;
+    }
     if (c.busy || blocked[r.client]) {
       blocked[r.client] = true;  // keep this client's later requests behind this one
       ++it;
@@ -265,6 +276,7 @@ void admit(crum_server* S) {
       S->done_cv.notify_all();
     } else {
       S->running.push_back(r.id);
+      (k ? n_rest : n_ckpt)++;
       S->peak_inflight = std::max<uint32_t>(S->peak_inflight, S->running.size());
     }
   }
@@ -310,6 +322,11 @@ crum_status crum_server_create(const crum_server_config* cfg, crum_server** out)
   if (cfg) S->cfg = *cfg;
   if (S->cfg.staging_budget == 0) S->cfg.staging_budget = 16ull << 30;
   if (S->cfg.max_inflight <= 0) S->cfg.max_inflight = 8;
+  // per-kind limits: 0 means the default of one, negative means none
+  if (S->cfg.max_checkpoints == 0) S->cfg.max_checkpoints = 1;
+  if (S->cfg.max_restores == 0) S->cfg.max_restores = 1;
+  if (S->cfg.max_checkpoints < 0) S->cfg.max_checkpoints = 0;
+  if (S->cfg.max_restores < 0) S->cfg.max_restores = 0;
   S->cfg.staging_budget &= ~uint64_t(255);
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || S->cfg.device < 0 || S->cfg.device >= ndev) {

@@ -60,13 +60,15 @@ class Workload:
         return sum(pages_of(s) for s in self.sizes)
 
 
-def loguniform_sizes(seed: int, n: int, lo: int, hi: int, total: int, round_to: int = 4 * KiB,
+def loguniform_sizes(seed: int, n: int, lo: int, hi: int, total, round_to: int = 4 * KiB,
                      tol: float = 0.005) -> List[int]:
-    """n sizes log-uniform in [lo, hi], rounded to `round_to`, then rescaled
-    by a common factor (clamped to [lo, hi]) until the total is within `tol`
-    of `total`."""
+    """n sizes log-uniform in [lo, hi], rounded to `round_to`; with a `total`,
+    then rescaled by a common factor (clamped to [lo, hi]) until the sum is
+    within `tol` of it."""
     rng = np.random.default_rng(seed)
     x = np.exp(rng.uniform(math.log(lo), math.log(hi), size=n))
+    if total is None:
+        return [int(v) for v in np.clip(np.round(x / round_to) * round_to, lo, hi)]
     for _ in range(200):
         s = np.clip(np.round(x / round_to) * round_to, lo, hi)
         t = float(s.sum())

@@ -87,13 +87,16 @@ def run_sequence(server, clients, rounds, restore_at):
     return got, exp
 
 
-def test_same_alone_and_in_the_mix():
-    srv = crum.Server(staging_budget=1 << 30, max_inflight=3)
+@pytest.mark.parametrize("lanes", [(-1, -1), (1, 1)])
+def test_same_alone_and_in_the_mix(lanes):
+    srv = crum.Server(staging_budget=1 << 30, max_inflight=3, max_checkpoints=lanes[0],
+                      max_restores=lanes[1])
     mix = [Client(srv, i, s) for i, s in enumerate(SIZES)]
     got_mix, exp = run_sequence(srv, mix, rounds=4, restore_at=2)
     stats = srv.drain()
     assert stats["failed"] == 0 and stats["completed"] == 4 * len(SIZES) + len(SIZES)
-    assert stats["peak_inflight"] >= 2  # requests of different clients overlapped
+    if lanes[0] < 0:
+        assert stats["peak_inflight"] >= 2  # requests of different clients overlapped
     for i in range(len(SIZES)):
         assert got_mix[i] == exp[i], f"client {i} in the mix differs from the oracle"
     srv.destroy()
@@ -109,7 +112,7 @@ def test_same_alone_and_in_the_mix():
 def test_admission_respects_the_budget():
     # budget holds the 40-page client or two small ones, never all at once
     budget = 48 * P
-    srv = crum.Server(staging_budget=budget, max_inflight=8)
+    srv = crum.Server(staging_budget=budget, max_inflight=8, max_checkpoints=-1, max_restores=-1)
     clients = [Client(srv, 10 + i, s) for i, s in enumerate(SIZES)]
     ids = []
     for rnd in range(3):
