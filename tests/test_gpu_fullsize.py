@@ -1,0 +1,134 @@
+"""Parity at full workload sizes, in the launch configuration bench.py times
+(staging halves that hold every page, autotuned mappings).  The oracle is
+too slow for whole images here, so: page tables are checked in full against
+the workload's known dirty set, every page hash against the oracle (hashed
+on all host cores over page-aligned slices: page hashes are page-local),
+the incremental image's checksum by the oracle's image checker, payload
+slots on a seeded sample, and the restored chain on a seeded sample."""
+from concurrent.futures import ThreadPoolExecutor
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1808_00117_b300 as crum
+from paper_1808_00117_b300 import workloads as W
+
+from helpers import page_table, parse_header, stream_handle, torch
+
+pytestmark = pytest.mark.gpu
+P = 65536
+
+
+@pytest.fixture(autouse=True)
+def _cuda():
+    t = torch()
+    if not t.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    free, _ = t.cuda.mem_get_info()
+    if free < 100 << 30:
+        pytest.skip("needs about 100 GB of free device memory")
+    crum.load()
+    yield
+    t.cuda.synchronize()
+    t.cuda.empty_cache()
+
+
+def oracle_hashes(host_allocs, chunk_pages=4096):
+    """Oracle page hashes of every page, in global page order, computed in
+    parallel over page-aligned slices (the C oracle releases the GIL)."""
+    jobs = []
+    for a in host_allocs:
+        for lo in range(0, a.size, chunk_pages * P):
+            jobs.append(a[lo:lo + chunk_pages * P])
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        parts = list(ex.map(lambda x: oracle.hash_all([x]), jobs))
+    return np.concatenate(parts)
+
+
+def make_bench_set(bufs):
+    n_pages = sum(W.pages_of(b.numel()) for b in bufs)
+    s = crum.CheckpointSet(staging_bytes=2 * (n_pages + 1) * P)
+    for b in bufs:
+        s.register(b.data_ptr(), b.numel())
+    return s
+
+
+def check_image_sample(img_bytes, host_allocs, offsets, rng, n_sample=64):
+    h = parse_header(img_bytes)
+    pt = page_table(img_bytes)
+    idx = rng.choice(h["n"], size=min(n_sample, h["n"]), replace=False)
+    for s in idx:
+        a, p = int(pt[s, 0]), int(pt[s, 1])
+        src = host_allocs[a][p * P:(p + 1) * P]
+        slot = np.frombuffer(img_bytes, dtype=np.uint8, count=P, offset=h["poff"] + int(s) * P)
+        assert np.array_equal(slot[:src.size], src) and not slot[src.size:].any(), f"slot {s}"
+
+
+def test_uint32_8g_full_size():
+    t = torch()
+    wl = W.workload("uint32_8g")
+    buf = t.empty(wl.sizes[0], dtype=t.uint8, device="cuda")
+    W.fill_(buf, wl.seed, wl.kind)
+    s = make_bench_set([buf])
+    s.checkpoint(stream_handle(), crum.FULL).wait()
+    s.autotune()
+    chain, rng = [], np.random.default_rng(11)
+    for step in (1, 2):
+        pages = W.choose_step(wl, step, wl.n_pages)
+        W.mutate_pages_(buf, pages, wl.seed + step)
+        img = s.checkpoint(stream_handle())
+        img.wait()
+        chain.append(img)
+        b = img.to_bytes()
+        assert page_table(b)[:, 1].tolist() == pages.tolist()  # in full, ascending
+        assert oracle.check_image(b) == oracle.OK               # trailer over every byte
+        host = buf.cpu().numpy()
+        check_image_sample(b, [host], [0], rng)
+        assert np.array_equal(s.hashes(), oracle_hashes([host]))
+        del b
+    state = buf.cpu().numpy()
+    sample = rng.choice(wl.n_pages, size=256, replace=False)
+    W.fill_(buf, 4242, "u32")
+    s.restore(chain[-1], stream_handle())
+    t.cuda.synchronize()
+    got = buf.cpu().numpy()
+    for p in sample:
+        assert np.array_equal(got[p * P:(p + 1) * P], state[p * P:(p + 1) * P]), p
+    for img in chain:
+        img.release()
+    s.destroy()
+
+
+def test_stencil_full_size():
+    t = torch()
+    wl = W.workload("stencil")
+    bufs = []
+    for i, n in enumerate(wl.sizes):
+        b = t.empty(n, dtype=t.uint8, device="cuda")
+        W.fill_(b, wl.seed * 7919 + i, wl.kind)
+        bufs.append(b)
+    s = make_bench_set(bufs)
+    s.checkpoint(stream_handle(), crum.FULL).wait()
+    s.autotune()
+    offsets = np.cumsum([0] + [W.pages_of(n) for n in wl.sizes])
+    plans = [W.stencil_plan(n, wl.dirty_frac, 77 + i) for i, n in enumerate(wl.sizes)]
+    for b, plan in zip(bufs, plans):
+        W.stencil_step_(b, plan)
+    img = s.checkpoint(stream_handle())
+    img.wait()
+    b = img.to_bytes()
+    plane = 8 * W.STENCIL_NX * W.STENCIL_NY
+    exp = []
+    for a, plan in enumerate(plans):
+        if plan is not None:
+            _, z0, L = plan
+            exp.extend((a, p) for p in range(z0 * plane // P, ((z0 + L) * plane - 1) // P + 1))
+    assert page_table(b).tolist() == [list(x) for x in exp]  # in full
+    assert oracle.check_image(b) == oracle.OK
+    hosts = [x.cpu().numpy() for x in bufs]
+    check_image_sample(b, hosts, offsets, np.random.default_rng(5))
+    assert np.array_equal(s.hashes(), oracle_hashes(hosts))
+    img.release()
+    s.destroy()
