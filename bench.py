@@ -57,6 +57,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-mib", type=int, default=512)
     ap.add_argument("--requests", type=int, default=2000, help="serving workload: request count")
+    ap.add_argument("--graph", type=int, default=1,
+                    help="1: launch each capture as one CUDA graph (0: one launch per op)")
     ap.add_argument("--footprint-gib", type=int, default=0,
                     help="resize the single-allocation uint32 workload (small profiling cases)")
     return ap.parse_args(argv)
@@ -321,7 +323,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     staging = 2 * ((n_pages + 1) * W.PAGE)  # two halves that each hold every page
     pool = full_image + (warmup + steps + 2) * incr_image
-    s = crum.CheckpointSet(device=local, staging_bytes=staging, host_pool_bytes=pool)
+    s = crum.CheckpointSet(device=local, staging_bytes=staging, host_pool_bytes=pool,
+                           use_graph=int(args.graph))
     for b in bufs:
         s.register(b.data_ptr(), b.numel())
     stream = torch.cuda.current_stream()
@@ -442,6 +445,7 @@ def run_ours(args):
                    "staging_bytes": staging, "parallelism": f"replica per GPU x{world}",
                    "l2": "inputs (8 GiB) larger than L2 (126 MB); no flush",
                    "value_def": "footprint bytes / capture-kernel device time (hash+scan+gather)",
+                   "capture_launch": "cuda graph" if args.graph else "one launch per op",
                    "hash_mapping": tune["hash_mapping"], "gather_mapping": tune["gather_mapping"],
                    "autotune_hash_ms": [round(x, 4) for x in tune["hash_ms"]],
                    "autotune_gather_ms": [round(x, 4) for x in tune["gather_ms"]]},
@@ -520,6 +524,11 @@ def run_e2e(torch, crum, W, s, bufs, wl, steps, sh, stream, step0, dist, dev, wo
         im.release()
         return m * W.PAGE, nbytes
 
+    # untimed: a fresh full image starts a new chain, so the previous chain
+    # (kept alive by its newest image) is freed and its pinned memory reused
+    im = s.checkpoint(sh, crum.FULL)
+    im.wait()
+    im.release()
     for warm in range(2):
         one(plan[warm])
     barrier(dist)

@@ -96,6 +96,15 @@ typedef struct crum_config {
     int gather_mapping;        /* thread mapping of the gather kernel, 0..5; -1 default */
     int external_staging;      /* 1: allocate no staging; a crum_server lends staging
                                   to the set for each request it admits */
+    int use_graph;             /* 1: launch each capture (memsets, hash, scan, gather
+                                  and their events) as one instantiated CUDA graph
+                                  per staging half, rebuilt when registrations or
+                                  mappings change; verify-mode and chunked captures
+                                  use plain launches */
+    int max_chain;             /* > 0: after this many incremental images the next
+                                  checkpoint is full, so restore replays at most
+                                  max_chain + 1 images and older chains can be freed;
+                                  0: chains grow without limit */
 } crum_config;
 
 /* Fill *cfg with defaults (device 0, 1 GiB staging, 64 MiB chunks, memory sink). */

@@ -176,6 +176,7 @@ crum_status ensure_capacity(crum_set* s, std::unique_lock<std::mutex>& lk) {
     s->needs_full = true;  // the shadow starts empty
   }
   s->table_dirty = true;
+  s->graph_epoch++;
   return CRUM_OK;
 }
 
@@ -403,6 +404,131 @@ crum_status checkpoint_chunked(crum_set* s, crum_image* img, cudaStream_t app,
   return CRUM_OK;
 }
 
+// Builds the capture graph of staging half h for the current registrations
+// (see crum::CaptureGraph); the node arguments are placeholders that
+// graph_launch replaces before every launch.
+crum_status graph_build(crum_set* s, int h, crum_image* img, const crum::HashArgs& ha,
+                        const crum::ScanArgs& sa, const crum::GatherArgs& ga) {
+  crum::CaptureGraph& G = s->graph[h];
+  Half& H = s->half[h];
+  if (G.exec) {
+    cudaGraphExecDestroy(G.exec);
+    G.exec = nullptr;
+  }
+  if (G.graph) {
+    cudaGraphDestroy(G.graph);
+    G.graph = nullptr;
+  }
+  for (cudaEvent_t& ev : G.placeholder)
+    if (ev == nullptr) CK(cudaEventCreate(&ev));
+  (void)img;
+  CK(crum::hash_spec(s->n_pages, s->map_hash, false, &G.hs));
+  CK(crum::scan_spec(&G.ss));
+  CK(crum::gather_spec(s->n_pages, s->map_gather, ga.shadow != nullptr, &G.gs));
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  cudaGraphNode_t prev = nullptr, n = nullptr;
+  auto after = [&](cudaGraphNode_t node) { prev = node; };
+  cudaError_t e = cudaSuccess;
+  cudaMemsetParams mp{};
+  mp.dst = s->d_mask;
+  mp.value = 0;
+  mp.elementSize = 4;
+  mp.width = (s->n_pages + 31) / 32;
+  mp.height = 1;
+  if (e == cudaSuccess) e = cudaGraphAddMemsetNode(&n, g, nullptr, 0, &mp);
+  after(n);
+  mp.dst = s->d_collisions;
+  mp.width = 4;  // two u64 counters as four u32
+  if (e == cudaSuccess) e = cudaGraphAddMemsetNode(&n, g, &prev, 1, &mp);
+  after(n);
+  if (e == cudaSuccess) e = cudaGraphAddEventRecordNode(&G.k0, g, &prev, 1, G.placeholder[0]);
+  after(G.k0);
+  auto kparams = [](const crum::KernelSpec& sp, void** args) {
+    cudaKernelNodeParams kp{};
+    kp.func = const_cast<void*>(sp.func);
+    kp.gridDim = dim3(sp.grid);
+    kp.blockDim = dim3(sp.block);
+    kp.sharedMemBytes = static_cast<unsigned>(sp.smem);
+    kp.kernelParams = args;
+    return kp;
+  };
+  crum::HashArgs ha_c = ha;
+  crum::ScanArgs sa_c = sa;
+  crum::GatherArgs ga_c = ga;
+  void* a_h[] = {&ha_c};
+  void* a_s[] = {&sa_c};
+  void* a_g[] = {&ga_c};
+  cudaKernelNodeParams kp = kparams(G.hs, a_h);
+  if (e == cudaSuccess) e = cudaGraphAddKernelNode(&G.hash, g, &prev, 1, &kp);
+  after(G.hash);
+  if (e == cudaSuccess) e = cudaGraphAddEventRecordNode(&G.k1, g, &prev, 1, G.placeholder[1]);
+  after(G.k1);
+  if (e == cudaSuccess) e = cudaGraphAddEventWaitNode(&n, g, &prev, 1, H.ev_drained);
+  after(n);
+  if (e == cudaSuccess) e = cudaGraphAddEventRecordNode(&G.k2, g, &prev, 1, G.placeholder[2]);
+  after(G.k2);
+  kp = kparams(G.ss, a_s);
+  if (e == cudaSuccess) e = cudaGraphAddKernelNode(&G.scan, g, &prev, 1, &kp);
+  after(G.scan);
+  if (e == cudaSuccess) e = cudaGraphAddEventRecordNode(&n, g, &prev, 1, H.ev_scanned);
+  after(n);
+  kp = kparams(G.gs, a_g);
+  if (e == cudaSuccess) e = cudaGraphAddKernelNode(&G.gather, g, &prev, 1, &kp);
+  after(G.gather);
+  if (e == cudaSuccess) e = cudaGraphAddEventRecordNode(&G.captured, g, &prev, 1, G.placeholder[3]);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&G.exec, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    G.exec = nullptr;
+    return fail(CRUM_ECUDA, "capture graph: %s", cudaGetErrorString(e));
+  }
+  G.graph = g;
+  G.epoch = s->graph_epoch;
+  return CRUM_OK;
+}
+
+crum_status graph_launch(crum_set* s, int h, crum_image* img, const crum::HashArgs& ha,
+                         const crum::ScanArgs& sa, const crum::GatherArgs& ga) {
+  crum::CaptureGraph& G = s->graph[h];
+  if (G.exec == nullptr || G.epoch != s->graph_epoch) {
+    crum_status st = graph_build(s, h, img, ha, sa, ga);
+    if (st != CRUM_OK) return st;
+  }
+  auto set_kernel = [&](cudaGraphNode_t node, const crum::KernelSpec& sp, void* arg) {
+    void* args[] = {arg};
+    cudaKernelNodeParams kp{};
+    kp.func = const_cast<void*>(sp.func);
+    kp.gridDim = dim3(sp.grid);
+    kp.blockDim = dim3(sp.block);
+    kp.sharedMemBytes = static_cast<unsigned>(sp.smem);
+    kp.kernelParams = args;
+    return cudaGraphExecKernelNodeSetParams(G.exec, node, &kp);
+  };
+  crum::HashArgs ha_c = ha;
+  crum::ScanArgs sa_c = sa;
+  crum::GatherArgs ga_c = ga;
+  cudaError_t e = set_kernel(G.hash, G.hs, &ha_c);
+  if (e == cudaSuccess) e = set_kernel(G.scan, G.ss, &sa_c);
+  if (e == cudaSuccess) e = set_kernel(G.gather, G.gs, &ga_c);
+  if (e == cudaSuccess) e = cudaGraphExecEventRecordNodeSetEvent(G.exec, G.k0, img->ev_k0);
+  if (e == cudaSuccess) e = cudaGraphExecEventRecordNodeSetEvent(G.exec, G.k1, img->ev_k1);
+  if (e == cudaSuccess) e = cudaGraphExecEventRecordNodeSetEvent(G.exec, G.k2, img->ev_k2);
+  if (e == cudaSuccess)
+    e = cudaGraphExecEventRecordNodeSetEvent(G.exec, G.captured, img->ev_captured);
+  if (e == cudaSuccess) e = cudaGraphLaunch(G.exec, s->cap_stream);
+  // back to the placeholders: the launch just queued keeps the image's
+  // events, and the executable graph never refers to an event that may die
+  const cudaGraphNode_t nodes[4] = {G.k0, G.k1, G.k2, G.captured};
+  for (int i = 0; i < 4; ++i) {
+    const cudaError_t r = cudaGraphExecEventRecordNodeSetEvent(G.exec, nodes[i], G.placeholder[i]);
+    if (e == cudaSuccess) e = r;
+  }
+  if (e != cudaSuccess) return fail(CRUM_ECUDA, "capture graph launch: %s", cudaGetErrorString(e));
+  crum::g_kernel_launches.fetch_add(3, std::memory_order_relaxed);
+  return CRUM_OK;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------ PinnedPool ---
@@ -570,6 +696,12 @@ crum_status crum_set_destroy(crum_set* s) {
   cudaStreamSynchronize(s->cap_stream);
   cudaStreamSynchronize(s->drain_stream);
   image_unref(s->last);
+  for (crum::CaptureGraph& G : s->graph) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    if (G.graph) cudaGraphDestroy(G.graph);
+    for (cudaEvent_t ev : G.placeholder)
+      if (ev) cudaEventDestroy(ev);
+  }
   for (Half& H : s->half) {
     cudaFree(H.meta);
     if (!s->cfg.external_staging) cudaFree(H.payload);
@@ -609,6 +741,7 @@ crum_status crum_register(crum_set* s, void* ptr, size_t bytes, uint32_t* alloc_
   s->allocs.push_back(a);
   s->n_pages += a.n_pages;
   s->table_dirty = s->reg_changed = true;
+  s->graph_epoch++;
   if (alloc_id) *alloc_id = a.id;
   return CRUM_OK;
 }
@@ -627,6 +760,7 @@ crum_status crum_unregister(crum_set* s, uint32_t id) {
   }
   s->n_pages = first;
   s->table_dirty = s->reg_changed = true;
+  s->graph_epoch++;
   return CRUM_OK;
 }
 
@@ -761,6 +895,7 @@ crum_status crum_autotune(crum_set* s, int* hash_mapping, int* gather_mapping, d
   if (st != CRUM_OK) return st;
   s->map_hash = best_h;
   s->map_gather = best_g;
+  s->graph_epoch++;
   if (hash_mapping) *hash_mapping = best_h;
   if (gather_mapping) *gather_mapping = best_g;
   return CRUM_OK;
@@ -784,7 +919,8 @@ crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, cr
   if (!s->cv.wait_for(lk, std::chrono::seconds(600), [&] { return H.drain_enqueued; }))
     return fail(CRUM_ETIMEOUT, "timed out waiting for a staging half");
 
-  const bool full = (flags & CRUM_FULL) || s->needs_full || s->reg_changed;
+  const bool full = (flags & CRUM_FULL) || s->needs_full || s->reg_changed ||
+                    (s->cfg.max_chain > 0 && s->chain_len >= static_cast<uint64_t>(s->cfg.max_chain));
   auto* img = new crum_image();
   img->pool = s->pool;
   img->device = s->device;
@@ -824,9 +960,6 @@ crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, cr
                      cudaGetErrorString(cudaGetLastError())));
   if ((st = upload_table(s)) != CRUM_OK) return bail(st);
   const uint64_t words = (s->n_pages + 31) / 32;
-  if (cudaMemsetAsync(s->d_mask, 0, words * sizeof(uint32_t), s->cap_stream) != cudaSuccess ||
-      cudaMemsetAsync(s->d_collisions, 0, 2 * sizeof(unsigned long long), s->cap_stream) != cudaSuccess)
-    return bail(fail(CRUM_ECUDA, "memset failed: %s", cudaGetErrorString(cudaGetLastError())));
 
   crum::HashArgs ha{};
   ha.allocs = s->d_allocs;
@@ -839,15 +972,6 @@ crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, cr
   ha.shadow = s->d_shadow;
   ha.collisions = s->d_collisions;
   ha.error = reinterpret_cast<unsigned int*>(s->d_collisions + 1);
-  cudaError_t ce = cudaEventRecord(img->ev_k0, s->cap_stream);
-  if (ce == cudaSuccess) ce = crum::launch_hash_dirty(ha, s->map_hash, verify, s->cap_stream);
-  if (ce == cudaSuccess) ce = cudaEventRecord(img->ev_k1, s->cap_stream);
-  if (ce != cudaSuccess) return bail(fail(CRUM_ECUDA, "hash launch: %s", cudaGetErrorString(ce)));
-
-  // this half's previous drain must be done before its metadata is rewritten
-  if (cudaStreamWaitEvent(s->cap_stream, H.ev_drained, 0) != cudaSuccess ||
-      cudaEventRecord(img->ev_k2, s->cap_stream) != cudaSuccess)
-    return bail(fail(CRUM_ECUDA, "stream wait failed"));
   crum::ScanArgs sa{};
   sa.mask = s->d_mask;
   sa.n_words = words;
@@ -863,11 +987,6 @@ crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, cr
   sa.seq = img->seq;
   sa.parent_seq = img->parent_seq;
   sa.flags = full ? 1u : 0u;
-  ce = crum::launch_scan(sa, s->cap_stream);
-  if (ce != cudaSuccess) return bail(fail(CRUM_ECUDA, "scan launch: %s", cudaGetErrorString(ce)));
-  if (cudaEventRecord(H.ev_scanned, s->cap_stream) != cudaSuccess)
-    return bail(fail(CRUM_ECUDA, "event record failed"));
-
   crum::GatherArgs ga{};
   ga.allocs = s->d_allocs;
   ga.first_page = s->d_first_page;
@@ -884,34 +1003,56 @@ crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, cr
   // CRUM_VERIFY checkpoint compares against the last checkpointed bytes
   ga.shadow = s->cfg.verify ? s->d_shadow : nullptr;
   const bool gather_shadow = ga.shadow != nullptr;
+  const bool fast = s->n_pages <= s->half_slots;
+  if (!fast && gather_shadow)
+    return bail(fail(CRUM_EINVAL, "verify mode needs staging that holds every page"));
+  if (fast) {
+    ga.payload = H.payload;
+    ga.s_begin = 0;
+    ga.s_end = s->n_pages;
+  }
 
   image_ref(img);  // in-flight reference, dropped by the writer
   s->inflight++;
   H.drain_enqueued = false;
-  if (s->n_pages <= s->half_slots) {
-    ga.payload = H.payload;
-    ga.s_begin = 0;
-    ga.s_end = s->n_pages;
-    ce = crum::launch_gather(ga, s->n_pages, s->map_gather, gather_shadow, s->cap_stream);
-    if (ce == cudaSuccess) ce = cudaEventRecord(img->ev_captured, s->cap_stream);
-    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(app, img->ev_captured, 0);
-    if (ce != cudaSuccess) {
-      cudaEventRecord(H.ev_drained, s->cap_stream);
-      H.drain_enqueued = true;
-      s->inflight--;
-      image_unref(img);
-      return bail(fail(CRUM_ECUDA, "gather: %s", cudaGetErrorString(ce)));
-    }
+  auto unwind = [&](crum_status e) {
+    cudaEventRecord(H.ev_drained, s->cap_stream);
+    H.drain_enqueued = true;
+    s->cv.notify_all();
+    s->inflight--;
+    image_unref(img);
+    return bail(e);
+  };
+  cudaError_t ce = cudaSuccess;
+  if (fast && s->cfg.use_graph && !verify && !s->cfg.external_staging) {
+    // one graph launch for the whole capture sequence
+    st = graph_launch(s, h, img, ha, sa, ga);
+    if (st != CRUM_OK) return unwind(st);
+  } else {
+    ce = cudaMemsetAsync(s->d_mask, 0, words * sizeof(uint32_t), s->cap_stream);
+    if (ce == cudaSuccess)
+      ce = cudaMemsetAsync(s->d_collisions, 0, 2 * sizeof(unsigned long long), s->cap_stream);
+    if (ce == cudaSuccess) ce = cudaEventRecord(img->ev_k0, s->cap_stream);
+    if (ce == cudaSuccess) ce = crum::launch_hash_dirty(ha, s->map_hash, verify, s->cap_stream);
+    if (ce == cudaSuccess) ce = cudaEventRecord(img->ev_k1, s->cap_stream);
+    // this half's previous drain must be done before its metadata is rewritten
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(s->cap_stream, H.ev_drained, 0);
+    if (ce == cudaSuccess) ce = cudaEventRecord(img->ev_k2, s->cap_stream);
+    if (ce == cudaSuccess) ce = crum::launch_scan(sa, s->cap_stream);
+    if (ce == cudaSuccess) ce = cudaEventRecord(H.ev_scanned, s->cap_stream);
+    if (ce == cudaSuccess && fast)
+      ce = crum::launch_gather(ga, s->n_pages, s->map_gather, gather_shadow, s->cap_stream);
+    if (ce == cudaSuccess && fast) ce = cudaEventRecord(img->ev_captured, s->cap_stream);
+    if (ce != cudaSuccess)
+      return unwind(fail(CRUM_ECUDA, "capture launch: %s", cudaGetErrorString(ce)));
+  }
+  if (fast) {
+    ce = cudaStreamWaitEvent(app, img->ev_captured, 0);
+    if (ce != cudaSuccess) return unwind(fail(CRUM_ECUDA, "app wait: %s", cudaGetErrorString(ce)));
     s->next_half = h ^ 1;
     s->plan_q.push_back(img);
     s->plan_cv.notify_one();
   } else {
-    if (gather_shadow) {
-      H.drain_enqueued = true;
-      s->inflight--;
-      image_unref(img);
-      return bail(fail(CRUM_EINVAL, "verify mode needs staging that holds every page"));
-    }
     st = checkpoint_chunked(s, img, app, lk, ga);
     H.drain_enqueued = true;
     s->cv.notify_all();
@@ -927,6 +1068,7 @@ crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, cr
   image_unref(s->last);
   s->last = img;
   s->seq++;
+  s->chain_len = full ? 0 : s->chain_len + 1;
   s->needs_full = false;
   s->reg_changed = false;
   *out = img;
@@ -1246,6 +1388,7 @@ crum_status crum_restore(crum_set* s, const crum_image* chain_end, crum_stream_t
   image_unref(s->last);
   s->last = end;
   s->seq = end->seq + 1;
+  s->chain_len = chain.size() - 1;
   s->needs_full = s->cfg.verify != 0;  // the verify shadow does not hold the restored bytes
   s->reg_changed = false;
   return CRUM_OK;

@@ -29,6 +29,7 @@
 
 #include "crum.h"
 #include "device.cuh"
+#include "kernels.h"
 
 namespace crum {
 
@@ -72,6 +73,24 @@ struct Half {
   cudaEvent_t ev_scanned = nullptr;
   cudaEvent_t ev_drained = nullptr;  // last device->host copy out of this half
   bool drain_enqueued = true;        // host: ev_drained is recorded for its last user
+};
+
+// The capture sequence of one staging half as an instantiated CUDA graph:
+// memset(bitmap), memset(counters), record k0, hash, record k1,
+// wait(half drained), record k2, scan, record scanned, gather,
+// record captured.  Kernel arguments and the per-image events are set on
+// the executable graph before each launch; `epoch` says which registration
+// and buffer layout it was built for.
+struct CaptureGraph {
+  cudaGraph_t graph = nullptr;  // kept: node handles below belong to it
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t k0 = nullptr, k1 = nullptr, k2 = nullptr, captured = nullptr;
+  cudaGraphNode_t hash = nullptr, scan = nullptr, gather = nullptr;
+  KernelSpec hs{}, ss{}, gs{};
+  // events the record nodes hold between launches (an image's events are
+  // set only for its own launch: images, and their events, die earlier)
+  cudaEvent_t placeholder[4] = {nullptr, nullptr, nullptr, nullptr};
+  uint64_t epoch = 0;
 };
 
 }  // namespace crum
@@ -137,8 +156,11 @@ struct crum_set {
   cudaStream_t cap_stream = nullptr, drain_stream = nullptr;
   cudaEvent_t ev_app = nullptr, ev_done = nullptr;
   int map_hash = 1, map_gather = 4;  // defaults until crum_autotune or the config
+  crum::CaptureGraph graph[2];       // per staging half (cfg.use_graph)
+  uint64_t graph_epoch = 1;          // bumped whenever a graph must be rebuilt
   // chain state
   uint64_t seq = 0;
+  uint64_t chain_len = 0;  // incremental images since the newest full one
   crum_image* last = nullptr;
   bool needs_full = true;
   // background threads

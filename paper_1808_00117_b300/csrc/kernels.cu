@@ -17,6 +17,9 @@
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "device.cuh"
 #include "kernels.h"
@@ -603,11 +606,29 @@ int num_sms() {
   return g_num_sms;
 }
 
+// CTAs of `func` resident per SM at once (cached per device and shape).
+int resident_per_sm(const void* func, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, int, size_t, int>, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const auto key = std::make_tuple(func, threads, smem, dev);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  per_sm = std::max(1, per_sm);
+  cache.emplace(key, per_sm);
+  return per_sm;
+}
+
 template <typename K>
 int resident_ctas(K kernel, int threads) {
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
-  return std::max(1, per_sm) * num_sms();
+  return resident_per_sm(reinterpret_cast<const void*>(kernel), threads, 0) * num_sms();
 }
 
 // Grid for `units` groups of a kernel with `groups_per_cta` groups per CTA:
@@ -620,42 +641,33 @@ unsigned grid_for(K kernel, uint64_t units, int groups_per_cta) {
 }
 
 template <int G, int U, bool V>
-cudaError_t launch_hash_t(const HashArgs& a, cudaStream_t st) {
+KernelSpec hash_spec_t(uint64_t n_pages) {
   auto kern = k_hash_dirty<G, U, V>;
-  const unsigned grid = grid_for(kern, a.n_pages, G == 32 ? 8 : 1);
-  kern<<<grid, 256, 0, st>>>(a);
-  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-  return cudaGetLastError();
+  return KernelSpec{reinterpret_cast<const void*>(kern), grid_for(kern, n_pages, G == 32 ? 8 : 1),
+                    256, 0};
 }
-
-template <int G, int U, bool V>
-cudaError_t launch_gather_t(const GatherArgs& a, uint64_t max_slots, cudaStream_t st) {
-  auto kern = k_gather<G, U, V>;
-  const unsigned grid = grid_for(kern, max_slots, G == 32 ? 8 : 1);
-  kern<<<grid, 256, 0, st>>>(a);
-  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-  return cudaGetLastError();
-}
-
-}  // namespace
-
-namespace {
 
 template <int STAGES, int CW>
-cudaError_t launch_hash_bulk_t(const HashArgs& a, cudaStream_t st) {
+cudaError_t hash_bulk_spec_t(uint64_t n_pages, KernelSpec* out) {
   auto kern = k_hash_dirty_bulk<STAGES, CW>;
   constexpr int kThreads = 32 * (CW + 1);
   constexpr int kSmem = STAGES * static_cast<int>(kQuarter);
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+  const cudaError_t e =
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
   if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, kSmem);
-  if (e != cudaSuccess) return e;
-  const uint64_t cap = static_cast<uint64_t>(std::max(1, per_sm)) * num_sms();
-  const unsigned grid = static_cast<unsigned>(std::max<uint64_t>(1, std::min(a.n_pages, cap)));
-  kern<<<grid, kThreads, kSmem, st>>>(a);
-  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-  return cudaGetLastError();
+  const int per_sm = resident_per_sm(reinterpret_cast<const void*>(kern), kThreads, kSmem);
+  const uint64_t cap = static_cast<uint64_t>(per_sm) * num_sms();
+  *out = KernelSpec{reinterpret_cast<const void*>(kern),
+                    static_cast<unsigned>(std::max<uint64_t>(1, std::min(n_pages, cap))), kThreads,
+                    kSmem};
+  return cudaSuccess;
+}
+
+template <int G, int U, bool V>
+KernelSpec gather_spec_t(uint64_t max_slots) {
+  auto kern = k_gather<G, U, V>;
+  return KernelSpec{reinterpret_cast<const void*>(kern), grid_for(kern, max_slots, G == 32 ? 8 : 1),
+                    256, 0};
 }
 
 }  // namespace
@@ -668,14 +680,14 @@ const Mapping kMappings[] = {
 };
 const int kNumMappings = sizeof(kMappings) / sizeof(kMappings[0]);
 
-cudaError_t launch_hash_dirty(const HashArgs& a, int mapping, bool verify, cudaStream_t st) {
-  if (a.n_pages == 0) return cudaSuccess;
+cudaError_t hash_spec(uint64_t n_pages, int mapping, bool verify, KernelSpec* out) {
   // verify mode compares pages against the shadow copy, which only the
   // register mappings do; bulk-copy mappings fall back to mapping 1 there
   if (verify && mapping >= 6) mapping = 1;
-#define CRUM_HASH_CASE(i, G, U)                                               \
-  case i:                                                                     \
-    return verify ? launch_hash_t<G, U, true>(a, st) : launch_hash_t<G, U, false>(a, st);
+#define CRUM_HASH_CASE(i, G, U)                                                       \
+  case i:                                                                             \
+    *out = verify ? hash_spec_t<G, U, true>(n_pages) : hash_spec_t<G, U, false>(n_pages); \
+    return cudaSuccess;
   switch (mapping) {
     CRUM_HASH_CASE(0, 32, 4)
     CRUM_HASH_CASE(1, 32, 8)
@@ -684,30 +696,27 @@ cudaError_t launch_hash_dirty(const HashArgs& a, int mapping, bool verify, cudaS
     CRUM_HASH_CASE(4, 256, 4)
     CRUM_HASH_CASE(5, 256, 8)
     case 6:
-      return launch_hash_bulk_t<4, 8>(a, st);
+      return hash_bulk_spec_t<4, 8>(n_pages, out);
     case 7:
-      return launch_hash_bulk_t<6, 8>(a, st);
+      return hash_bulk_spec_t<6, 8>(n_pages, out);
     case 8:
-      return launch_hash_bulk_t<4, 16>(a, st);
+      return hash_bulk_spec_t<4, 16>(n_pages, out);
     default:
       return cudaErrorInvalidValue;
   }
 #undef CRUM_HASH_CASE
 }
 
-cudaError_t launch_scan(const ScanArgs& a, cudaStream_t st) {
-  k_scan<<<1, kScanThreads, 0, st>>>(a);
-  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-  return cudaGetLastError();
+cudaError_t scan_spec(KernelSpec* out) {
+  *out = KernelSpec{reinterpret_cast<const void*>(k_scan), 1, kScanThreads, 0};
+  return cudaSuccess;
 }
 
-cudaError_t launch_gather(const GatherArgs& a, uint64_t max_slots, int mapping, bool verify,
-                          cudaStream_t st) {
-  if (max_slots == 0) return cudaSuccess;
-#define CRUM_GATHER_CASE(i, G, U)                                                     \
-  case i:                                                                             \
-    return verify ? launch_gather_t<G, U, true>(a, max_slots, st)                     \
-                  : launch_gather_t<G, U, false>(a, max_slots, st);
+cudaError_t gather_spec(uint64_t max_slots, int mapping, bool verify, KernelSpec* out) {
+#define CRUM_GATHER_CASE(i, G, U)                                                              \
+  case i:                                                                                      \
+    *out = verify ? gather_spec_t<G, U, true>(max_slots) : gather_spec_t<G, U, false>(max_slots); \
+    return cudaSuccess;
   switch (mapping) {
     CRUM_GATHER_CASE(0, 32, 4)
     CRUM_GATHER_CASE(1, 32, 8)
@@ -719,6 +728,39 @@ cudaError_t launch_gather(const GatherArgs& a, uint64_t max_slots, int mapping, 
       return cudaErrorInvalidValue;
   }
 #undef CRUM_GATHER_CASE
+}
+
+cudaError_t launch_spec(const KernelSpec& s, void* arg, cudaStream_t st) {
+  void* args[] = {arg};
+  const cudaError_t e = cudaLaunchKernel(s.func, dim3(s.grid), dim3(s.block), args, s.smem, st);
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  return e;
+}
+
+cudaError_t launch_hash_dirty(const HashArgs& a, int mapping, bool verify, cudaStream_t st) {
+  if (a.n_pages == 0) return cudaSuccess;
+  KernelSpec s;
+  const cudaError_t e = hash_spec(a.n_pages, mapping, verify, &s);
+  if (e != cudaSuccess) return e;
+  HashArgs copy = a;
+  return launch_spec(s, &copy, st);
+}
+
+cudaError_t launch_scan(const ScanArgs& a, cudaStream_t st) {
+  KernelSpec s;
+  scan_spec(&s);
+  ScanArgs copy = a;
+  return launch_spec(s, &copy, st);
+}
+
+cudaError_t launch_gather(const GatherArgs& a, uint64_t max_slots, int mapping, bool verify,
+                          cudaStream_t st) {
+  if (max_slots == 0) return cudaSuccess;
+  KernelSpec s;
+  const cudaError_t e = gather_spec(max_slots, mapping, verify, &s);
+  if (e != cudaSuccess) return e;
+  GatherArgs copy = a;
+  return launch_spec(s, &copy, st);
 }
 
 cudaError_t launch_restore(const RestoreArgs& a, cudaStream_t st) {

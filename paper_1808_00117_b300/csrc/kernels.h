@@ -84,6 +84,19 @@ struct RestoreArgs {
   uint64_t* h_table;
 };
 
+// Launch shape of one kernel: launched directly (launch_spec) or added to a
+// CUDA graph as a kernel node whose single parameter is the args struct.
+struct KernelSpec {
+  const void* func;
+  unsigned grid;
+  unsigned block;
+  size_t smem;
+};
+cudaError_t hash_spec(uint64_t n_pages, int mapping, bool verify, KernelSpec* out);
+cudaError_t scan_spec(KernelSpec* out);
+cudaError_t gather_spec(uint64_t max_slots, int mapping, bool verify, KernelSpec* out);
+cudaError_t launch_spec(const KernelSpec& s, void* arg, cudaStream_t st);
+
 cudaError_t launch_hash_dirty(const HashArgs& a, int mapping, bool verify, cudaStream_t st);
 cudaError_t launch_scan(const ScanArgs& a, cudaStream_t st);
 cudaError_t launch_gather(const GatherArgs& a, uint64_t max_slots, int mapping, bool verify,

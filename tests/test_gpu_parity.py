@@ -354,3 +354,62 @@ def test_autotune_keeps_parity():
     e1, *_ = o.checkpoint(host_copies(bufs))
     assert first_diff(b1, e1) is None
     s.destroy()
+
+
+@pytest.mark.parametrize("hm", [1, 6])
+def test_graph_launch_matches_oracle(hm):
+    """Captures launched as one CUDA graph per staging half: same images,
+    phase timings recorded, rebuilt after a registration change."""
+    sizes = RAGGED + [9 * P]
+    bufs = device_buffers(sizes, seed=60 + hm)
+    s = make_set(bufs, use_graph=1, hash_mapping=hm)
+    o = oracle.OracleSet(sizes)
+    for step in range(4):
+        if step:
+            mutate(bufs, sizes, 0.3, seed=600 + step)
+        img, got = _checkpoint_bytes(s)
+        exp, *_ = o.checkpoint(host_copies(bufs))
+        assert first_diff(got, exp) is None, f"step {step}"
+        info = img.info()
+        assert info["t_hash_ms"] > 0 and info["t_compact_ms"] > 0
+    extra = device_buffers([3 * P + 1], seed=99)
+    s.register(extra[0].data_ptr(), extra[0].numel())
+    _, got = _checkpoint_bytes(s)
+    exp, *_ = oracle.OracleSet(sizes + [3 * P + 1]).checkpoint(host_copies(bufs + extra))
+    assert first_diff(got[32:-8], exp[32:-8]) is None and parse_header(got)["flags"] == 1
+    s.destroy()
+
+
+def test_max_chain_bounds_incremental_chains():
+    sizes = [6 * P + 9]
+    bufs = device_buffers(sizes, seed=71)
+    s = make_set(bufs, max_chain=2)
+    o = oracle.OracleSet(sizes)
+    flags = []
+    for step in range(7):
+        if step:
+            mutate(bufs, sizes, 0.5, seed=710 + step)
+        img, got = _checkpoint_bytes(s)
+        full = parse_header(got)["flags"] == 1
+        exp, *_ = o.checkpoint(host_copies(bufs), full=full)
+        assert first_diff(got, exp) is None
+        flags.append(int(full))
+    assert flags == [1, 0, 0, 1, 0, 0, 1]
+    s.destroy()
+
+
+def test_graph_survives_released_images():
+    """Images (and their events) are released between captures; the graph
+    path must not refer to them afterwards."""
+    sizes = [12 * P + 3]
+    bufs = device_buffers(sizes, seed=81)
+    s = make_set(bufs, use_graph=1)
+    o = oracle.OracleSet(sizes)
+    for step in range(6):
+        if step:
+            mutate(bufs, sizes, 0.4, seed=810 + step)
+        img, got = _checkpoint_bytes(s, crum.FULL if step == 3 else crum.INCR)
+        exp, *_ = o.checkpoint(host_copies(bufs), full=(step == 3))
+        assert first_diff(got, exp) is None, f"step {step}"
+        img.release()
+    s.destroy()
