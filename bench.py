@@ -57,6 +57,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-mib", type=int, default=512)
     ap.add_argument("--requests", type=int, default=2000, help="serving workload: request count")
+    ap.add_argument("--mapping", default="",
+                    help="'H,G': fixed hash and gather thread mappings instead of the autotuner")
     ap.add_argument("--graph", type=int, default=1,
                     help="1: launch each capture as one CUDA graph (0: one launch per op)")
     ap.add_argument("--footprint-gib", type=int, default=0,
@@ -323,15 +325,21 @@ def run_ours(args):
     torch.cuda.synchronize()
     staging = 2 * ((n_pages + 1) * W.PAGE)  # two halves that each hold every page
     pool = full_image + (warmup + steps + 2) * incr_image
+    fixed = [int(x) for x in args.mapping.split(",")] if args.mapping else None
     s = crum.CheckpointSet(device=local, staging_bytes=staging, host_pool_bytes=pool,
-                           use_graph=int(args.graph))
+                           use_graph=int(args.graph),
+                           hash_mapping=fixed[0] if fixed else -1,
+                           gather_mapping=fixed[1] if fixed else -1)
     for b in bufs:
         s.register(b.data_ptr(), b.numel())
     stream = torch.cuda.current_stream()
     sh = stream.cuda_stream
     full = s.checkpoint(sh, crum.FULL)
     full.wait()
-    tune = s.autotune()  # untimed: picks the hash and gather thread mappings
+    if fixed:
+        tune = {"hash_mapping": fixed[0], "gather_mapping": fixed[1], "hash_ms": [], "gather_ms": []}
+    else:
+        tune = s.autotune()  # untimed: picks the hash and gather thread mappings
     chain = [full]
     offsets = np.cumsum([0] + [W.pages_of(n) for n in wl.sizes])
 

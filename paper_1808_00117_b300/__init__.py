@@ -263,7 +263,7 @@ class CheckpointSet:
     def autotune(self) -> dict:
         """Pick the fastest hash and gather mappings for the registrations."""
         hm, gm = _I(), _I()
-        ht, gt = (ctypes.c_double * 9)(), (ctypes.c_double * 6)()
+        ht, gt = (ctypes.c_double * 12)(), (ctypes.c_double * 6)()
         _check(load().crum_autotune(self.handle, ctypes.byref(hm), ctypes.byref(gm), ht, gt),
                "crum_autotune")
         return {"hash_mapping": hm.value, "gather_mapping": gm.value,

@@ -136,8 +136,10 @@ __device__ __forceinline__ bool page_differs(const uint8_t* src, const uint8_t* 
   return group_any<G>(diff, sh);
 }
 
-template <int G, int U, bool VERIFY>
-__global__ void __launch_bounds__(256) k_hash_dirty(HashArgs a) {
+// MINB > 1 caps registers so MINB CTAs fit on an SM (more warps, hence more
+// loads in flight, at the cost of registers for the unrolled loads).
+template <int G, int U, bool VERIFY, int MINB = 1>
+__global__ void __launch_bounds__(256, MINB) k_hash_dirty(HashArgs a) {
   __shared__ GroupShared<G> sh;
   constexpr int kGroupsPerCta = (G == 32) ? 256 / 32 : 1;
   const int t = threadIdx.x % G;
@@ -640,9 +642,9 @@ unsigned grid_for(K kernel, uint64_t units, int groups_per_cta) {
   return static_cast<unsigned>(std::max<uint64_t>(1, std::min(need, cap)));
 }
 
-template <int G, int U, bool V>
+template <int G, int U, bool V, int MINB = 1>
 KernelSpec hash_spec_t(uint64_t n_pages) {
-  auto kern = k_hash_dirty<G, U, V>;
+  auto kern = k_hash_dirty<G, U, V, MINB>;
   return KernelSpec{reinterpret_cast<const void*>(kern), grid_for(kern, n_pages, G == 32 ? 8 : 1),
                     256, 0};
 }
@@ -674,9 +676,10 @@ KernelSpec gather_spec_t(uint64_t max_slots) {
 
 // Hash mappings 0-5 are register mappings, 6-8 bulk-copy mappings; gather
 // and restore use the register mappings 0-5 only.
+// 9-11: register mappings capped at 32 registers (8 CTAs of 256 per SM).
 const Mapping kMappings[] = {
-    {32, 4, 0},  {32, 8, 0},  {32, 16, 0},  {256, 2, 0}, {256, 4, 0},
-    {256, 8, 0}, {256, 0, 4}, {256, 0, 6},  {512, 0, 4},
+    {32, 4, 0},  {32, 8, 0},  {32, 16, 0},  {256, 2, 0}, {256, 4, 0}, {256, 8, 0},
+    {256, 0, 4}, {256, 0, 6}, {512, 0, 4},  {32, 4, 0},  {32, 8, 0},  {256, 4, 0},
 };
 const int kNumMappings = sizeof(kMappings) / sizeof(kMappings[0]);
 
@@ -701,6 +704,15 @@ cudaError_t hash_spec(uint64_t n_pages, int mapping, bool verify, KernelSpec* ou
       return hash_bulk_spec_t<6, 8>(n_pages, out);
     case 8:
       return hash_bulk_spec_t<4, 16>(n_pages, out);
+    case 9:
+      *out = hash_spec_t<32, 4, false, 8>(n_pages);
+      return cudaSuccess;
+    case 10:
+      *out = hash_spec_t<32, 8, false, 8>(n_pages);
+      return cudaSuccess;
+    case 11:
+      *out = hash_spec_t<256, 4, false, 8>(n_pages);
+      return cudaSuccess;
     default:
       return cudaErrorInvalidValue;
   }
@@ -765,8 +777,10 @@ cudaError_t launch_gather(const GatherArgs& a, uint64_t max_slots, int mapping, 
 
 cudaError_t launch_restore(const RestoreArgs& a, cudaStream_t st) {
   if (a.n_slots == 0) return cudaSuccess;
-  auto kern = k_restore<32>;
-  const unsigned grid = grid_for(kern, a.n_slots, 8);
+  // one CTA per image slot: restores carry few slots per launch, and a
+  // warp per slot left most of the device idle
+  auto kern = k_restore<256>;
+  const unsigned grid = grid_for(kern, a.n_slots, 1);
   kern<<<grid, 256, 0, st>>>(a);
   g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
