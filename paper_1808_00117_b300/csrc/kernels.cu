@@ -139,7 +139,7 @@ __device__ __forceinline__ bool page_differs(const uint8_t* src, const uint8_t* 
 // MINB > 1 caps registers so MINB CTAs fit on an SM (more warps, hence more
 // loads in flight, at the cost of registers for the unrolled loads).
 template <int G, int U, bool VERIFY, int MINB = 1>
-__global__ void __launch_bounds__(256, MINB) k_hash_dirty(HashArgs a) {
+__global__ void __launch_bounds__(256, (MINB > 1 ? MINB : 0)) k_hash_dirty(HashArgs a) {
   __shared__ GroupShared<G> sh;
   constexpr int kGroupsPerCta = (G == 32) ? 256 / 32 : 1;
   const int t = threadIdx.x % G;
