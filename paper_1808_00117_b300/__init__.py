@@ -213,7 +213,8 @@ class Image:
         return i.as_dict()
 
     def to_bytes(self) -> bytes:
-        self.wait(WAIT_DRAINED)
+        # a failed sink (EIO) leaves the drained bytes usable
+        self.wait(WAIT_DRAINED, allow=(OK, ECOLLISION, EIO))
         n = self.info()["image_bytes"]
         buf = ctypes.create_string_buffer(n)
         _check(load().crum_image_copy(self.handle, buf, n), "crum_image_copy")

@@ -1103,6 +1103,15 @@ crum_status crum_image_wait(crum_image* img, int what, int64_t timeout_ns) {
   return img->status;
 }
 
+// OK once the image's bytes are in host memory, even if its sink failed
+// afterwards (those bytes stay usable for copies, saves and restores).
+static crum_status wait_drained(crum_image* img) {
+  const crum_status st = crum_image_wait(img, CRUM_WAIT_DRAINED, -1);
+  if (st == CRUM_OK || st == CRUM_ECOLLISION) return CRUM_OK;
+  std::lock_guard<std::mutex> lk(img->mu);
+  return img->stage >= CRUM_WAIT_DRAINED ? CRUM_OK : st;
+}
+
 crum_status crum_image_info_get(const crum_image* cimg, crum_image_info* info) {
   if (cimg == nullptr || info == nullptr) return fail(CRUM_EINVAL, "null image or info");
   crum_image* img = const_cast<crum_image*>(cimg);
@@ -1133,8 +1142,8 @@ crum_status crum_image_info_get(const crum_image* cimg, crum_image_info* info) {
 crum_status crum_image_copy(crum_image* img, void* dst, uint64_t dst_bytes) {
   t_err.clear();
   if (img == nullptr || dst == nullptr) return fail(CRUM_EINVAL, "null image or destination");
-  crum_status st = crum_image_wait(img, CRUM_WAIT_DRAINED, -1);
-  if (st != CRUM_OK && st != CRUM_ECOLLISION) return st;
+  crum_status st = wait_drained(img);
+  if (st != CRUM_OK) return st;
   std::lock_guard<std::mutex> lk(img->mu);
   if (img->host == nullptr) return fail(CRUM_EIO, "image payload was dropped (null sink)");
   if (dst_bytes < img->image_bytes) return fail(CRUM_EINVAL, "destination holds %llu of %llu bytes",
@@ -1146,8 +1155,8 @@ crum_status crum_image_copy(crum_image* img, void* dst, uint64_t dst_bytes) {
 crum_status crum_image_save(crum_image* img, const char* path) {
   t_err.clear();
   if (img == nullptr || path == nullptr) return fail(CRUM_EINVAL, "null image or path");
-  crum_status st = crum_image_wait(img, CRUM_WAIT_DRAINED, -1);
-  if (st != CRUM_OK && st != CRUM_ECOLLISION) return st;
+  crum_status st = wait_drained(img);
+  if (st != CRUM_OK) return st;
   if (img->host == nullptr) return fail(CRUM_EIO, "image payload was dropped (null sink)");
   return write_file(img->host, img->image_bytes, path, false);
 }
@@ -1331,8 +1340,8 @@ crum_status crum_restore(crum_set* s, const crum_image* chain_end, crum_stream_t
   std::reverse(chain.begin(), chain.end());
   if (!chain.front()->full) return fail(CRUM_ECORRUPT, "chain has no full base image");
   for (crum_image* img : chain) {
-    const crum_status st = crum_image_wait(img, CRUM_WAIT_DRAINED, -1);
-    if (st != CRUM_OK && st != CRUM_ECOLLISION) return st;
+    const crum_status st = wait_drained(img);
+    if (st != CRUM_OK) return st;
     if (img->host == nullptr) return fail(CRUM_EIO, "image %llu has no payload (null sink)", (unsigned long long)img->seq);
   }
   DeviceGuard dg(s->device);

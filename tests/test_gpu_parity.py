@@ -413,3 +413,22 @@ def test_graph_survives_released_images():
         assert first_diff(got, exp) is None, f"step {step}"
         img.release()
     s.destroy()
+
+
+def test_sink_failure_reports_eio_and_forces_full(tmp_path):
+    """A sink that cannot write (host-made failure): the image still drains
+    and is correct, PERSISTED reports CRUM_EIO, and the set's next
+    checkpoint is full so no chain depends on the unpersisted image."""
+    sizes = [5 * P + 1]
+    bufs = device_buffers(sizes, seed=91)
+    s = make_set(bufs, sink=crum.SINK_FILE, sink_dir=str(tmp_path / "missing" / "dir"))
+    o = oracle.OracleSet(sizes)
+    img = s.checkpoint(stream_handle())
+    assert img.wait(crum.WAIT_PERSISTED, allow=(crum.EIO,)) == crum.EIO
+    exp, *_ = o.checkpoint(host_copies(bufs))
+    assert first_diff(img.to_bytes(), exp) is None  # drained bytes are intact
+    mutate(bufs, sizes, 0.4, seed=92)
+    img2 = s.checkpoint(stream_handle())
+    img2.wait(crum.WAIT_DRAINED, allow=(crum.OK, crum.EIO))
+    assert img2.info()["full"] == 1
+    s.destroy()
