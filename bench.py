@@ -588,24 +588,52 @@ def run_batched(args):
     S, n_pages = wl.total_bytes, wl.n_pages
     steps, warmup = args.steps, max(args.warmup, 3)
     link_peak = link_d2h_peak(torch)
+    stencil = wl.dirty_mode == "stencil"
     bufs = []
-    for i, n in enumerate(wl.sizes):
-        b = torch.empty(n, dtype=torch.uint8, device=dev)
-        W.fill_(b, wl.seed * 7919 + i + 1000 * rank, wl.kind)
-        bufs.append(b)
-    plans = {t: [W.stencil_plan(n, wl.dirty_frac, wl.seed * 1000 + 7 * t + i)
-                 for i, n in enumerate(wl.sizes)] for t in range(1, warmup + steps + 8)}
-    dirty = {t: len(stencil_dirty_pages(wl, plans[t])) for t in plans}
+    if stencil:
+        for i, n in enumerate(wl.sizes):
+            b = torch.empty(n, dtype=torch.uint8, device=dev)
+            W.fill_(b, wl.seed * 7919 + i + 1000 * rank, wl.kind)
+            bufs.append(b)
+        plans = {t: [W.stencil_plan(n, wl.dirty_frac, wl.seed * 1000 + 7 * t + i)
+                     for i, n in enumerate(wl.sizes)] for t in range(1, warmup + steps + 8)}
+        dirty = {t: len(stencil_dirty_pages(wl, plans[t])) for t in plans}
 
-    def app_update(t):
-        for b, plan in zip(bufs, plans[t]):
-            W.stencil_step_(b, plan)
+        def app_update(t):
+            for b, plan in zip(bufs, plans[t]):
+                W.stencil_step_(b, plan)
+    else:
+        # one device tensor carved into the allocations (offsets are 4 KiB
+        # multiples); the application's update is one seeded scatter that
+        # xors a nonzero mask into the first word of every chosen page
+        big = torch.empty(S, dtype=torch.uint8, device=dev)
+        W.fill_(big, wl.seed + 1000 * rank, wl.kind)
+        offs = np.cumsum([0] + list(wl.sizes))
+        bufs = [big[int(offs[i]):int(offs[i + 1])] for i in range(len(wl.sizes))]
+        page_byte = np.concatenate([offs[i] + np.arange(W.pages_of(n), dtype=np.int64) * W.PAGE
+                                    for i, n in enumerate(wl.sizes)])
+        big64 = big.view(torch.int64)
+        scatter, dirty = {}, {}
+        for t in range(1, warmup + steps + 8):
+            chosen = W.choose_step(wl, t, n_pages)
+            gen = np.random.default_rng(wl.seed * 31 + t)
+            masks = gen.integers(1, 2**62, size=chosen.size, dtype=np.int64) | 1
+            scatter[t] = (torch.as_tensor(page_byte[chosen] // 8, device=dev),
+                          torch.as_tensor(masks, device=dev))
+            dirty[t] = int(chosen.size)
+
+        def app_update(t):
+            idx, m = scatter[t]
+            big64[idx] = big64[idx] ^ m
 
     torch.cuda.synchronize()
-    staging = 2 * (n_pages + 1) * W.PAGE
-    max_img = 64 + 16 * len(wl.sizes) + 16 * n_pages + 8 + n_pages * W.PAGE
+    if stencil:
+        staging = 2 * (n_pages + 1) * W.PAGE  # both halves hold every page
+    else:
+        staging = 2 * (int(1.5 * max(dirty.values())) + 1) * W.PAGE  # halves hold a step's pages
+    max_img = 64 + 16 * len(wl.sizes) + 16 * n_pages + 8 + min(n_pages, staging // 2 // W.PAGE) * W.PAGE
     s = crum.CheckpointSet(device=local, staging_bytes=staging, sink=crum.SINK_NULL,
-                           host_pool_bytes=max_img)
+                           host_pool_bytes=max_img if stencil else 3 * max_img)
     for b in bufs:
         s.register(b.data_ptr(), b.numel())
     stream = torch.cuda.current_stream()
@@ -654,8 +682,29 @@ def run_batched(args):
     # batched vs plain P1 at equal bytes: application-stream time from the
     # submit until every dirty page is captured, staging idle beforehand
     p1_steps = min(3, steps)
+    p1_what = "one set (hash, scan and gather launches) per allocation"
     p1_sets = []
-    for b in bufs:
+    if not stencil:
+        # thousands of one-allocation sets would need two host threads each;
+        # compare the hash pass alone: one launch over the flattened page list
+        # against one launch per allocation, same thread mapping (1)
+        p1_what = "hash pass only: one launch per allocation vs one batched launch (mapping 1)"
+        out = torch.empty(n_pages, dtype=torch.int64, device=dev)
+        plain_ms_hash = []
+        for j in range(p1_steps):
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            g = 0
+            for b in bufs:
+                crum.hash_pages(b.data_ptr(), b.numel(), out[g:].data_ptr(), sh)
+                g += W.pages_of(b.numel())
+            a1.record(stream)
+            torch.cuda.synchronize()
+            plain_ms_hash.append(a0.elapsed_time(a1))
+        # the set's own batched hash over the flattened list, same mapping
+        batched_ms_hash = [tune["hash_ms"][1]] * p1_steps
+        del out
+    for b in (bufs if stencil else []):
         n_b = W.pages_of(b.numel())
         ps = crum.CheckpointSet(device=local, staging_bytes=2 * (n_b + 1) * W.PAGE,
                                 sink=crum.SINK_NULL, hash_mapping=tune["hash_mapping"],
@@ -664,8 +713,10 @@ def run_batched(args):
         ps.checkpoint(sh, crum.FULL).wait()
         p1_sets.append(ps)
     batched_ms, plain_ms = [], []
+    if not stencil:
+        batched_ms, plain_ms = batched_ms_hash, plain_ms_hash
     base_t = warmup + steps + 1
-    for j in range(p1_steps):
+    for j in range(p1_steps if stencil else 0):
         app_update(base_t + j)
         torch.cuda.synchronize()
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -711,7 +762,7 @@ def run_batched(args):
                        "captured_p99": pct([i["t_captured_ms"] for i in infos], 99),
                        "drained_p50": pct([i["t_drained_ms"] for i in infos], 50),
                        "drained_p99": pct([i["t_drained_ms"] for i in infos], 99)},
-        "batched_vs_plain_p1": {"steps": p1_steps,
+        "batched_vs_plain_p1": {"steps": p1_steps, "what": p1_what,
                                 "batched_capture_ms": [round(x, 3) for x in batched_ms],
                                 "plain_p1_capture_ms": [round(x, 3) for x in plain_ms],
                                 "speedup": round(statistics.mean(plain_ms) / statistics.mean(batched_ms), 3)},

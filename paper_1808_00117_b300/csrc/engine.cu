@@ -199,6 +199,17 @@ crum_status upload_table(crum_set* s) {
   return CRUM_OK;
 }
 
+// Host address the payload of slots [s0, ...) lands at.  A null-sink image
+// drains its payload across the link into one bounce region of at most a
+// staging half (chunks of a chunked capture reuse it in stream order), so a
+// full checkpoint of a footprint larger than host memory can still be timed.
+uint8_t* payload_dst(crum_image* img, uint64_t s0) {
+  const uint64_t meta = meta_bytes(img->n_allocs, img->n_dirty);
+  return img->host + meta + (img->drop_payload ? 0 : s0 * kPage);
+}
+
+uint8_t* trailer_dst(crum_image* img) { return img->host + img->host_len - 8; }
+
 // Queue the device->host copies of a captured image from half H into its
 // pinned host buffer, on the drain stream.
 crum_status enqueue_drain(crum_set* s, crum_image* img, Half& H) {
@@ -208,10 +219,9 @@ crum_status enqueue_drain(crum_set* s, crum_image* img, Half& H) {
   CK(cudaMemcpyAsync(img->host, H.meta, meta_bytes(A, n), cudaMemcpyDeviceToHost, s->drain_stream));
   // the null sink drains too (the bytes cross the link); the writer drops them
   if (n > 0)
-    CK(cudaMemcpyAsync(img->host + meta_bytes(A, n), H.payload, n * kPage, cudaMemcpyDeviceToHost,
+    CK(cudaMemcpyAsync(payload_dst(img, 0), H.payload, n * kPage, cudaMemcpyDeviceToHost,
                        s->drain_stream));
-  CK(cudaMemcpyAsync(img->host + img->image_bytes - 8, H.scalars + 1, 8, cudaMemcpyDeviceToHost,
-                     s->drain_stream));
+  CK(cudaMemcpyAsync(trailer_dst(img), H.scalars + 1, 8, cudaMemcpyDeviceToHost, s->drain_stream));
   CK(cudaEventRecord(img->ev_drained, s->drain_stream));
   CK(cudaEventRecord(H.ev_drained, s->drain_stream));
   return CRUM_OK;
@@ -219,9 +229,10 @@ crum_status enqueue_drain(crum_set* s, crum_image* img, Half& H) {
 
 crum_status alloc_image_host(crum_set* s, crum_image* img) {
   img->image_bytes = image_size(img->n_allocs, img->n_dirty);
-  // null sink: the payload still crosses the link, into a pooled buffer that
-  // is handed back as soon as the drain ends
   img->host_len = img->image_bytes;
+  if (img->drop_payload)
+    img->host_len = meta_bytes(img->n_allocs, img->n_dirty) +
+                    std::min<uint64_t>(img->n_dirty, s->half_slots) * kPage + 8;
   img->host = s->pool->alloc(img->host_len);
   if (img->host == nullptr) return fail(CRUM_ENOMEM, "pinned host pool exhausted (%zu bytes)", img->host_len);
   return CRUM_OK;
@@ -318,7 +329,7 @@ void writer_main(crum_set* s) {
         img->t_compact_ms = ms;
       if (cudaEventElapsedTime(&ms, img->ev_d0, img->ev_drained) == cudaSuccess)
         img->t_drain_ms = ms;
-      std::memcpy(&img->checksum, img->host + img->image_bytes - 8, 8);
+      std::memcpy(&img->checksum, trailer_dst(img), 8);
       image_set_stage(img, CRUM_WAIT_DRAINED, img->collisions ? CRUM_ECOLLISION : CRUM_OK, "");
       if (img->drop_payload) {
         std::lock_guard<std::mutex> lk(img->mu);
@@ -385,18 +396,18 @@ crum_status checkpoint_chunked(crum_set* s, crum_image* img, cudaStream_t app,
     CK(cudaEventRecord(ev, s->cap_stream));
     CK(cudaStreamWaitEvent(s->drain_stream, ev, 0));
     CK(cudaEventDestroy(ev));  // released once the recorded work completes
-    CK(cudaMemcpyAsync(img->host + meta_bytes(A, n) + s0 * kPage, H.payload, (s1 - s0) * kPage,
-                       cudaMemcpyDeviceToHost, s->drain_stream));
+    if (s0 == 0) CK(cudaEventRecord(img->ev_d0, s->drain_stream));  // drain starts here
+    CK(cudaMemcpyAsync(payload_dst(img, s0), H.payload, (s1 - s0) * kPage, cudaMemcpyDeviceToHost,
+                       s->drain_stream));
     CK(cudaEventRecord(H.ev_drained, s->drain_stream));
     h ^= 1;
   }
   CK(cudaEventRecord(img->ev_captured, s->cap_stream));
   CK(cudaStreamWaitEvent(app, img->ev_captured, 0));
   CK(cudaStreamWaitEvent(s->drain_stream, img->ev_captured, 0));
-  CK(cudaEventRecord(img->ev_d0, s->drain_stream));
+  if (n == 0) CK(cudaEventRecord(img->ev_d0, s->drain_stream));  // no payload chunk was copied
   CK(cudaMemcpyAsync(img->host, H0.meta, meta_bytes(A, n), cudaMemcpyDeviceToHost, s->drain_stream));
-  CK(cudaMemcpyAsync(img->host + img->image_bytes - 8, H0.scalars + 1, 8, cudaMemcpyDeviceToHost,
-                     s->drain_stream));
+  CK(cudaMemcpyAsync(trailer_dst(img), H0.scalars + 1, 8, cudaMemcpyDeviceToHost, s->drain_stream));
   CK(cudaEventRecord(img->ev_drained, s->drain_stream));
   CK(cudaEventRecord(s->half[0].ev_drained, s->drain_stream));
   CK(cudaEventRecord(s->half[1].ev_drained, s->drain_stream));
