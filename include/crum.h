@@ -165,6 +165,10 @@ crum_status crum_autotune(crum_set *set, int *hash_mapping, int *gather_mapping,
 #define CRUM_INCR   0  /* pages whose hash changed, plus never-checkpointed pages */
 #define CRUM_FULL   1  /* every page */
 #define CRUM_VERIFY 2  /* also byte-compare hash-clean pages (needs cfg.verify) */
+#define CRUM_NO_PAYLOAD 4  /* drain this image's payload across the link but keep only
+                              its metadata on the host (as the null sink does): for a
+                              base image larger than host memory that only has to set
+                              the hashes; a chain through it cannot be restored (EIO) */
 
 /* Take a checkpoint of every registered allocation as of this point in
    app_stream's order.  The capture runs on the set's own streams after the

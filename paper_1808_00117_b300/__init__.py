@@ -23,7 +23,7 @@ __all__ = [
 
 PAGE_SIZE = 65536
 NO_PARENT = 0xFFFFFFFFFFFFFFFF
-INCR, FULL, VERIFY = 0, 1, 2
+INCR, FULL, VERIFY, NO_PAYLOAD = 0, 1, 2, 4
 WAIT_CAPTURED, WAIT_DRAINED, WAIT_PERSISTED = 1, 2, 3
 SINK_MEMORY, SINK_FILE, SINK_NULL = 0, 1, 2
 

@@ -945,7 +945,7 @@ crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, cr
   for (const Alloc& a : s->allocs) img->table.emplace_back(a.id, a.bytes);
   img->half = h;
   img->t_submit = std::chrono::steady_clock::now();
-  img->drop_payload = s->cfg.sink == CRUM_SINK_NULL;
+  img->drop_payload = s->cfg.sink == CRUM_SINK_NULL || (flags & CRUM_NO_PAYLOAD) != 0;
   img->do_fsync = s->cfg.fsync != 0;
   if (s->cfg.sink == CRUM_SINK_FILE) {
     char name[96];

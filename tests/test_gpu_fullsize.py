@@ -132,3 +132,61 @@ def test_stencil_full_size():
     assert np.array_equal(s.hashes(), oracle_hashes(hosts))
     img.release()
     s.destroy()
+
+
+def test_large_4096_allocations_sampled():
+    """The 140 GiB / 4,096-allocation footprint: the base image is drained
+    without keeping its payload (it exceeds host memory); two incremental
+    steps of a seeded 2 % scatter are checked: page table in full, the image
+    checksum by the oracle's checker, sampled payload slots, and committed
+    hashes on a seeded sample of pages against the oracle."""
+    t = torch()
+    free, _ = t.cuda.mem_get_info()
+    wl = W.workload("large")
+    if free < wl.total_bytes + (24 << 30):
+        pytest.skip("needs about 165 GB of free device memory")
+    S = wl.total_bytes
+    big = t.empty(S, dtype=t.uint8, device="cuda")
+    W.fill_(big, wl.seed, wl.kind)
+    offs = np.cumsum([0] + list(wl.sizes))
+    bufs = [big[int(offs[i]):int(offs[i + 1])] for i in range(len(wl.sizes))]
+    first = np.cumsum([0] + [W.pages_of(n) for n in wl.sizes])
+    page_alloc = np.repeat(np.arange(len(wl.sizes)), np.diff(first))
+    page_local = np.arange(wl.n_pages) - first[page_alloc]
+    k = int(round(wl.dirty_frac * wl.n_pages))
+    s = crum.CheckpointSet(staging_bytes=2 * (int(1.5 * k) + 1) * P)
+    for b in bufs:
+        s.register(b.data_ptr(), b.numel())
+    s.checkpoint(stream_handle(), crum.FULL | crum.NO_PAYLOAD).wait()
+    big64 = big.view(t.int64)
+    rng = np.random.default_rng(3)
+    for step in (1, 2):
+        chosen = W.choose_step(wl, step, wl.n_pages)
+        words = (offs[page_alloc[chosen]] + page_local[chosen] * P) // 8
+        idx = t.as_tensor(words, device="cuda")
+        big64[idx] = big64[idx] ^ t.as_tensor(rng.integers(1, 2**62, size=chosen.size) | 1,
+                                              device="cuda")
+        img = s.checkpoint(stream_handle())
+        img.wait()
+        b = img.to_bytes()
+        pt = page_table(b)
+        assert pt[:, 0].tolist() == page_alloc[chosen].tolist()
+        assert pt[:, 1].tolist() == page_local[chosen].tolist()
+        assert oracle.check_image(b) == oracle.OK
+        h = parse_header(b)
+        hashes = s.hashes()
+        for slot in rng.choice(h["n"], size=64, replace=False):
+            a, p = int(pt[slot, 0]), int(pt[slot, 1])
+            lo = int(offs[a]) + p * P
+            n_valid = min(P, int(wl.sizes[a]) - p * P)
+            page = big[lo:lo + n_valid].cpu().numpy()
+            got = np.frombuffer(b, dtype=np.uint8, count=P, offset=h["poff"] + int(slot) * P)
+            assert np.array_equal(got[:n_valid], page)
+        for g in rng.choice(wl.n_pages, size=512, replace=False):
+            a = int(page_alloc[g])
+            lo = int(offs[a]) + int(page_local[g]) * P
+            n_valid = min(P, int(wl.sizes[a]) - int(page_local[g]) * P)
+            assert int(hashes[g]) == oracle.page_hash(big[lo:lo + n_valid].cpu().numpy())
+        img.release()
+    s.destroy()
+    del big
