@@ -286,6 +286,15 @@ crum_status crum_poke_hash(crum_set *set, uint64_t global_page, uint64_t value);
 /* Kernel launches the library has issued since load (for launch accounting). */
 uint64_t crum_kernel_launches(void);
 
+/* Self-test of the bounded device waits: hashes [ptr, ptr+bytes) (device
+   pointer, 16-byte aligned, at least one full page) with a shared-memory
+   bulk-copy mapping whose producer deliberately never issues one chunk, so
+   the consumers' wait for it runs out after limit_ns (clamped to 1 ms..10 s).
+   *timed_out receives 1 if the kernel reported the timeout and finished.
+   The device stays usable afterwards.  Synchronous.  Errors: EINVAL, ECUDA. */
+crum_status crum_selftest_wait_timeout(const void *ptr, uint64_t bytes, uint64_t limit_ns,
+                                       int *timed_out, crum_stream_t stream);
+
 /* ---- serving: checkpoint/restore requests from many clients ----
    The paper checkpoints each MPI rank's process (Sections 3.3-3.4); here a
    server takes checkpoint and restore requests from many clients as they

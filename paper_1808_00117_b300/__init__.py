@@ -120,6 +120,7 @@ SIGNATURES = {
     "crum_get_hashes": ([_VP, _VP, _U64], _I),
     "crum_poke_hash": ([_VP, _U64, _U64], _I),
     "crum_kernel_launches": ([], _U64),
+    "crum_selftest_wait_timeout": ([_VP, _U64, _U64, ctypes.POINTER(_I), _VP], _I),
     "crum_dirty_pages_static": ([_VP, _U64, _VP, _I, _VP, _VP, _VP], _I),
     "crum_server_create": ([ctypes.POINTER(ServerConfig), ctypes.POINTER(_VP)], _I),
     "crum_server_destroy": ([_VP], _I),
@@ -194,6 +195,15 @@ def dirty_pages_static(ptr: int, nbytes: int, hashes_ptr: int, full: bool, pages
     library (its scratch is a fixed device array; see include/crum.h)."""
     _check(load().crum_dirty_pages_static(ptr, nbytes, hashes_ptr, int(bool(full)), pages_out_ptr,
                                           count_out_ptr, stream), "crum_dirty_pages_static")
+
+
+def selftest_wait_timeout(ptr: int, nbytes: int, limit_ns: int, stream: int = 0) -> bool:
+    """Run the bounded-wait self-test (one bulk copy is never issued);
+    True if the kernel reported that its wait ran out and finished."""
+    flag = ctypes.c_int(-1)
+    _check(load().crum_selftest_wait_timeout(ptr, nbytes, limit_ns, ctypes.byref(flag), stream),
+           "crum_selftest_wait_timeout")
+    return flag.value == 1
 
 
 class Image:

@@ -1484,3 +1484,39 @@ crum_status bind_staging(crum_set* s, uint8_t* payload, uint64_t slots) {
   return CRUM_OK;
 }
 }  // namespace crum
+
+extern "C" crum_status crum_selftest_wait_timeout(const void* ptr, uint64_t bytes, uint64_t limit_ns,
+                                                  int* timed_out, crum_stream_t stream) {
+  t_err.clear();
+  if (ptr == nullptr || timed_out == nullptr || bytes < kPage)
+    return fail(CRUM_EINVAL, "needs a device pointer to at least one full page");
+  if (reinterpret_cast<uintptr_t>(ptr) % 16 != 0) return fail(CRUM_EINVAL, "pointer not 16-byte aligned");
+  limit_ns = std::min<uint64_t>(std::max<uint64_t>(limit_ns, 1000000ull), 10000000000ull);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint64_t n = pages_of(bytes);
+  uint64_t* out = nullptr;
+  unsigned int* flag = nullptr;
+  CK(cudaMalloc(&out, n * sizeof(uint64_t)));
+  if (cudaMalloc(&flag, sizeof(unsigned int)) != cudaSuccess) {
+    cudaFree(out);
+    return fail(CRUM_ENOMEM, "cannot allocate the self-test flag");
+  }
+  crum::HashArgs ha{};
+  ha.one = DevAlloc{static_cast<uint8_t*>(const_cast<void*>(ptr)), bytes, 0, 0, static_cast<uint32_t>(n)};
+  ha.n_allocs = 1;
+  ha.n_pages = n;
+  ha.h_out = out;
+  ha.error = flag;
+  ha.wait_limit_ns = limit_ns;
+  ha.test_skip_chunk = 1;  // CTA 0 never issues its first quarter page
+  unsigned int host_flag = 0;
+  cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(unsigned int), st);
+  if (e == cudaSuccess) e = crum::launch_hash_dirty(ha, 6, false, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&host_flag, flag, sizeof host_flag, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(out);
+  cudaFree(flag);
+  if (e != cudaSuccess) return fail(CRUM_ECUDA, "self-test: %s", cudaGetErrorString(e));
+  *timed_out = host_flag != 0 ? 1 : 0;
+  return CRUM_OK;
+}

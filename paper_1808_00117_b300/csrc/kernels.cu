@@ -437,9 +437,17 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
 
 // true once the barrier's phase with this parity has completed; false if the
 // bounded number of polls ran out or *stop became nonzero.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Waits for at most `limit_ns` (globaltimer) and kWaitLimit polls.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
-                                          const volatile int* stop) {
+                                          const volatile int* stop, uint64_t limit_ns) {
   const uint32_t addr = smem_u32(bar);
+  const uint64_t deadline = global_ns() + limit_ns;
   for (uint32_t i = 0; i < kWaitLimit; ++i) {
     uint32_t done;
     asm volatile(
@@ -450,7 +458,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
         : "r"(addr), "r"(parity)
         : "memory");
     if (done) return true;
-    if ((i & 1023u) == 1023u && stop != nullptr && *stop) return false;
+    if ((i & 255u) == 255u) {
+      if (stop != nullptr && *stop) return false;
+      if (global_ns() > deadline) return false;
+    }
   }
   return false;
 }
@@ -476,6 +487,7 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_hash_dirty_bulk(HashArgs a) {
   __shared__ uint64_t red[CW];
   __shared__ int stop;
   constexpr int kConsumers = 32 * CW;
+  const uint64_t limit_ns = a.wait_limit_ns != 0 ? a.wait_limit_ns : 2000000000ull;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -490,7 +502,10 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_hash_dirty_bulk(HashArgs a) {
   if (warp == 0) {
     // ---- producer ----
     if (lane != 0) return;
-    uint32_t chunk = 0, issued = 0;
+    uint32_t chunk = 0;
+    int last_issued[STAGES];  // newest chunk issued into each stage, -1: none
+#pragma unroll
+    for (int s = 0; s < STAGES; ++s) last_issued[s] = -1;
     bool ok = true;
     for (uint64_t g = blockIdx.x; ok && g < a.n_pages; g += gridDim.x) {
       const uint8_t* base;
@@ -510,22 +525,29 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_hash_dirty_bulk(HashArgs a) {
       const uint8_t* src = base + p * kPage;
       for (uint32_t q = 0; q < 4; ++q, ++chunk) {
         const uint32_t s = chunk % STAGES, k = chunk / STAGES;
-        if (k > 0 && !mbar_wait(&empty_bar[s], (k - 1) & 1, &stop)) {
+        if (k > 0 && !mbar_wait(&empty_bar[s], (k - 1) & 1, &stop, limit_ns)) {
           ok = false;
           break;
         }
+        // self-test hook: one chunk is never issued, so its consumers' wait
+        // runs out (a flag nothing sets)
+        if (a.test_skip_chunk != 0 && blockIdx.x == 0 && chunk + 1 == a.test_skip_chunk) continue;
         mbar_arrive_expect_tx(&full_bar[s], kQuarter);
         bulk_load(ring + s * kQuarter, src + q * kQuarter, kQuarter, &full_bar[s]);
-        ++issued;
+        last_issued[s] = static_cast<int>(chunk);
       }
     }
     if (!ok) {
       if (a.error) atomicExch(a.error, 1u);
       stop = 1;
-      // let the copies already issued land before the CTA can retire
-      for (uint32_t c = (issued > STAGES ? issued - STAGES : 0); c < issued; ++c)
-        mbar_wait(&full_bar[c % STAGES], (c / STAGES) & 1, nullptr);
     }
+    // The CTA must not retire with a copy into its shared memory in flight,
+    // also when the consumers gave up on it: wait for the newest copy of
+    // every stage (bounded as well).
+    for (uint32_t s = 0; s < STAGES; ++s)
+      if (last_issued[s] >= 0)
+        mbar_wait(&full_bar[s], (static_cast<uint32_t>(last_issued[s]) / STAGES) & 1, nullptr,
+                  limit_ns);
     return;
   }
 
@@ -555,7 +577,10 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_hash_dirty_bulk(HashArgs a) {
     if (valid == kPage) {
       for (uint32_t q = 0; q < 4; ++q, ++chunk) {
         const uint32_t s = chunk % STAGES, k = chunk / STAGES;
-        if (bad || !mbar_wait(&full_bar[s], k & 1, &stop)) {
+        bool got = false;
+        if (!bad) got = mbar_wait(&full_bar[s], k & 1, &stop, limit_ns);
+        // warp-uniform, so the warp's later collectives see all 32 lanes
+        if (!__all_sync(0xffffffffu, got)) {
           bad = true;
           stop = 1;  // the producer stops issuing at its next poll
           continue;
@@ -577,7 +602,8 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_hash_dirty_bulk(HashArgs a) {
     consumer_sync(kConsumers);
     if (lane == 0) red[cw] = h;
     consumer_sync(kConsumers);
-    if (ct == 0 && !bad) {
+    // `stop` is set before the barrier by any warp that gave up on this page
+    if (ct == 0 && !*static_cast<volatile int*>(&stop)) {
       uint64_t total = 0;
 #pragma unroll
       for (int w = 0; w < CW; ++w) total += red[w];

@@ -38,6 +38,8 @@ struct HashArgs {
   const uint8_t* shadow;  // verify mode: last checkpointed bytes, page g at g*64 KiB
   unsigned long long* collisions;
   unsigned int* error;    // bulk-copy mappings: set to 1 if a bounded wait ran out (optional)
+  uint64_t wait_limit_ns;     // bulk-copy mappings: bound of each wait (0: 2 s)
+  uint32_t test_skip_chunk;   // self-test only: CTA 0 never issues chunk n-1 (0: off)
 };
 
 struct ScanArgs {

@@ -432,3 +432,68 @@ def test_sink_failure_reports_eio_and_forces_full(tmp_path):
     img2.wait(crum.WAIT_DRAINED, allow=(crum.OK, crum.EIO))
     assert img2.info()["full"] == 1
     s.destroy()
+
+
+@pytest.mark.gpu
+def test_bounded_wait_runs_out_and_device_stays_usable():
+    """A bulk copy that is never issued (a flag nothing sets): the waiting
+    consumers give up after the limit, the kernel reports it and returns,
+    and the same process then checkpoints bit-exactly."""
+    import time
+    sizes = [40 * P + 24]
+    bufs = device_buffers(sizes, seed=95)
+    t0 = time.perf_counter()
+    assert crum.selftest_wait_timeout(bufs[0].data_ptr(), bufs[0].numel(), 50_000_000, stream_handle())
+    assert time.perf_counter() - t0 < 5.0
+    with pytest.raises(crum.CrumError):
+        crum.selftest_wait_timeout(bufs[0].data_ptr() + 8, bufs[0].numel() - 8, 50_000_000)
+    s = make_set(bufs, hash_mapping=6)
+    o = oracle.OracleSet(sizes)
+    for step in range(2):
+        if step:
+            mutate(bufs, sizes, 0.3, seed=96)
+        img, got = _checkpoint_bytes(s)
+        exp, *_ = o.checkpoint(host_copies(bufs))
+        assert first_diff(got, exp) is None, f"step {step}"
+        img.release()
+    s.destroy()
+
+
+@pytest.mark.gpu
+def test_sink_lost_mid_chain_keeps_earlier_images(tmp_path):
+    """The writer's directory disappears after two persisted images (the
+    host-side stand-in for a writer that died): later images report EIO,
+    the two earlier files still load and restore the state they captured."""
+    sizes = [9 * P + 5, 3 * P]
+    d = tmp_path / "sink"
+    d.mkdir()
+    bufs = device_buffers(sizes, seed=97)
+    s = make_set(bufs, sink=crum.SINK_FILE, sink_dir=str(d))
+    states = []
+    for step in range(2):
+        if step:
+            mutate(bufs, sizes, 0.5, seed=98)
+        img = s.checkpoint(stream_handle())
+        img.wait(crum.WAIT_PERSISTED)
+        states.append(host_copies(bufs))
+        img.release()
+    kept = tmp_path / "kept"
+    d.rename(kept)
+    mutate(bufs, sizes, 0.5, seed=99)
+    img = s.checkpoint(stream_handle())
+    assert img.wait(crum.WAIT_PERSISTED, allow=(crum.EIO,)) == crum.EIO
+    img.release()
+    files = sorted(kept.iterdir(), key=lambda x: int(x.stem.rsplit("_", 1)[1]))
+    assert len(files) == 2
+    chain = []
+    for f, want in zip(files, states):
+        chain.append(s.load_image(str(f), chain[-1] if chain else None))
+        W.fill_(bufs[0], 4242, "u32")
+        W.fill_(bufs[1], 4243, "u32")
+        s.restore(chain[-1], stream_handle())
+        torch().cuda.synchronize()
+        got = host_copies(bufs)
+        assert all(np.array_equal(g, w) for g, w in zip(got, want)), f.name
+    for c in chain:
+        c.release()
+    s.destroy()
