@@ -415,6 +415,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     restore_ms = r0.elapsed_time(r1)
     restore_bytes = sum(img.info()["n_dirty"] for img in chain) * W.PAGE
+    restore_images = len(chain)
 
     # plain form P0 (Section 3.4): synchronize, then copy every allocation whole
     host_plain = torch.empty(S, dtype=torch.uint8, pin_memory=True)
@@ -477,11 +478,14 @@ def run_ours(args):
                        "persisted_p50": pct([i["t_persisted_ms"] for i in infos], 50),
                        "persisted_p99": pct([i["t_persisted_ms"] for i in infos], 99),
                        "n": len(infos)},
-        "restore": {"images": len(chain), "ms": round(restore_ms, 3),
+        "restore": {"images": restore_images, "ms": round(restore_ms, 3),
                     "payload_bytes": restore_bytes,
                     "gbs": round(restore_bytes / (restore_ms * 1e-3) / 1e9, 2)},
         "plain_p0": {"ms": round(plain_ms, 3), "gbs": round(S / (plain_ms * 1e-3) / 1e9, 2),
                      "what": "synchronize + full device->host copy of the footprint"},
+        "whole_step": {"gbs": round(world * S / (total_ms / steps * 1e-3) / 1e9, 2),
+                       "what": "footprint bytes / wall-clock ms per step; each step also drains "
+                               "its dirty pages over the host link"},
         "clocks": clk,
         "gpu_launches": int(launches),
         "cpu_baseline": cpu,

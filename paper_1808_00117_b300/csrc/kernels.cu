@@ -161,6 +161,10 @@ __global__ void __launch_bounds__(256, (MINB > 1 ? MINB : 0)) k_hash_dirty(HashA
     const uint64_t p = g - first;
     const uint8_t* src = base + p * kPage;
     const uint32_t valid = dev::valid_bytes(bytes, p);
+    // the committed hash is loaded before the page so that its latency hides
+    // under the page's loads instead of following them
+    uint64_t prev = 0;
+    if (a.h_out == nullptr && t == 0 && !a.full) prev = a.h_table[g];
     uint64_t h = (valid == kPage) ? hash_full_page<G, U>(src, t) : hash_tail_page<G>(src, valid, t);
     h = group_sum<G>(h, sh);
     if (a.h_out != nullptr) {
@@ -168,7 +172,7 @@ __global__ void __launch_bounds__(256, (MINB > 1 ? MINB : 0)) k_hash_dirty(HashA
       continue;
     }
     int d = 0;
-    if (t == 0) d = a.full || h != a.h_table[g];
+    if (t == 0) d = a.full || h != prev;
     if constexpr (VERIFY) {
       d = group_bcast0<G>(d, sh);
       if (!d && page_differs<G>(src, a.shadow + g * kPage, valid, t, sh)) {
@@ -573,6 +577,8 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_hash_dirty_bulk(HashArgs a) {
     }
     const uint64_t p = g - first;
     const uint32_t valid = dev::valid_bytes(bytes, p);
+    uint64_t prev = 0;  // committed hash, loaded early (see k_hash_dirty)
+    if (a.h_out == nullptr && ct == 0 && !a.full) prev = a.h_table[g];
     uint64_t h = 0;
     if (valid == kPage) {
       for (uint32_t q = 0; q < 4; ++q, ++chunk) {
@@ -610,7 +616,7 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_hash_dirty_bulk(HashArgs a) {
       if (a.h_out != nullptr) {
         a.h_out[g] = total;
       } else {
-        const bool d = a.full || total != a.h_table[g];
+        const bool d = a.full || total != prev;
         a.h_table[g] = total;
         if (d) atomicOr(a.dirty_mask + (g >> 5), 1u << (g & 31));
       }
