@@ -404,16 +404,28 @@ def run_ours(args):
     achieved = hash_bytes / (mean_hash * 1e-3) / 1e9
     drain_gbs = statistics.mean(b / (t * 1e-3) / 1e9 for b, t in zip(drained_bytes, drain_ms))
 
-    # restore of the chain end (full image + every incremental) onto garbage
+    # restore of the chain end (full image + every incremental) onto
+    # garbage, in both forms: merged (the set's automatic choice for this
+    # chain: every page once, from its newest image) and replay (every
+    # image in turn, through a second set on the same allocations)
+    def timed_restore(target):
+        for b in bufs:
+            W.fill_(b, 4242, "u32")
+        torch.cuda.synchronize()
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0.record(stream)
+        target.restore(chain[-1], sh)
+        r1.record(stream)
+        torch.cuda.synchronize()
+        return r0.elapsed_time(r1)
+
+    replay_set = crum.CheckpointSet(device=local, staging_bytes=2 << 30,
+                                    restore_mode=crum.RESTORE_REPLAY)
     for b in bufs:
-        W.fill_(b, 4242, "u32")
-    torch.cuda.synchronize()
-    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    r0.record(stream)
-    s.restore(chain[-1], sh)
-    r1.record(stream)
-    torch.cuda.synchronize()
-    restore_ms = r0.elapsed_time(r1)
+        replay_set.register(b.data_ptr(), b.numel())
+    replay_ms = timed_restore(replay_set)
+    replay_set.destroy()
+    restore_ms = timed_restore(s)  # leaves the set's memory at the chain end
     restore_bytes = sum(img.info()["n_dirty"] for img in chain) * W.PAGE
     restore_images = len(chain)
 
@@ -478,9 +490,14 @@ def run_ours(args):
                        "persisted_p50": pct([i["t_persisted_ms"] for i in infos], 50),
                        "persisted_p99": pct([i["t_persisted_ms"] for i in infos], 99),
                        "n": len(infos)},
-        "restore": {"images": restore_images, "ms": round(restore_ms, 3),
-                    "payload_bytes": restore_bytes,
-                    "gbs": round(restore_bytes / (restore_ms * 1e-3) / 1e9, 2)},
+        "restore": {"images": restore_images, "form": "merged", "ms": round(restore_ms, 3),
+                    "chain_payload_bytes": restore_bytes, "link_bytes": S,
+                    "chain_gbs": round(restore_bytes / (restore_ms * 1e-3) / 1e9, 2),
+                    "link_gbs": round(S / (restore_ms * 1e-3) / 1e9, 2),
+                    "replay_ms": round(replay_ms, 3),
+                    "replay_link_gbs": round(restore_bytes / (replay_ms * 1e-3) / 1e9, 2),
+                    "what": "chain end restored onto garbage; chain_gbs = the chain's payload "
+                            "bytes / ms (what replaying the chain would move)"},
         "plain_p0": {"ms": round(plain_ms, 3), "gbs": round(S / (plain_ms * 1e-3) / 1e9, 2),
                      "what": "synchronize + full device->host copy of the footprint"},
         "whole_step": {"gbs": round(world * S / (total_ms / steps * 1e-3) / 1e9, 2),
@@ -503,60 +520,95 @@ def run_ours(args):
 
 def run_e2e(torch, crum, W, s, bufs, wl, steps, sh, stream, step0, dist, dev, world):
     """Public API end to end: each step copies the application's new page
-    contents host->device from pinned memory, checkpoints, and waits until
-    the image is persisted in host memory (its bytes crossed device->host).
-    Each image is released once persisted, so the pinned pool is reused."""
+    contents host->device from pinned memory, checkpoints, and reads the
+    image back (PERSISTED: its bytes crossed device->host).  Two forms, each
+    step holding its own uploads and its own image drain:
+    - pipelined (the value): step k+1's upload is issued before waiting for
+      image k, so the upload and the previous drain share the full-duplex
+      link, as an application that keeps running while its checkpoint
+      drains would;
+    - serial: each step waits for its image before the next upload.
+    Images are released once persisted, so the pinned pool is reused."""
     n_pages = wl.n_pages
     k = int(round(wl.dirty_frac * n_pages))
     gen = torch.Generator(device="cpu")
     gen.manual_seed(wl.seed + 99)
     new = torch.randint(0, 256, (k, W.PAGE), dtype=torch.uint8, generator=gen).pin_memory()
     n_full = bufs[0].numel() // W.PAGE
-    flat_new = new.view(-1)
+    pages_view = bufs[0][:n_full * W.PAGE].view(n_full, W.PAGE)
+    landing = torch.empty((k, W.PAGE), dtype=torch.uint8, device=dev)
     plan = []
-    for step in range(steps + 2):
+    for step in range(2 * steps + 4):
         p = W.choose_step(wl, step0 + step, n_pages)
-        p = p[p < n_full]
-        # contiguous runs of chosen pages: (first page, page count)
-        cut = np.flatnonzero(np.diff(p) != 1) + 1
-        plan.append([(int(r[0]), int(r.size)) for r in np.split(p, cut) if r.size])
-    h2d, d2h = [], []
+        plan.append(torch.as_tensor(p[p < n_full], device=dev))
 
-    def one(runs):
-        # the application writes its new page contents into place, one
-        # pinned host->device copy per contiguous run of pages
-        m = 0
-        for first, count in runs:
-            dst = bufs[0][first * W.PAGE:(first + count) * W.PAGE]
-            dst.copy_(flat_new[m * W.PAGE:(m + count) * W.PAGE], non_blocking=True)
-            m += count
-        im = s.checkpoint(sh)
+    def upload(idx):
+        # the application's new page contents: one pinned host->device copy
+        # of the step's pages, then a device scatter into place
+        m = int(idx.numel())
+        landing[:m].copy_(new[:m], non_blocking=True)
+        pages_view.index_copy_(0, idx, landing[:m])
+        return m * W.PAGE
+
+    def finish(im, infos):
         im.wait()
-        nbytes = im.info()["image_bytes"]
+        infos.append(im.info())
         im.release()
-        return m * W.PAGE, nbytes
 
-    # untimed: a fresh full image starts a new chain, so the previous chain
-    # (kept alive by its newest image) is freed and its pinned memory reused
-    im = s.checkpoint(sh, crum.FULL)
-    im.wait()
-    im.release()
-    for warm in range(2):
-        one(plan[warm])
-    barrier(dist)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for step in range(steps):
-        a, b = one(plan[2 + step])
-        h2d.append(a)
-        d2h.append(b)
-    torch.cuda.synchronize()
-    dt = max_over_ranks(dist, time.perf_counter() - t0, dev)
-    return {"value": round(world * wl.total_bytes * steps / dt / 1e9, 2), "unit": UNIT,
+    def fresh_chain():
+        # untimed: a fresh full image starts a new chain, so the previous
+        # chain (kept alive by its newest image) is freed and its pinned
+        # memory reused
+        im = s.checkpoint(sh, crum.FULL)
+        im.wait()
+        im.release()
+
+    def timed(first_step, pipelined):
+        h2d, infos, ev = [], [], []
+        for warm in range(2):
+            upload(plan[first_step + warm])
+            finish(s.checkpoint(sh), [])
+        barrier(dist)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        prev = None
+        for step in range(steps):
+            u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            u0.record(stream)
+            h2d.append(upload(plan[first_step + 2 + step]))
+            u1.record(stream)
+            ev.append((u0, u1))
+            im = s.checkpoint(sh)
+            if pipelined:
+                if prev is not None:
+                    finish(prev, infos)
+                prev = im
+            else:
+                finish(im, infos)
+        if prev is not None:
+            finish(prev, infos)
+        torch.cuda.synchronize()
+        dt = max_over_ranks(dist, time.perf_counter() - t0, dev)
+        return dt, h2d, infos, statistics.mean(a.elapsed_time(b) for a, b in ev)
+
+    fresh_chain()
+    dt, h2d, infos, up_ms = timed(0, True)
+    fresh_chain()
+    dt_s, _, infos_s, up_ms_s = timed(steps + 2, False)
+    per = lambda x: round(world * wl.total_bytes * steps / x / 1e9, 2)
+    return {"value": per(dt), "unit": UNIT,
             "h2d_bytes_per_step": int(statistics.mean(h2d)),
-            "d2h_bytes_per_step": int(statistics.mean(d2h)),
+            "d2h_bytes_per_step": int(statistics.mean(i["image_bytes"] for i in infos)),
             "ms_per_step": round(dt * 1e3 / steps, 3),
-            "what": "pinned H2D of the step's new pages + crum_checkpoint + wait PERSISTED"}
+            "what": "pinned H2D of the step's new pages + crum_checkpoint + image read back "
+                    "(PERSISTED); step k+1's upload overlaps image k's drain",
+            "submit_to_persisted_ms": round(statistics.mean(i["t_persisted_ms"] for i in infos), 3),
+            "upload_ms": round(up_ms, 3),
+            "serial": {"value": per(dt_s), "ms_per_step": round(dt_s * 1e3 / steps, 3),
+                       "upload_ms": round(up_ms_s, 3),
+                       "submit_to_persisted_ms":
+                           round(statistics.mean(i["t_persisted_ms"] for i in infos_s), 3),
+                       "what": "each step waits for its image before the next upload"}}
 
 
 def stencil_dirty_pages(wl, plans):

@@ -106,6 +106,11 @@ typedef struct crum_config {
                                   checkpoint is full, so restore replays at most
                                   max_chain + 1 images and older chains can be freed;
                                   0: chains grow without limit */
+    int restore_mode;          /* crum_restore of a chain: 0 auto (merged when the
+                                  chain's incrementals hold more than 8 % of the
+                                  base's pages), 1 replay every image in order,
+                                  2 merged: every page once, from the newest image
+                                  holding it */
 } crum_config;
 
 /* Fill *cfg with defaults (device 0, 1 GiB staging, 64 MiB chunks, memory sink). */
@@ -250,6 +255,12 @@ crum_status crum_image_release(crum_image *img);
 /* Restore the set's registered allocations to the state captured by
    chain_end: the chain's full base image first, then each incremental in
    order, later pages winning.  Only each page's valid bytes are written.
+   Two forms with the same result (crum_config.restore_mode): replay copies
+   each image's payload to the device in turn (sum of the chain's payloads
+   over the link, by DMA); merged finds the newest image of every page on
+   the device and copies each page once, read by the kernels straight from
+   the images' pinned host memory (one footprint over the link at the
+   link's read rate, about 7 % below DMA).
    The set's hash table becomes the chain's hashes, so the next incremental
    checkpoint is relative to chain_end (its parent).  Stream ordered on
    `stream`; returns once the work is queued, and the caller's host image

@@ -26,6 +26,7 @@ NO_PARENT = 0xFFFFFFFFFFFFFFFF
 INCR, FULL, VERIFY, NO_PAYLOAD = 0, 1, 2, 4
 WAIT_CAPTURED, WAIT_DRAINED, WAIT_PERSISTED = 1, 2, 3
 SINK_MEMORY, SINK_FILE, SINK_NULL = 0, 1, 2
+RESTORE_AUTO, RESTORE_REPLAY, RESTORE_MERGED = 0, 1, 2
 
 STATUS = {0: "CRUM_OK", 1: "CRUM_EINVAL", 2: "CRUM_ENOMEM", 3: "CRUM_EBUSY", 4: "CRUM_ECUDA",
           5: "CRUM_EIO", 6: "CRUM_EMISMATCH", 7: "CRUM_ECOLLISION", 8: "CRUM_ETIMEOUT",
@@ -43,7 +44,7 @@ class Config(ctypes.Structure):
                 ("verify", ctypes.c_int), ("fsync", ctypes.c_int),
                 ("hash_mapping", ctypes.c_int), ("gather_mapping", ctypes.c_int),
                 ("external_staging", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("max_chain", ctypes.c_int)]
+                ("max_chain", ctypes.c_int), ("restore_mode", ctypes.c_int)]
 
 
 class ServerConfig(ctypes.Structure):

@@ -199,13 +199,28 @@ crum_status upload_table(crum_set* s) {
   return CRUM_OK;
 }
 
-// Host address the payload of slots [s0, ...) lands at.  A null-sink image
-// drains its payload across the link into one bounce region of at most a
-// staging half (chunks of a chunked capture reuse it in stream order), so a
-// full checkpoint of a footprint larger than host memory can still be timed.
-uint8_t* payload_dst(crum_image* img, uint64_t s0) {
-  const uint64_t meta = meta_bytes(img->n_allocs, img->n_dirty);
-  return img->host + meta + (img->drop_payload ? 0 : s0 * kPage);
+constexpr uint64_t kBounceBytes = 256ull << 20;  // 4,096 pages
+
+// Queues the device->host copy of `bytes` of payload (slots from s0 on) on
+// the drain stream: into the image's own buffer, or, when the image keeps no
+// payload, through the set's bounce region so that a footprint larger than
+// host memory can still be drained and timed.
+crum_status drain_payload(crum_set* s, crum_image* img, uint64_t s0, const uint8_t* src,
+                          uint64_t bytes) {
+  if (!img->drop_payload) {
+    CK(cudaMemcpyAsync(img->host + meta_bytes(img->n_allocs, img->n_dirty) + s0 * kPage, src, bytes,
+                       cudaMemcpyDeviceToHost, s->drain_stream));
+    return CRUM_OK;
+  }
+  {
+    std::lock_guard<std::mutex> lk(s->bounce_mu);
+    if (s->bounce == nullptr) s->bounce = s->pool->alloc(kBounceBytes);
+    if (s->bounce == nullptr) return fail(CRUM_ENOMEM, "pinned host pool exhausted (bounce region)");
+  }
+  for (uint64_t off = 0; off < bytes; off += kBounceBytes)
+    CK(cudaMemcpyAsync(s->bounce, src + off, std::min(kBounceBytes, bytes - off),
+                       cudaMemcpyDeviceToHost, s->drain_stream));
+  return CRUM_OK;
 }
 
 uint8_t* trailer_dst(crum_image* img) { return img->host + img->host_len - 8; }
@@ -218,9 +233,10 @@ crum_status enqueue_drain(crum_set* s, crum_image* img, Half& H) {
   CK(cudaEventRecord(img->ev_d0, s->drain_stream));
   CK(cudaMemcpyAsync(img->host, H.meta, meta_bytes(A, n), cudaMemcpyDeviceToHost, s->drain_stream));
   // the null sink drains too (the bytes cross the link); the writer drops them
-  if (n > 0)
-    CK(cudaMemcpyAsync(payload_dst(img, 0), H.payload, n * kPage, cudaMemcpyDeviceToHost,
-                       s->drain_stream));
+  if (n > 0) {
+    const crum_status st = drain_payload(s, img, 0, H.payload, n * kPage);
+    if (st != CRUM_OK) return st;
+  }
   CK(cudaMemcpyAsync(trailer_dst(img), H.scalars + 1, 8, cudaMemcpyDeviceToHost, s->drain_stream));
   CK(cudaEventRecord(img->ev_drained, s->drain_stream));
   CK(cudaEventRecord(H.ev_drained, s->drain_stream));
@@ -230,9 +246,7 @@ crum_status enqueue_drain(crum_set* s, crum_image* img, Half& H) {
 crum_status alloc_image_host(crum_set* s, crum_image* img) {
   img->image_bytes = image_size(img->n_allocs, img->n_dirty);
   img->host_len = img->image_bytes;
-  if (img->drop_payload)
-    img->host_len = meta_bytes(img->n_allocs, img->n_dirty) +
-                    std::min<uint64_t>(img->n_dirty, s->half_slots) * kPage + 8;
+  if (img->drop_payload) img->host_len = meta_bytes(img->n_allocs, img->n_dirty) + 8;
   img->host = s->pool->alloc(img->host_len);
   if (img->host == nullptr) return fail(CRUM_ENOMEM, "pinned host pool exhausted (%zu bytes)", img->host_len);
   return CRUM_OK;
@@ -364,6 +378,48 @@ crum_status new_image_events(crum_image* img) {
 
 // Captures in staging-sized chunks when the set has more pages than one
 // staging half holds.  The dirty count is read on the host first.
+// Restore of a whole chain in two launches (see k_chain_owner and
+// k_restore_merged): every page once, from the newest image holding it.
+crum_status restore_merged(crum_set* s, const std::vector<crum::ChainImage>& ci,
+                           uint64_t total_slots) {
+  if (s->owner_cap < s->n_pages) {
+    cudaFree(s->d_owner);
+    s->d_owner = nullptr;
+    s->owner_cap = 0;
+    CK(cudaMalloc(&s->d_owner, s->n_pages * sizeof(uint64_t)));
+    s->owner_cap = s->n_pages;
+  }
+  if (s->chain_cap < ci.size()) {
+    cudaFree(s->d_chain);
+    s->d_chain = nullptr;
+    s->chain_cap = 0;
+    CK(cudaMalloc(&s->d_chain, ci.size() * sizeof(crum::ChainImage)));
+    s->chain_cap = ci.size();
+  }
+  // pageable source: staged by the runtime before the call returns
+  CK(cudaMemcpyAsync(s->d_chain, ci.data(), ci.size() * sizeof(crum::ChainImage),
+                     cudaMemcpyHostToDevice, s->cap_stream));
+  CK(cudaMemsetAsync(s->d_owner, 0, s->n_pages * sizeof(uint64_t), s->cap_stream));
+  crum::OwnerArgs oa{};
+  oa.allocs = s->d_allocs;
+  oa.n_allocs = static_cast<uint32_t>(s->allocs.size());
+  oa.images = s->d_chain;
+  oa.n_images = static_cast<uint32_t>(ci.size());
+  oa.total_slots = total_slots;
+  oa.owner = s->d_owner;
+  CK(crum::launch_chain_owner(oa, s->cap_stream));
+  crum::MergedRestoreArgs ma{};
+  ma.allocs = s->d_allocs;
+  ma.first_page = s->d_first_page;
+  ma.n_allocs = oa.n_allocs;
+  ma.n_pages = s->n_pages;
+  ma.images = s->d_chain;
+  ma.owner = s->d_owner;
+  ma.h_table = s->d_h;
+  CK(crum::launch_restore_merged(ma, s->cap_stream));
+  return CRUM_OK;
+}
+
 crum_status checkpoint_chunked(crum_set* s, crum_image* img, cudaStream_t app,
                                std::unique_lock<std::mutex>& lk, const crum::GatherArgs& base) {
   Half& H0 = s->half[img->half];
@@ -397,8 +453,7 @@ crum_status checkpoint_chunked(crum_set* s, crum_image* img, cudaStream_t app,
     CK(cudaStreamWaitEvent(s->drain_stream, ev, 0));
     CK(cudaEventDestroy(ev));  // released once the recorded work completes
     if (s0 == 0) CK(cudaEventRecord(img->ev_d0, s->drain_stream));  // drain starts here
-    CK(cudaMemcpyAsync(payload_dst(img, s0), H.payload, (s1 - s0) * kPage, cudaMemcpyDeviceToHost,
-                       s->drain_stream));
+    if ((st = drain_payload(s, img, s0, H.payload, (s1 - s0) * kPage)) != CRUM_OK) return st;
     CK(cudaEventRecord(H.ev_drained, s->drain_stream));
     h ^= 1;
   }
@@ -569,7 +624,8 @@ uint8_t* PinnedPool::alloc(size_t n) {
   size = std::max(size, std::min(std::max(reserved_, size_t(4) << 20), size_t(256) << 20));
   size = (size + (size_t(2) << 20) - 1) & ~((size_t(2) << 20) - 1);
   uint8_t* p = nullptr;
-  if (cudaHostAlloc(reinterpret_cast<void**>(&p), size, cudaHostAllocPortable) != cudaSuccess) {
+  if (cudaHostAlloc(reinterpret_cast<void**>(&p), size, cudaHostAllocPortable | cudaHostAllocMapped) !=
+      cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
@@ -645,6 +701,7 @@ crum_status crum_set_create(const crum_config* cfg_in, crum_set** out) {
   if (cfg.hash_mapping < -1 || cfg.hash_mapping >= crum::kNumMappings ||
       cfg.gather_mapping < -1 || cfg.gather_mapping > 5)
     return fail(CRUM_EINVAL, "mapping out of range");
+  if (cfg.restore_mode < 0 || cfg.restore_mode > 2) return fail(CRUM_EINVAL, "bad restore_mode");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg.device < 0 || cfg.device >= ndev) {
     cudaGetLastError();
@@ -706,6 +763,7 @@ crum_status crum_set_destroy(crum_set* s) {
   if (s->writer.joinable()) s->writer.join();
   cudaStreamSynchronize(s->cap_stream);
   cudaStreamSynchronize(s->drain_stream);
+  if (s->bounce != nullptr) s->pool->free(s->bounce, kBounceBytes);
   image_unref(s->last);
   for (crum::CaptureGraph& G : s->graph) {
     if (G.exec) cudaGraphExecDestroy(G.exec);
@@ -728,6 +786,8 @@ crum_status crum_set_destroy(crum_set* s) {
   cudaFree(s->d_word_offset);
   cudaFree(s->d_collisions);
   cudaFree(s->d_shadow);
+  cudaFree(s->d_owner);
+  cudaFree(s->d_chain);
   cudaEventDestroy(s->ev_app);
   cudaEventDestroy(s->ev_done);
   cudaStreamDestroy(s->cap_stream);
@@ -1364,15 +1424,40 @@ crum_status crum_restore(crum_set* s, const crum_image* chain_end, crum_stream_t
         return fail(CRUM_EMISMATCH, "allocation %zu: image %llu bytes, set %llu bytes", a,
                     (unsigned long long)img->table[a].second, (unsigned long long)s->allocs[a].bytes);
   }
-  if (s->half_slots == 0) return fail(CRUM_EINVAL, "no staging bound to this set");
+  const uint64_t A = s->allocs.size();
+  // merged when the incrementals would carry more than 8 % of the base's
+  // pages a second time (kernel reads of host memory run ~7 % below DMA)
+  uint64_t incr_pages = 0;
+  for (size_t i = 1; i < chain.size(); ++i) incr_pages += chain[i]->n_dirty;
+  bool merged = s->cfg.restore_mode == 2 ||
+                (s->cfg.restore_mode == 0 && incr_pages * 100 > 8 * chain.front()->n_dirty);
+  std::vector<crum::ChainImage> ci;
+  uint64_t total_slots = 0;
+  for (size_t i = 0; merged && i < chain.size(); ++i) {
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, chain[i]->host) != cudaSuccess || pa.devicePointer == nullptr) {
+      cudaGetLastError();
+      if (s->cfg.restore_mode == 2)
+        return fail(CRUM_EINVAL, "image %llu is not in device-mapped host memory",
+                    (unsigned long long)chain[i]->seq);
+      merged = false;
+      break;
+    }
+    const uint8_t* d = static_cast<const uint8_t*>(pa.devicePointer);
+    const uint64_t n = chain[i]->n_dirty;
+    ci.push_back(crum::ChainImage{d + kHeaderBytes + 16 * A, d + kHeaderBytes + 16 * A + 8 * n,
+                                  d + meta_bytes(A, n), total_slots});
+    total_slots += n;
+  }
+  if (!merged && s->half_slots == 0) return fail(CRUM_EINVAL, "no staging bound to this set");
   crum_status st = ensure_capacity(s, lk);
   if (st != CRUM_OK) return st;
   CK(cudaEventRecord(s->ev_app, us));
   CK(cudaStreamWaitEvent(s->cap_stream, s->ev_app, 0));
   if ((st = upload_table(s)) != CRUM_OK) return st;
-  const uint64_t A = s->allocs.size();
+  if (merged && (st = restore_merged(s, ci, total_slots)) != CRUM_OK) return st;
   int h = s->next_half;
-  for (crum_image* img : chain) {
+  for (crum_image* img : (merged ? std::vector<crum_image*>{} : chain)) {
     const uint64_t n = img->n_dirty;
     const uint8_t* ptab = img->host + kHeaderBytes + 16 * A;
     const uint8_t* hashes = ptab + 8 * n;

@@ -150,6 +150,10 @@ struct crum_set {
   unsigned long long* d_collisions = nullptr;
   uint8_t* d_shadow = nullptr;
   size_t shadow_cap = 0;  // pages
+  uint64_t* d_owner = nullptr;  // merged restore: newest image slot of each page
+  size_t owner_cap = 0;         // pages
+  crum::ChainImage* d_chain = nullptr;
+  size_t chain_cap = 0;         // images
   crum::Half half[2];
   int next_half = 0;
   uint64_t half_slots = 0;
@@ -165,6 +169,11 @@ struct crum_set {
   bool needs_full = true;
   // background threads
   std::shared_ptr<crum::PinnedPool> pool;
+  // pinned landing region of every payload that is not kept (null sink,
+  // CRUM_NO_PAYLOAD): its bytes still cross the link, in region-sized
+  // copies on the drain stream, and are overwritten by the next copy
+  uint8_t* bounce = nullptr;
+  std::mutex bounce_mu;
   std::deque<crum_image*> plan_q, write_q;
   std::condition_variable plan_cv, write_cv;
   std::thread planner, writer;

@@ -385,6 +385,58 @@ __global__ void __launch_bounds__(256) k_restore(RestoreArgs a) {
   }
 }
 
+// ----------------------------------------------- merged (last-writer) restore ---
+//
+// A chain base..end restored page by page from the newest image that holds
+// each page, so every page crosses the link once however long the chain.
+// The images stay in pinned host memory; both kernels read them there.
+
+constexpr uint64_t kSlotMask = (1ull << 40) - 1;
+
+__global__ void __launch_bounds__(256) k_chain_owner(OwnerArgs a) {
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  for (uint64_t j = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+       j < a.total_slots; j += stride) {
+    uint32_t lo = 0, hi = a.n_images;  // image holding global slot j, in [lo, hi)
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (a.images[mid].slot0 <= j)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    const uint64_t s = j - a.images[lo].slot0;
+    const uint2 e = *reinterpret_cast<const uint2*>(a.images[lo].ptab + 8 * s);
+    if (e.x >= a.n_allocs || e.y >= a.allocs[e.x].n_pages) continue;  // rejected on the host already
+    const uint64_t g = a.allocs[e.x].first_page + e.y;
+    // later images carry larger tags, so the maximum is the last writer
+    atomicMax(reinterpret_cast<unsigned long long*>(a.owner + g),
+              static_cast<unsigned long long>((static_cast<uint64_t>(lo) + 1) << 40 | s));
+  }
+}
+
+__global__ void __launch_bounds__(256) k_restore_merged(MergedRestoreArgs a) {
+  for (uint64_t g = blockIdx.x; g < a.n_pages; g += gridDim.x) {
+    const uint64_t o = a.owner[g];
+    if (o == 0) continue;  // no image of the chain holds this page
+    const ChainImage& im = a.images[(o >> 40) - 1];
+    const uint64_t s = o & kSlotMask;
+    const uint32_t k = dev::find_alloc(a.first_page, a.n_allocs, g);
+    const uint64_t p = g - a.allocs[k].first_page;
+    uint8_t* dst = a.allocs[k].base + p * kPage;
+    const uint8_t* src = im.payload + s * kPage;
+    const uint32_t valid = dev::valid_bytes(a.allocs[k].bytes, p);
+    const uint32_t nvec = valid >> 4;
+    // plain loads: the source is host memory behind the link
+    for (uint32_t v = threadIdx.x; v < nvec; v += blockDim.x)
+      reinterpret_cast<uint4*>(dst)[v] = reinterpret_cast<const uint4*>(src)[v];
+    const uint32_t rem = valid & 15u;
+    if (rem != 0 && threadIdx.x == 0)
+      for (uint32_t b = 0; b < rem; ++b) dst[16ull * nvec + b] = src[16ull * nvec + b];
+    if (threadIdx.x == 0) a.h_table[g] = reinterpret_cast<const uint64_t*>(im.hashes)[s];
+  }
+}
+
 // ------------------------------------------------------------ hash bytes ---
 
 __global__ void __launch_bounds__(256) k_hash_bytes(const uint8_t* p, uint64_t n,
@@ -814,6 +866,26 @@ cudaError_t launch_restore(const RestoreArgs& a, cudaStream_t st) {
   auto kern = k_restore<256>;
   const unsigned grid = grid_for(kern, a.n_slots, 1);
   kern<<<grid, 256, 0, st>>>(a);
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chain_owner(const OwnerArgs& a, cudaStream_t st) {
+  if (a.total_slots == 0 || a.n_images == 0) return cudaSuccess;
+  const uint64_t cap = static_cast<uint64_t>(resident_ctas(k_chain_owner, 256));
+  const unsigned grid =
+      static_cast<unsigned>(std::max<uint64_t>(1, std::min((a.total_slots + 255) / 256, cap)));
+  k_chain_owner<<<grid, 256, 0, st>>>(a);
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restore_merged(const MergedRestoreArgs& a, cudaStream_t st) {
+  if (a.n_pages == 0) return cudaSuccess;
+  // one CTA per page; any shape that keeps a few MB of reads in flight
+  // saturates the link
+  const unsigned grid = grid_for(k_restore_merged, a.n_pages, 1);
+  k_restore_merged<<<grid, 256, 0, st>>>(a);
   g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }

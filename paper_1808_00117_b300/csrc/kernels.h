@@ -86,6 +86,36 @@ struct RestoreArgs {
   uint64_t* h_table;
 };
 
+// One image of a restore chain as the device sees it: pointers into the
+// image's pinned host buffer (mapped, read by the kernels across the link).
+struct ChainImage {
+  const uint8_t* ptab;     // 2 u32 per slot: allocation index, page index
+  const uint8_t* hashes;   // u64 per slot
+  const uint8_t* payload;  // slot s at payload + s * 64 KiB
+  uint64_t slot0;          // slots of the images before this one
+};
+
+// owner[g] = (image + 1) << 40 | slot of the newest chain image holding
+// page g; 0 if no image holds it (pre-zeroed).
+struct OwnerArgs {
+  const DevAlloc* allocs;
+  uint32_t n_allocs;
+  const ChainImage* images;  // device, base first
+  uint32_t n_images;
+  uint64_t total_slots;
+  uint64_t* owner;
+};
+
+struct MergedRestoreArgs {
+  const DevAlloc* allocs;
+  const uint64_t* first_page;
+  uint32_t n_allocs;
+  uint64_t n_pages;
+  const ChainImage* images;
+  const uint64_t* owner;
+  uint64_t* h_table;
+};
+
 // Launch shape of one kernel: launched directly (launch_spec) or added to a
 // CUDA graph as a kernel node whose single parameter is the args struct.
 struct KernelSpec {
@@ -104,6 +134,8 @@ cudaError_t launch_scan(const ScanArgs& a, cudaStream_t st);
 cudaError_t launch_gather(const GatherArgs& a, uint64_t max_slots, int mapping, bool verify,
                           cudaStream_t st);
 cudaError_t launch_restore(const RestoreArgs& a, cudaStream_t st);
+cudaError_t launch_chain_owner(const OwnerArgs& a, cudaStream_t st);
+cudaError_t launch_restore_merged(const MergedRestoreArgs& a, cudaStream_t st);
 cudaError_t launch_hash_bytes(const uint8_t* p, uint64_t n, uint64_t first_index, uint64_t* out,
                               cudaStream_t st);
 

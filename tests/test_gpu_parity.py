@@ -497,3 +497,69 @@ def test_sink_lost_mid_chain_keeps_earlier_images(tmp_path):
     for c in chain:
         c.release()
     s.destroy()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("mode", [crum.RESTORE_REPLAY, crum.RESTORE_MERGED, crum.RESTORE_AUTO])
+def test_chain_restore_forms_agree(mode):
+    """Replay (every image in turn) and merged (every page once, from the
+    newest image holding it) restore the same bytes and hashes: chain ends
+    restored in a non-monotonic order onto garbage, over ragged allocations."""
+    sizes = RAGGED
+    bufs = device_buffers(sizes, seed=61)
+    s = make_set(bufs, restore_mode=mode)
+    o = oracle.OracleSet(sizes)
+    chain, states, hashes = [], [], []
+    for step in range(5):
+        if step:
+            mutate(bufs, sizes, 0.35, seed=620 + step)
+        img = s.checkpoint(stream_handle())
+        img.wait()
+        chain.append(img)
+        states.append(host_copies(bufs))
+        _, _, h, _ = o.checkpoint(states[-1])
+        hashes.append(h)
+    for k in (4, 2, 0, 3):
+        for i, b in enumerate(bufs):
+            W.fill_(b, 5000 + 17 * k + i, "u32")
+        s.restore(chain[k], stream_handle())
+        torch().cuda.synchronize()
+        got = host_copies(bufs)
+        assert all(np.array_equal(g, w) for g, w in zip(got, states[k])), f"chain end {k}"
+        assert np.array_equal(s.hashes(), hashes[k]), f"hashes after chain end {k}"
+    img = s.checkpoint(stream_handle())
+    img.wait()
+    info = img.info()
+    assert info["n_dirty"] == 0 and info["parent_seq"] == chain[3].info()["seq"]
+    img.release()
+    for c in chain:
+        c.release()
+    s.destroy()
+
+
+@pytest.mark.gpu
+def test_merged_restore_of_images_from_bytes():
+    """Images rebuilt from their bytes (new pinned buffers) restore through
+    the merged form; a chain whose newest image rewrote every page."""
+    sizes = [3 * P + 40, 7 * P]
+    bufs = device_buffers(sizes, seed=63)
+    s = make_set(bufs, restore_mode=crum.RESTORE_MERGED)
+    blobs, states = [], []
+    for step in range(3):
+        if step:
+            mutate(bufs, sizes, 1.0 if step == 2 else 0.5, seed=640 + step)
+        img, b = _checkpoint_bytes(s)
+        blobs.append(b)
+        states.append(host_copies(bufs))
+        img.release()
+    chain = []
+    for b in blobs:
+        chain.append(s.image_from_bytes(b, chain[-1] if chain else None))
+    for i, b in enumerate(bufs):
+        W.fill_(b, 6400 + i, "u32")
+    s.restore(chain[-1], stream_handle())
+    torch().cuda.synchronize()
+    assert all(np.array_equal(g, w) for g, w in zip(host_copies(bufs), states[-1]))
+    for c in chain:
+        c.release()
+    s.destroy()
