@@ -246,6 +246,37 @@ def oracle_sample_run(sample_mib: int, steps: int, warmup: int, wl):
             "ms_per_checkpoint": mean * 1e3}
 
 
+def oracle_parallel_hash(sample_mib: int, reps: int, wl):
+    """The oracle's page hash (the dominant step of a checkpoint: every page
+    is read; the dirty pages' image is d = 5 % of it) on page-aligned slices
+    of the same sample, one host thread per core; the oracle itself is
+    unchanged (its C calls release the interpreter lock)."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_1808_00117_b300 import workloads as W
+    nbytes = sample_mib << 20
+    n_pages = W.pages_of(nbytes)
+    rng = np.random.default_rng(wl.seed)
+    data = rng.integers(0, 2**32, size=nbytes // 4, dtype=np.uint32).view(np.uint8)
+    cores = len(os.sched_getaffinity(0))
+    edges = [(n_pages * i // cores) * W.PAGE for i in range(cores + 1)]
+    slices = [data[a:b] for a, b in zip(edges[:-1], edges[1:]) if b > a]
+    ref = oracle.hash_all([data])
+    times = []
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        for r in range(reps + 1):
+            t0 = time.perf_counter()
+            parts = list(ex.map(lambda x: oracle.hash_all([x]), slices))
+            dt = time.perf_counter() - t0
+            if r:
+                times.append(dt)
+    assert np.array_equal(np.concatenate(parts), ref)
+    mean = statistics.mean(times)
+    return {"value": nbytes / mean / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"page hashes of {sample_mib} MiB of the {wl.name} workload on "
+                      f"{len(slices)} page-aligned slices, one thread per core, {reps} passes"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -454,6 +485,7 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu_baseline:
         cb = oracle_sample_run(args.cpu_sample_mib, 3, 1, wl)
         cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        cpu["parallel_hash"] = oracle_parallel_hash(4 * args.cpu_sample_mib, 3, wl)
 
     traffic = traffic_from_profile("k_hash_dirty", wl.name)
     line = {

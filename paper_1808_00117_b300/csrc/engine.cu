@@ -802,6 +802,20 @@ crum_status crum_register(crum_set* s, void* ptr, size_t bytes, uint32_t* alloc_
   if (bytes == 0) return fail(CRUM_EINVAL, "zero-byte registration");
   if (reinterpret_cast<uintptr_t>(ptr) % 16 != 0) return fail(CRUM_EINVAL, "pointer not 16-byte aligned");
   if (pages_of(bytes) > 0xFFFFFFFFull) return fail(CRUM_EINVAL, "allocation too large");
+  // both ends must be device memory of the set's device or managed memory
+  // (read by the kernels wherever its pages are), so no kernel is ever
+  // handed an address it cannot read
+  for (const uint8_t* q : {static_cast<const uint8_t*>(ptr), static_cast<const uint8_t*>(ptr) + bytes - 1}) {
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, q) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(CRUM_EINVAL, "not a CUDA allocation");
+    }
+    if (pa.type != cudaMemoryTypeManaged && (pa.type != cudaMemoryTypeDevice || pa.device != s->device)) {
+      return fail(CRUM_EINVAL, "range is neither device memory of device %d nor managed memory",
+                  s->device);
+    }
+  }
   std::lock_guard<std::mutex> lk(s->mu);
   const uintptr_t lo = reinterpret_cast<uintptr_t>(ptr), hi = lo + bytes;
   for (const Alloc& a : s->allocs) {

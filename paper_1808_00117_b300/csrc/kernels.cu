@@ -415,7 +415,16 @@ __global__ void __launch_bounds__(256) k_chain_owner(OwnerArgs a) {
   }
 }
 
+// An image's payload starts 64 + 16A + 16n bytes into it: 16-byte aligned,
+// rarely 128-byte aligned.  Read across the link, a warp's 512 contiguous
+// bytes would then span five 128-byte lines instead of four; so each CTA
+// reads whole aligned lines of a 16 KiB stretch into shared memory and
+// writes the page from there, shifted by the misalignment (a whole number
+// of 16-byte vectors).
+constexpr uint32_t kMergeChunkVecs = 1024;  // 16 KiB per step
+
 __global__ void __launch_bounds__(256) k_restore_merged(MergedRestoreArgs a) {
+  __shared__ uint4 buf[kMergeChunkVecs + 8];
   for (uint64_t g = blockIdx.x; g < a.n_pages; g += gridDim.x) {
     const uint64_t o = a.owner[g];
     if (o == 0) continue;  // no image of the chain holds this page
@@ -427,9 +436,18 @@ __global__ void __launch_bounds__(256) k_restore_merged(MergedRestoreArgs a) {
     const uint8_t* src = im.payload + s * kPage;
     const uint32_t valid = dev::valid_bytes(a.allocs[k].bytes, p);
     const uint32_t nvec = valid >> 4;
-    // plain loads: the source is host memory behind the link
-    for (uint32_t v = threadIdx.x; v < nvec; v += blockDim.x)
-      reinterpret_cast<uint4*>(dst)[v] = reinterpret_cast<const uint4*>(src)[v];
+    const uintptr_t sa = reinterpret_cast<uintptr_t>(src);
+    const uint4* line = reinterpret_cast<const uint4*>(sa & ~uintptr_t(127));
+    const uint32_t m = static_cast<uint32_t>(sa & 127u) >> 4;
+    for (uint32_t c = 0; c < nvec; c += kMergeChunkVecs) {
+      const uint32_t cnt = min(kMergeChunkVecs, nvec - c);
+      // vectors line[c .. c+cnt+m) end at the last whole vector of the page
+      for (uint32_t i = threadIdx.x; i < cnt + m; i += blockDim.x) buf[i] = line[c + i];
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x)
+        reinterpret_cast<uint4*>(dst)[c + i] = buf[i + m];
+      __syncthreads();
+    }
     const uint32_t rem = valid & 15u;
     if (rem != 0 && threadIdx.x == 0)
       for (uint32_t b = 0; b < rem; ++b) dst[16ull * nvec + b] = src[16ull * nvec + b];

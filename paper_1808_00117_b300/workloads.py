@@ -26,6 +26,7 @@ per-page mask, so every chosen page really changes.
 """
 from __future__ import annotations
 
+import ctypes
 import math
 from dataclasses import dataclass, field
 from typing import List
@@ -208,3 +209,72 @@ def mutate_pages_(buf, pages, seed: int, has_tail=None) -> None:
     if tail:
         m = torch.randint(1, 256, (1,), dtype=torch.int64, device=buf.device, generator=g).to(torch.uint8)
         buf[n_full * PAGE:].bitwise_xor_(m)
+
+
+# ----------------------------------------------------- managed memory -------
+#
+# The paper's applications keep their data in CUDA managed (unified) memory.
+# `managed_empty` makes such an allocation with the CUDA runtime, asks for
+# its pages to sit on the device (as they do after a kernel has touched
+# them), and returns a uint8 tensor over it; the allocation is freed when the
+# last tensor viewing it goes away.
+
+class _CudaMemLocation(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("id", ctypes.c_int)]
+
+
+_cudart = None
+
+
+def _rt():
+    global _cudart
+    if _cudart is None:
+        rt = ctypes.CDLL("libcudart.so.13")
+        rt.cudaMallocManaged.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_size_t, ctypes.c_uint]
+        rt.cudaMemPrefetchAsync.argtypes = [ctypes.c_void_p, ctypes.c_size_t, _CudaMemLocation,
+                                            ctypes.c_uint, ctypes.c_void_p]
+        rt.cudaFree.argtypes = [ctypes.c_void_p]
+        rt.cudaStreamSynchronize.argtypes = [ctypes.c_void_p]
+        _cudart = rt
+    return _cudart
+
+
+class _Managed:
+    """Owner of one managed allocation, exported to torch by the CUDA array
+    interface (torch keeps this object alive as long as the tensor)."""
+
+    def __init__(self, nbytes: int, device: int, where: str):
+        rt = _rt()
+        p = ctypes.c_void_p()
+        if rt.cudaMallocManaged(ctypes.byref(p), nbytes, 1) != 0:  # cudaMemAttachGlobal
+            raise MemoryError(f"cudaMallocManaged({nbytes}) failed")
+        self.ptr, self.nbytes = p.value, nbytes
+        try:
+            managed_prefetch(self.ptr, nbytes, where, device)
+        except RuntimeError:
+            rt.cudaFree(self.ptr)
+            self.ptr = None
+            raise
+        self.__cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1",
+                                         "data": (self.ptr, False), "version": 3, "strides": None}
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            _rt().cudaFree(self.ptr)
+            self.ptr = None
+
+
+def managed_prefetch(ptr: int, nbytes: int, where: str, device: int = 0) -> None:
+    """Move managed pages to the device or the host (synchronous)."""
+    rt = _rt()
+    # cudaMemLocationTypeDevice = 1, cudaMemLocationTypeHost = 2
+    loc = _CudaMemLocation(1, device) if where == "device" else _CudaMemLocation(2, 0)
+    if rt.cudaMemPrefetchAsync(ptr, nbytes, loc, 0, None) != 0 or rt.cudaStreamSynchronize(None) != 0:
+        raise RuntimeError("cudaMemPrefetchAsync failed")
+
+
+def managed_empty(nbytes: int, device: int = 0, where: str = "device"):
+    """uint8 CUDA tensor over a new managed allocation whose pages were
+    prefetched to `where` ("device" or "host")."""
+    t = _torch()
+    return t.as_tensor(_Managed(nbytes, device, where), device=f"cuda:{device}")

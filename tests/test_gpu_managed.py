@@ -1,0 +1,120 @@
+"""Managed (unified) memory, the paper's subject: allocations made with
+cudaMallocManaged are registered like device memory and must give the same
+bit-exact images and restores, whether their pages sit on the device or on
+the host when the checkpoint runs.  Registration rejects memory the kernels
+cannot read."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1808_00117_b300 as crum
+from paper_1808_00117_b300 import workloads as W
+
+from helpers import first_diff, host_copies, make_set, stream_handle, torch
+
+pytestmark = pytest.mark.gpu
+P = W.PAGE
+SIZES = [1, 24, P - 8, P, 3 * P + 40, 37 * P + 4104]
+
+
+@pytest.fixture(autouse=True)
+def _cuda():
+    t = torch()
+    if not t.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    crum.load()
+    yield
+    t.cuda.synchronize()
+
+
+def _managed(sizes, seed):
+    bufs = []
+    for i, n in enumerate(sizes):
+        b = W.managed_empty(n)
+        W.fill_(b, seed * 7919 + i, "u32")
+        bufs.append(b)
+    torch().cuda.synchronize()
+    return bufs
+
+
+def _ckpt(s, flags=crum.INCR):
+    img = s.checkpoint(stream_handle(), flags)
+    img.wait()
+    return img, img.to_bytes()
+
+
+def _mutate(bufs, frac, seed):
+    for i, b in enumerate(bufs):
+        n = W.pages_of(b.numel())
+        k = max(1, int(round(frac * n)))
+        W.mutate_pages_(b, W.choose_uniform(seed * 31 + i, n, k), seed * 131 + i)
+    torch().cuda.synchronize()
+
+
+@pytest.mark.parametrize("where", ["device", "host"])
+def test_managed_chain_and_restore(where):
+    """Full + two incrementals of managed allocations against the oracle;
+    before each checkpoint the pages are moved to `where` (host-resident
+    pages migrate back as the kernels read them); then the chain end is
+    restored onto garbage through both restore forms."""
+    bufs = _managed(SIZES, seed=71)
+    o = oracle.OracleSet(SIZES)
+    states, chain = [], []
+    s = make_set(bufs)
+    for step in range(3):
+        if step:
+            _mutate(bufs, 0.4, seed=710 + step)
+        states.append(host_copies(bufs))
+        for b in bufs:
+            W.managed_prefetch(b.data_ptr(), b.numel(), where)
+        img, got = _ckpt(s)
+        exp, *_ = o.checkpoint(states[-1])
+        assert first_diff(got, exp) is None, f"step {step}"
+        chain.append(img)
+    for mode in (crum.RESTORE_REPLAY, crum.RESTORE_MERGED):
+        r = make_set(bufs, restore_mode=mode)
+        for i, b in enumerate(bufs):
+            W.fill_(b, 9000 + i, "u32")
+        if where == "host":
+            for b in bufs:
+                W.managed_prefetch(b.data_ptr(), b.numel(), "host")
+        r.restore(chain[-1], stream_handle())
+        torch().cuda.synchronize()
+        assert all(np.array_equal(g, w) for g, w in zip(host_copies(bufs), states[-1])), mode
+        r.destroy()
+    for c in chain:
+        c.release()
+    s.destroy()
+
+
+def test_managed_and_device_memory_in_one_set():
+    t = torch()
+    sizes = [5 * P + 8, 2 * P]
+    m = _managed(sizes[:1], seed=73)[0]
+    d = t.empty(sizes[1], dtype=t.uint8, device="cuda")
+    W.fill_(d, 74, "u32")
+    s = make_set([m, d])
+    img, got = _ckpt(s)
+    exp, *_ = oracle.OracleSet(sizes).checkpoint(host_copies([m, d]))
+    assert first_diff(got, exp) is None
+    img.release()
+    s.destroy()
+
+
+def test_registration_rejects_memory_kernels_cannot_read():
+    t = torch()
+    s = crum.CheckpointSet()
+    pinned = t.empty(4 * P, dtype=t.uint8).pin_memory()
+    pageable = np.zeros(4 * P + 16, dtype=np.uint8)
+    addr = pageable.ctypes.data + (-pageable.ctypes.data) % 16
+    dev = t.empty(4 * P, dtype=t.uint8, device="cuda")
+    for ptr, n in [(pinned.data_ptr(), 4 * P), (addr, 4 * P), (dev.data_ptr(), 2 * P + (1 << 40))]:
+        with pytest.raises(crum.CrumError) as e:
+            s.register(ptr, n)
+        assert e.value.status == crum.EINVAL
+    s.register(dev.data_ptr(), 4 * P)
+    s.destroy()
