@@ -63,7 +63,27 @@ def parse_args(argv=None):
                     help="1: launch each capture as one CUDA graph (0: one launch per op)")
     ap.add_argument("--footprint-gib", type=int, default=0,
                     help="resize the single-allocation uint32 workload (small profiling cases)")
+    ap.add_argument("--memory", choices=["device", "managed"], default=None,
+                    help="application memory: cudaMalloc (PyTorch) or cudaMallocManaged "
+                         "prefetched to the device; default managed for the large workload")
     return ap.parse_args(argv)
+
+
+def app_memory(args, wl) -> str:
+    return args.memory or ("managed" if wl.name == "large" else "device")
+
+
+def app_alloc(torch, kind: str, nbytes: int, dev):
+    """The application's allocation: device memory or managed memory whose
+    pages sit on the device."""
+    from paper_1808_00117_b300 import workloads as W
+    if kind == "managed":
+        return W.managed_empty(nbytes, device=dev.index if dev.index is not None else 0)
+    return torch.empty(nbytes, dtype=torch.uint8, device=dev)
+
+
+MEMORY_DESC = {"device": "device memory (cudaMalloc through PyTorch)",
+               "managed": "managed memory (cudaMallocManaged, pages prefetched to the device)"}
 
 
 # ------------------------------------------------------------ distributed ---
@@ -349,8 +369,9 @@ def run_ours(args):
 
     link_peak = link_d2h_peak(torch)
     bufs = []
+    memory = app_memory(args, wl)
     for i, n in enumerate(wl.sizes):
-        b = torch.empty(n, dtype=torch.uint8, device=dev)
+        b = app_alloc(torch, memory, n, dev)
         W.fill_(b, wl.seed * 7919 + i + 1000 * rank, wl.kind)
         bufs.append(b)
     torch.cuda.synchronize()
@@ -495,6 +516,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": wl.name, "footprint_bytes": S, "allocations": len(wl.sizes),
                    "n_pages": n_pages, "dirty_pages_per_step": k_dirty,
+                   "memory": MEMORY_DESC[memory],
                    "staging_bytes": staging, "parallelism": f"replica per GPU x{world}",
                    "l2": "inputs (8 GiB) larger than L2 (126 MB); no flush",
                    "value_def": "footprint bytes / capture-kernel device time (hash+scan+gather)",
@@ -678,9 +700,10 @@ def run_batched(args):
     link_peak = link_d2h_peak(torch)
     stencil = wl.dirty_mode == "stencil"
     bufs = []
+    memory = app_memory(args, wl)
     if stencil:
         for i, n in enumerate(wl.sizes):
-            b = torch.empty(n, dtype=torch.uint8, device=dev)
+            b = app_alloc(torch, memory, n, dev)
             W.fill_(b, wl.seed * 7919 + i + 1000 * rank, wl.kind)
             bufs.append(b)
         plans = {t: [W.stencil_plan(n, wl.dirty_frac, wl.seed * 1000 + 7 * t + i)
@@ -694,7 +717,7 @@ def run_batched(args):
         # one device tensor carved into the allocations (offsets are 4 KiB
         # multiples); the application's update is one seeded scatter that
         # xors a nonzero mask into the first word of every chosen page
-        big = torch.empty(S, dtype=torch.uint8, device=dev)
+        big = app_alloc(torch, memory, S, dev)
         W.fill_(big, wl.seed + 1000 * rank, wl.kind)
         offs = np.cumsum([0] + list(wl.sizes))
         bufs = [big[int(offs[i]):int(offs[i + 1])] for i in range(len(wl.sizes))]
@@ -834,7 +857,7 @@ def run_batched(args):
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": wl.name, "footprint_bytes": S, "allocations": len(wl.sizes),
                    "n_pages": n_pages, "dirty_pages_per_step": int(statistics.mean(i["n_dirty"] for i in infos)),
-                   "sink": "null", "staging_bytes": staging,
+                   "sink": "null", "staging_bytes": staging, "memory": MEMORY_DESC[memory],
                    "hash_mapping": tune["hash_mapping"], "gather_mapping": tune["gather_mapping"],
                    "autotune_hash_ms": [round(x, 4) for x in tune["hash_ms"]],
                    "autotune_gather_ms": [round(x, 4) for x in tune["gather_ms"]]},

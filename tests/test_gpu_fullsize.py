@@ -146,7 +146,7 @@ def test_large_4096_allocations_sampled():
     if free < wl.total_bytes + (24 << 30):
         pytest.skip("needs about 165 GB of free device memory")
     S = wl.total_bytes
-    big = t.empty(S, dtype=t.uint8, device="cuda")
+    big = W.managed_empty(S)  # the configuration names device-resident managed memory
     W.fill_(big, wl.seed, wl.kind)
     offs = np.cumsum([0] + list(wl.sizes))
     bufs = [big[int(offs[i]):int(offs[i + 1])] for i in range(len(wl.sizes))]
