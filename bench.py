@@ -55,6 +55,7 @@ def parse_args(argv=None):
     ap.add_argument("--workload", default="uint32_8g")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-verify", action="store_true", help="skip the verify-mode measurement")
     ap.add_argument("--cpu-sample-mib", type=int, default=512)
     ap.add_argument("--requests", type=int, default=2000, help="serving workload: request count")
     ap.add_argument("--mapping", default="",
@@ -398,7 +399,7 @@ def run_ours(args):
     # the application's page choices are drawn up front (host-side numpy),
     # so the timed steps hold only the application's update kernels
     choices = {}
-    for step in range(1, warmup + steps + 1):
+    for step in range(1, warmup + steps + 5):  # + the verify-mode steps
         pages = W.choose_step(wl, step, n_pages)
         per = []
         for i, b in enumerate(bufs):
@@ -502,6 +503,32 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = run_e2e(torch, crum, W, s, bufs, wl, steps, sh, stream, warmup + steps + 1, dist, dev, world)
 
+    # verify mode (exact byte compare against a device shadow of the last
+    # checkpointed contents): the hash pass then reads every page and its
+    # shadow; a few untimed-setup steps, device-timed like the main loop
+    verify = None
+    if not args.no_verify:
+        vs = crum.CheckpointSet(device=local, staging_bytes=staging, host_pool_bytes=pool,
+                                verify=1, sink=crum.SINK_NULL)
+        for b in bufs:
+            vs.register(b.data_ptr(), b.numel())
+        vs.checkpoint(sh, crum.FULL | crum.VERIFY).wait()
+        vinfo = []
+        for j in range(4):
+            app_update(warmup + steps + 1 + j)  # steps the timed loop did not use
+            im = vs.checkpoint(sh, crum.VERIFY)
+            im.wait()
+            vinfo.append(im.info())
+            im.release()
+        vinfo = vinfo[1:]
+        vms = statistics.mean(i["t_hash_ms"] for i in vinfo)
+        verify = {"hash_ms": round(vms, 4), "read_bytes": 2 * S,
+                  "gbs": round(2 * S / (vms * 1e-3) / 1e9, 1),
+                  "frac": round(2 * S / (vms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
+                  "collisions": int(sum(i["collisions"] for i in vinfo)),
+                  "what": "verify-mode hash pass: every page and its shadow read once"}
+        vs.destroy()
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cb = oracle_sample_run(args.cpu_sample_mib, 3, 1, wl)
@@ -554,6 +581,7 @@ def run_ours(args):
                             "bytes / ms (what replaying the chain would move)"},
         "plain_p0": {"ms": round(plain_ms, 3), "gbs": round(S / (plain_ms * 1e-3) / 1e9, 2),
                      "what": "synchronize + full device->host copy of the footprint"},
+        "verify": verify,
         "whole_step": {"gbs": round(world * S / (total_ms / steps * 1e-3) / 1e9, 2),
                        "what": "footprint bytes / wall-clock ms per step; each step also drains "
                                "its dirty pages over the host link"},

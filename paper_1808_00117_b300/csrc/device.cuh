@@ -46,6 +46,24 @@ __device__ __forceinline__ uint4 ld_stream(const void* p) {
   return v;
 }
 
+// L2 policy for data read once: its lines are the first to be replaced, so a
+// streaming pass does not push out (and force the write-back of) lines that
+// earlier kernels left dirty in L2.
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+// ld_stream with an explicit L2 cache policy.
+__device__ __forceinline__ uint4 ld_stream_hint(const void* p, uint64_t pol) {
+  uint4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.L2::256B.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+      : "l"(p), "l"(pol));
+  return v;
+}
+
 // Coherent 16-byte load (data written earlier in the same stream).
 __device__ __forceinline__ uint4 ld_plain(const void* p) {
   return *reinterpret_cast<const uint4*>(p);

@@ -917,11 +917,12 @@ crum_status crum_autotune(crum_set* s, int* hash_mapping, int* gather_mapping, d
     }
   }
   // gather: a synthetic dirty set (bit 0 of every bitmap byte, 1 page in 8)
-  // scanned into staging half 0, then each mapping gathers it
+  // scanned into staging half 0, then each mapping gathers its first slots
+  // (as many as one staging half holds)
   int best_g = s->map_gather;
   Half& H = s->half[0];
   const uint64_t slots = std::min<uint64_t>((n + 7) / 8, s->half_slots);
-  if (st == CRUM_OK && slots == (n + 7) / 8) {
+  if (st == CRUM_OK && slots > 0) {
     cudaError_t ce = cudaMemsetAsync(s->d_mask, 0x01, words * sizeof(uint32_t), s->cap_stream);
     crum::ScanArgs sa{};
     sa.mask = s->d_mask;

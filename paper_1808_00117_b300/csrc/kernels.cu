@@ -92,17 +92,50 @@ __device__ __forceinline__ uint64_t hash_full_page(const uint8_t* src, int t) {
   const uint4* v4 = reinterpret_cast<const uint4*>(src) + t;
   uint64_t c = static_cast<uint64_t>(2 * t) * kPhi;
   uint64_t h = 0;
+  const uint64_t pol = dev::l2_evict_first_policy();
 #pragma unroll 1
   for (int k = 0; k < kPer; k += U) {
     uint4 v[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) v[u] = ld_stream(v4 + (k + u) * G);
+    for (int u = 0; u < U; ++u) v[u] = dev::ld_stream_hint(v4 + (k + u) * G, pol);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       h += hash_vec(v[u], c);
       c += kStep;
     }
   }
+  return h;
+}
+
+// Verify mode, full page: the hash of `src` as above, and whether any of
+// its bytes differs from `shadow`, in one pass over both.
+template <int G, int U>
+__device__ __forceinline__ uint64_t hash_full_page_cmp(const uint8_t* src, const uint8_t* shadow,
+                                                       int t, bool& differs) {
+  constexpr int kPer = kPageVecs / G;
+  static_assert(kPer % U == 0, "unroll must divide the per-thread vector count");
+  constexpr uint64_t kStep = static_cast<uint64_t>(2 * G) * kPhi;
+  const uint4* v4 = reinterpret_cast<const uint4*>(src) + t;
+  const uint4* w4 = reinterpret_cast<const uint4*>(shadow) + t;
+  uint64_t c = static_cast<uint64_t>(2 * t) * kPhi;
+  uint64_t h = 0;
+  uint32_t x = 0;
+#pragma unroll 1
+  for (int k = 0; k < kPer; k += U) {
+    uint4 v[U], w[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      v[u] = ld_stream(v4 + (k + u) * G);
+      w[u] = ld_stream(w4 + (k + u) * G);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      h += hash_vec(v[u], c);
+      c += kStep;
+      x |= (v[u].x ^ w[u].x) | (v[u].y ^ w[u].y) | (v[u].z ^ w[u].z) | (v[u].w ^ w[u].w);
+    }
+  }
+  differs = x != 0;
   return h;
 }
 
@@ -165,7 +198,15 @@ __global__ void __launch_bounds__(256, (MINB > 1 ? MINB : 0)) k_hash_dirty(HashA
     // under the page's loads instead of following them
     uint64_t prev = 0;
     if (a.h_out == nullptr && t == 0 && !a.full) prev = a.h_table[g];
-    uint64_t h = (valid == kPage) ? hash_full_page<G, U>(src, t) : hash_tail_page<G>(src, valid, t);
+    // verify mode reads a full page's shadow in the same pass (two page
+    // reads instead of three for an unchanged page)
+    bool fused = false, differs = false;
+    uint64_t h;
+    if constexpr (VERIFY) fused = !a.full && valid == kPage;
+    if (fused)
+      h = hash_full_page_cmp<G, U>(src, a.shadow + g * kPage, t, differs);
+    else
+      h = (valid == kPage) ? hash_full_page<G, U>(src, t) : hash_tail_page<G>(src, valid, t);
     h = group_sum<G>(h, sh);
     if (a.h_out != nullptr) {
       if (t == 0) a.h_out[g] = h;
@@ -175,7 +216,9 @@ __global__ void __launch_bounds__(256, (MINB > 1 ? MINB : 0)) k_hash_dirty(HashA
     if (t == 0) d = a.full || h != prev;
     if constexpr (VERIFY) {
       d = group_bcast0<G>(d, sh);
-      if (!d && page_differs<G>(src, a.shadow + g * kPage, valid, t, sh)) {
+      const bool any = fused ? group_any<G>(differs, sh)
+                             : (!d && page_differs<G>(src, a.shadow + g * kPage, valid, t, sh));
+      if (!d && any) {
         d = 1;
         if (t == 0) atomicAdd(a.collisions, 1ull);
       }

@@ -18,7 +18,8 @@ pytestmark = pytest.mark.gpu
 
 P = 65536
 # sizes that exercise full pages, every kind of tail and several tiles
-RAGGED = [1, 7, 8, 9, 15, 16, 17, 24, 4096 + 3, P - 8, P, P + 24, 3 * P - 5, 300 * P + 4104]
+RAGGED = [1, 7, 8, 9, 15, 16, 17, 24, 4096, 4096 + 3, 4096 + 8, P - 8, P, P + 24, 3 * P - 5,
+          300 * P + 4104]
 
 
 @pytest.fixture(autouse=True)
@@ -562,4 +563,38 @@ def test_merged_restore_of_images_from_bytes():
     assert all(np.array_equal(g, w) for g, w in zip(host_copies(bufs), states[-1]))
     for c in chain:
         c.release()
+    s.destroy()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("hm", [0, 1, 2, 3, 4, 5, 9, 10, 11])
+def test_verify_mode_collisions_every_mapping(hm):
+    """Verify mode over full and tail pages with each register mapping: two
+    injected collisions (a full page and a tail page whose committed hash is
+    made equal to the new one), one ordinary change, the rest unchanged."""
+    sizes = [4 * P, 2 * P + 40]
+    bufs = device_buffers(sizes, seed=13)
+    s = make_set(bufs, verify=1, hash_mapping=hm)
+    o = oracle.OracleSet(sizes)
+    _checkpoint_bytes(s, crum.VERIFY)
+    prev = host_copies(bufs)
+    o.checkpoint(prev)
+    W.mutate_pages_(bufs[0], [1, 2], 78)
+    W.mutate_pages_(bufs[1], [2], 79)  # the 40-byte tail page
+    now = host_copies(bufs)
+    h = oracle.hash_all(now)
+    for g in (2, 6):  # global pages: allocation 0 page 2, allocation 1 page 2
+        s.poke_hash(g, int(h[g]))
+        o.h_prev[g] = int(h[g])
+    img = s.checkpoint(stream_handle(), crum.VERIFY)
+    assert img.wait(crum.WAIT_PERSISTED) == crum.ECOLLISION
+    assert img.info()["collisions"] == 2
+    exp, d, _, coll = o.checkpoint(now, verify_prev=prev)
+    assert coll == 2
+    got = img.to_bytes()
+    assert first_diff(got, exp) is None
+    assert page_table(got).tolist() == [[0, 1], [0, 2], [1, 2]]
+    # unchanged since: a verify checkpoint is empty and collision-free
+    img2 = s.checkpoint(stream_handle(), crum.VERIFY)
+    assert img2.wait(crum.WAIT_PERSISTED) == crum.OK and img2.info()["n_dirty"] == 0
     s.destroy()
