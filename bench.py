@@ -399,7 +399,7 @@ def run_ours(args):
     # the application's page choices are drawn up front (host-side numpy),
     # so the timed steps hold only the application's update kernels
     choices = {}
-    for step in range(1, warmup + steps + 5):  # + the verify-mode steps
+    for step in range(1, warmup + steps + 6):  # + the verify-mode and rollback steps
         pages = W.choose_step(wl, step, n_pages)
         per = []
         for i, b in enumerate(bufs):
@@ -481,6 +481,23 @@ def run_ours(args):
     restore_ms = timed_restore(s)  # leaves the set's memory at the chain end
     restore_bytes = sum(img.info()["n_dirty"] for img in chain) * W.PAGE
     restore_images = len(chain)
+    # rollback: one more application update, then a delta restore of the
+    # chain end, which copies only the pages that now differ
+    delta_set = crum.CheckpointSet(device=local, staging_bytes=2 * W.PAGE,
+                                   restore_mode=crum.RESTORE_DELTA)
+    for b in bufs:
+        delta_set.register(b.data_ptr(), b.numel())
+    app_update(warmup + steps + 5)
+    torch.cuda.synchronize()
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d0.record(stream)
+    delta_set.restore(chain[-1], sh)
+    d1.record(stream)
+    torch.cuda.synchronize()
+    rollback = {"ms": round(d0.elapsed_time(d1), 3), "pages_copied": delta_set.restore_pages(),
+                "what": "delta restore of the chain end after one more application update "
+                        "(5 % of pages rewritten): pages whose hash differs are copied"}
+    delta_set.destroy()
 
     # plain form P0 (Section 3.4): synchronize, then copy every allocation whole
     host_plain = torch.empty(S, dtype=torch.uint8, pin_memory=True)
@@ -575,7 +592,7 @@ def run_ours(args):
                     "chain_payload_bytes": restore_bytes, "link_bytes": S,
                     "chain_gbs": round(restore_bytes / (restore_ms * 1e-3) / 1e9, 2),
                     "link_gbs": round(S / (restore_ms * 1e-3) / 1e9, 2),
-                    "replay_ms": round(replay_ms, 3),
+                    "replay_ms": round(replay_ms, 3), "rollback": rollback,
                     "replay_link_gbs": round(restore_bytes / (replay_ms * 1e-3) / 1e9, 2),
                     "what": "chain end restored onto garbage; chain_gbs = the chain's payload "
                             "bytes / ms (what replaying the chain would move)"},
@@ -920,7 +937,9 @@ def run_serving(args):
     crum_server: footprints log-uniform 1 MiB..4 GiB (int32/fp32/fp64 in
     turn), 80 % checkpoints (every 4th of a client full, so chains stay
     short) and 20 % restores of the client's newest chain, each checkpoint
-    preceded by the client rewriting U[1 %, 50 %] of its pages.  Runs:
+    and each restore preceded by the client rewriting U[1 %, 50 %] of its
+    pages (a restore rolls them back: delta restores copy the pages that
+    differ).  Runs:
     plain sequential form (one request on the device at a time) saturated,
     which gives its service rate mu; then Poisson arrivals at 0.8 mu through
     the sequential form and through continuous batching (8 slots, 16 GiB
@@ -956,7 +975,8 @@ def run_serving(args):
     torch.cuda.synchronize()
 
     for c in clients:  # sets (and their pinned pools) are reused by every run
-        c.set = crum.CheckpointSet(external_staging=1, host_pool_bytes=2 * c.size + (8 << 20))
+        c.set = crum.CheckpointSet(external_staging=1, host_pool_bytes=2 * c.size + (8 << 20),
+                                   restore_mode=crum.RESTORE_DELTA)
         c.set.register(c.buf.data_ptr(), c.size)
 
     def run(max_inflight, rate_hz, label, max_ckpt=0, max_rest=0):
@@ -987,13 +1007,15 @@ def run_serving(args):
                     time.sleep(delay)
                 if last is not None:  # the client's consistency rule
                     srv.wait(last[0], crum.WAIT_CAPTURED if last[1] != crum.REQ_RESTORE else crum.WAIT_PERSISTED)
+                # the request's share of rewritten pages: a checkpoint
+                # captures them, a restore rolls them back
+                k = max(1, int(round(req_frac[r] * c.pages)))
+                pages = W.choose_uniform(int(r) * 31 + ci, c.pages, k)
+                with torch.cuda.stream(c.stream):
+                    W.mutate_pages_(c.buf, pages, int(r))
                 if req_restore[r]:
                     kind = crum.REQ_RESTORE
                 else:
-                    k = max(1, int(round(req_frac[r] * c.pages)))
-                    pages = W.choose_uniform(int(r) * 31 + ci, c.pages, k)
-                    with torch.cuda.stream(c.stream):
-                        W.mutate_pages_(c.buf, pages, int(r))
                     kind = crum.REQ_CHECKPOINT_FULL if c.n_ckpt % 4 == 0 else crum.REQ_CHECKPOINT
                     c.n_ckpt += 1
                 ids[r] = srv.submit(c.cid, kind)

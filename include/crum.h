@@ -106,12 +106,24 @@ typedef struct crum_config {
                                   checkpoint is full, so restore replays at most
                                   max_chain + 1 images and older chains can be freed;
                                   0: chains grow without limit */
-    int restore_mode;          /* crum_restore of a chain: 0 auto (merged when the
-                                  chain's incrementals hold more than 8 % of the
-                                  base's pages), 1 replay every image in order,
-                                  2 merged: every page once, from the newest image
-                                  holding it */
+    int restore_mode;          /* crum_restore of a chain (crum_restore_mode):
+                                  0 auto (merged when the chain's incrementals hold
+                                  more than 8 % of the base's pages, else replay),
+                                  1 replay every image in order, 2 merged: every
+                                  page once, from the newest image holding it,
+                                  3 delta: merged, but a page whose current
+                                  contents already hash to the chain's value is
+                                  not copied (a rollback moves only what changed;
+                                  a changed page with an equal hash, probability
+                                  2^-64, is left as it is, as a checkpoint would) */
 } crum_config;
+
+typedef enum crum_restore_mode {
+    CRUM_RESTORE_AUTO = 0,
+    CRUM_RESTORE_REPLAY = 1,
+    CRUM_RESTORE_MERGED = 2,
+    CRUM_RESTORE_DELTA = 3
+} crum_restore_mode;
 
 /* Fill *cfg with defaults (device 0, 1 GiB staging, 64 MiB chunks, memory sink). */
 void crum_config_default(crum_config *cfg);
@@ -269,6 +281,12 @@ crum_status crum_image_release(crum_image *img);
    order), ECORRUPT (broken chain), EBUSY (checkpoint being captured),
    ECUDA. */
 crum_status crum_restore(crum_set *set, const crum_image *chain_end, crum_stream_t stream);
+
+/* Pages the set's last crum_restore copied across the host link (replay:
+   every slot of every chain image; merged: every page; delta: the pages
+   whose contents differed).  Waits for that restore to finish.  0 before
+   any restore.  Errors: EINVAL, ETIMEOUT, ECUDA. */
+crum_status crum_restore_pages(crum_set *set, uint64_t *pages);
 
 /* ---- single-step entry points (each a single step of the path, for tests
         and for callers that manage their own memory) ---- */

@@ -26,7 +26,7 @@ NO_PARENT = 0xFFFFFFFFFFFFFFFF
 INCR, FULL, VERIFY, NO_PAYLOAD = 0, 1, 2, 4
 WAIT_CAPTURED, WAIT_DRAINED, WAIT_PERSISTED = 1, 2, 3
 SINK_MEMORY, SINK_FILE, SINK_NULL = 0, 1, 2
-RESTORE_AUTO, RESTORE_REPLAY, RESTORE_MERGED = 0, 1, 2
+RESTORE_AUTO, RESTORE_REPLAY, RESTORE_MERGED, RESTORE_DELTA = 0, 1, 2, 3
 
 STATUS = {0: "CRUM_OK", 1: "CRUM_EINVAL", 2: "CRUM_ENOMEM", 3: "CRUM_EBUSY", 4: "CRUM_ECUDA",
           5: "CRUM_EIO", 6: "CRUM_EMISMATCH", 7: "CRUM_ECOLLISION", 8: "CRUM_ETIMEOUT",
@@ -116,6 +116,7 @@ SIGNATURES = {
     "crum_image_from_bytes": ([_VP, _VP, _U64, _VP, ctypes.POINTER(_VP)], _I),
     "crum_image_release": ([_VP], _I),
     "crum_restore": ([_VP, _VP, _VP], _I),
+    "crum_restore_pages": ([_VP, ctypes.POINTER(_U64)], _I),
     "crum_hash_pages": ([_VP, _U64, _VP, _VP], _I),
     "crum_hash_bytes": ([_VP, _U64, _U64, _VP, _VP], _I),
     "crum_get_hashes": ([_VP, _VP, _U64], _I),
@@ -288,6 +289,12 @@ class CheckpointSet:
 
     def restore(self, image: Image, stream: int = 0) -> None:
         _check(load().crum_restore(self.handle, image.handle, stream), "crum_restore")
+
+    def restore_pages(self) -> int:
+        """Pages the last restore copied across the host link (waits for it)."""
+        n = _U64()
+        _check(load().crum_restore_pages(self.handle, ctypes.byref(n)), "crum_restore_pages")
+        return n.value
 
     def load_image(self, path: str, parent: Optional[Image] = None) -> Image:
         h = _VP()

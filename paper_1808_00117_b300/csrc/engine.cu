@@ -381,7 +381,7 @@ crum_status new_image_events(crum_image* img) {
 // Restore of a whole chain in two launches (see k_chain_owner and
 // k_restore_merged): every page once, from the newest image holding it.
 crum_status restore_merged(crum_set* s, const std::vector<crum::ChainImage>& ci,
-                           uint64_t total_slots) {
+                           uint64_t total_slots, bool delta) {
   if (s->owner_cap < s->n_pages) {
     cudaFree(s->d_owner);
     s->d_owner = nullptr;
@@ -396,9 +396,28 @@ crum_status restore_merged(crum_set* s, const std::vector<crum::ChainImage>& ci,
     CK(cudaMalloc(&s->d_chain, ci.size() * sizeof(crum::ChainImage)));
     s->chain_cap = ci.size();
   }
+  if (s->d_copied == nullptr) CK(cudaMalloc(&s->d_copied, sizeof(unsigned long long)));
+  if (delta && s->cur_cap < s->n_pages) {
+    cudaFree(s->d_cur);
+    s->d_cur = nullptr;
+    s->cur_cap = 0;
+    CK(cudaMalloc(&s->d_cur, s->n_pages * sizeof(uint64_t)));
+    s->cur_cap = s->n_pages;
+  }
   // pageable source: staged by the runtime before the call returns
   CK(cudaMemcpyAsync(s->d_chain, ci.data(), ci.size() * sizeof(crum::ChainImage),
                      cudaMemcpyHostToDevice, s->cap_stream));
+  CK(cudaMemsetAsync(s->d_copied, 0, sizeof(unsigned long long), s->cap_stream));
+  if (delta) {
+    // the current contents' page hashes, to leave pages that already match
+    crum::HashArgs ha{};
+    ha.allocs = s->d_allocs;
+    ha.first_page = s->d_first_page;
+    ha.n_allocs = static_cast<uint32_t>(s->allocs.size());
+    ha.n_pages = s->n_pages;
+    ha.h_out = s->d_cur;
+    CK(crum::launch_hash_dirty(ha, s->map_hash, false, s->cap_stream));
+  }
   CK(cudaMemsetAsync(s->d_owner, 0, s->n_pages * sizeof(uint64_t), s->cap_stream));
   crum::OwnerArgs oa{};
   oa.allocs = s->d_allocs;
@@ -416,6 +435,8 @@ crum_status restore_merged(crum_set* s, const std::vector<crum::ChainImage>& ci,
   ma.images = s->d_chain;
   ma.owner = s->d_owner;
   ma.h_table = s->d_h;
+  ma.current = delta ? s->d_cur : nullptr;
+  ma.copied = s->d_copied;
   CK(crum::launch_restore_merged(ma, s->cap_stream));
   return CRUM_OK;
 }
@@ -701,7 +722,7 @@ crum_status crum_set_create(const crum_config* cfg_in, crum_set** out) {
   if (cfg.hash_mapping < -1 || cfg.hash_mapping >= crum::kNumMappings ||
       cfg.gather_mapping < -1 || cfg.gather_mapping > 5)
     return fail(CRUM_EINVAL, "mapping out of range");
-  if (cfg.restore_mode < 0 || cfg.restore_mode > 2) return fail(CRUM_EINVAL, "bad restore_mode");
+  if (cfg.restore_mode < 0 || cfg.restore_mode > 3) return fail(CRUM_EINVAL, "bad restore_mode");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg.device < 0 || cfg.device >= ndev) {
     cudaGetLastError();
@@ -788,6 +809,8 @@ crum_status crum_set_destroy(crum_set* s) {
   cudaFree(s->d_shadow);
   cudaFree(s->d_owner);
   cudaFree(s->d_chain);
+  cudaFree(s->d_cur);
+  cudaFree(s->d_copied);
   cudaEventDestroy(s->ev_app);
   cudaEventDestroy(s->ev_done);
   cudaStreamDestroy(s->cap_stream);
@@ -1440,11 +1463,13 @@ crum_status crum_restore(crum_set* s, const crum_image* chain_end, crum_stream_t
                     (unsigned long long)img->table[a].second, (unsigned long long)s->allocs[a].bytes);
   }
   const uint64_t A = s->allocs.size();
-  // merged when the incrementals would carry more than 8 % of the base's
-  // pages a second time (kernel reads of host memory run ~7 % below DMA)
+  // auto: merged when the incrementals would carry more than 8 % of the
+  // base's pages a second time (kernel reads of host memory run ~7 % below
+  // DMA); delta is merged restricted to pages whose contents differ
   uint64_t incr_pages = 0;
   for (size_t i = 1; i < chain.size(); ++i) incr_pages += chain[i]->n_dirty;
-  bool merged = s->cfg.restore_mode == 2 ||
+  const bool delta = s->cfg.restore_mode == 3;
+  bool merged = s->cfg.restore_mode == 2 || delta ||
                 (s->cfg.restore_mode == 0 && incr_pages * 100 > 8 * chain.front()->n_dirty);
   std::vector<crum::ChainImage> ci;
   uint64_t total_slots = 0;
@@ -1452,7 +1477,7 @@ crum_status crum_restore(crum_set* s, const crum_image* chain_end, crum_stream_t
     cudaPointerAttributes pa{};
     if (cudaPointerGetAttributes(&pa, chain[i]->host) != cudaSuccess || pa.devicePointer == nullptr) {
       cudaGetLastError();
-      if (s->cfg.restore_mode == 2)
+      if (s->cfg.restore_mode >= 2)
         return fail(CRUM_EINVAL, "image %llu is not in device-mapped host memory",
                     (unsigned long long)chain[i]->seq);
       merged = false;
@@ -1470,7 +1495,9 @@ crum_status crum_restore(crum_set* s, const crum_image* chain_end, crum_stream_t
   CK(cudaEventRecord(s->ev_app, us));
   CK(cudaStreamWaitEvent(s->cap_stream, s->ev_app, 0));
   if ((st = upload_table(s)) != CRUM_OK) return st;
-  if (merged && (st = restore_merged(s, ci, total_slots)) != CRUM_OK) return st;
+  if (merged && (st = restore_merged(s, ci, total_slots, delta)) != CRUM_OK) return st;
+  s->restore_counted_on_device = merged;
+  s->restore_pages = merged ? 0 : incr_pages + chain.front()->n_dirty;
   int h = s->next_half;
   for (crum_image* img : (merged ? std::vector<crum_image*>{} : chain)) {
     const uint64_t n = img->n_dirty;
@@ -1511,6 +1538,29 @@ crum_status crum_restore(crum_set* s, const crum_image* chain_end, crum_stream_t
   s->chain_len = chain.size() - 1;
   s->needs_full = s->cfg.verify != 0;  // the verify shadow does not hold the restored bytes
   s->reg_changed = false;
+  return CRUM_OK;
+}
+
+crum_status crum_restore_pages(crum_set* s, uint64_t* pages) {
+  t_err.clear();
+  if (s == nullptr || pages == nullptr) return fail(CRUM_EINVAL, "null argument");
+  DeviceGuard dg(s->device);
+  bool on_device;
+  uint64_t host_count;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    on_device = s->restore_counted_on_device;
+    host_count = s->restore_pages;
+  }
+  crum_status st = wait_event(s->ev_done, kBackgroundLimitNs);
+  if (st != CRUM_OK) return st;
+  if (!on_device) {
+    *pages = host_count;
+    return CRUM_OK;
+  }
+  unsigned long long n = 0;
+  CK(cudaMemcpy(&n, s->d_copied, sizeof n, cudaMemcpyDeviceToHost));
+  *pages = n;
   return CRUM_OK;
 }
 

@@ -154,6 +154,11 @@ struct crum_set {
   size_t owner_cap = 0;         // pages
   crum::ChainImage* d_chain = nullptr;
   size_t chain_cap = 0;         // images
+  uint64_t* d_cur = nullptr;    // delta restore: current hash of every page
+  size_t cur_cap = 0;           // pages
+  unsigned long long* d_copied = nullptr;  // merged restore: pages copied across the link
+  uint64_t restore_pages = 0;   // replay restore: pages copied across the link
+  bool restore_counted_on_device = false;
   crum::Half half[2];
   int next_half = 0;
   uint64_t half_slots = 0;

@@ -468,11 +468,25 @@ constexpr uint32_t kMergeChunkVecs = 1024;  // 16 KiB per step
 
 __global__ void __launch_bounds__(256) k_restore_merged(MergedRestoreArgs a) {
   __shared__ uint4 buf[kMergeChunkVecs + 8];
+  __shared__ int skip_sh;
   for (uint64_t g = blockIdx.x; g < a.n_pages; g += gridDim.x) {
     const uint64_t o = a.owner[g];
     if (o == 0) continue;  // no image of the chain holds this page
     const ChainImage& im = a.images[(o >> 40) - 1];
     const uint64_t s = o & kSlotMask;
+    // the chain's hash of the page is installed first; in delta mode a page
+    // whose current contents already hash to it is left as it is
+    if (threadIdx.x == 0) {
+      const uint64_t hc = reinterpret_cast<const uint64_t*>(im.hashes)[s];
+      a.h_table[g] = hc;
+      const bool skip = a.current != nullptr && a.current[g] == hc;
+      if (!skip && a.copied != nullptr) atomicAdd(a.copied, 1ull);
+      skip_sh = skip;
+    }
+    __syncthreads();
+    const bool skip = skip_sh;
+    __syncthreads();  // every thread has read the flag before it is rewritten
+    if (skip) continue;
     const uint32_t k = dev::find_alloc(a.first_page, a.n_allocs, g);
     const uint64_t p = g - a.allocs[k].first_page;
     uint8_t* dst = a.allocs[k].base + p * kPage;
@@ -494,7 +508,6 @@ __global__ void __launch_bounds__(256) k_restore_merged(MergedRestoreArgs a) {
     const uint32_t rem = valid & 15u;
     if (rem != 0 && threadIdx.x == 0)
       for (uint32_t b = 0; b < rem; ++b) dst[16ull * nvec + b] = src[16ull * nvec + b];
-    if (threadIdx.x == 0) a.h_table[g] = reinterpret_cast<const uint64_t*>(im.hashes)[s];
   }
 }
 

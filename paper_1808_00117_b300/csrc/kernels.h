@@ -114,6 +114,8 @@ struct MergedRestoreArgs {
   const ChainImage* images;
   const uint64_t* owner;
   uint64_t* h_table;
+  const uint64_t* current;          // delta mode: current hash of every page, else nullptr
+  unsigned long long* copied;       // pages copied across the link (optional)
 };
 
 // Launch shape of one kernel: launched directly (launch_spec) or added to a

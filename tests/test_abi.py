@@ -61,3 +61,30 @@ def test_argument_errors_need_no_device():
     cfg = crum.config(staging_bytes=1000)
     h = ctypes.c_void_p()
     assert lib.crum_set_create(ctypes.byref(cfg), ctypes.byref(h)) == crum.EINVAL
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every struct the binding passes by pointer has the header's size and
+    field offsets (a C program compiled from include/crum.h prints them)."""
+    structs = {"crum_config": crum.Config, "crum_image_info": crum.ImageInfo,
+               "crum_server_config": crum.ServerConfig, "crum_request_info": crum.RequestInfo,
+               "crum_server_stats": crum.ServerStats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "crum.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        name, field, val = line.split()
+        got[(name, field)] = int(val)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, f"{cname}.{f}"

@@ -501,7 +501,8 @@ def test_sink_lost_mid_chain_keeps_earlier_images(tmp_path):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("mode", [crum.RESTORE_REPLAY, crum.RESTORE_MERGED, crum.RESTORE_AUTO])
+@pytest.mark.parametrize("mode", [crum.RESTORE_REPLAY, crum.RESTORE_MERGED, crum.RESTORE_AUTO,
+                                  crum.RESTORE_DELTA])
 def test_chain_restore_forms_agree(mode):
     """Replay (every image in turn) and merged (every page once, from the
     newest image holding it) restore the same bytes and hashes: chain ends
@@ -598,3 +599,44 @@ def test_verify_mode_collisions_every_mapping(hm):
     img2 = s.checkpoint(stream_handle(), crum.VERIFY)
     assert img2.wait(crum.WAIT_PERSISTED) == crum.OK and img2.info()["n_dirty"] == 0
     s.destroy()
+
+
+@pytest.mark.gpu
+def test_delta_restore_moves_only_changed_pages():
+    """Rollback: after the chain end, some pages (full and tail) are
+    rewritten; a delta restore brings back exactly the chain end's bytes and
+    hashes and copies only the rewritten pages across the link, while the
+    merged and replay forms copy every page / every image slot."""
+    sizes = RAGGED
+    bufs = device_buffers(sizes, seed=67)
+    n_pages = sum(W.pages_of(n) for n in sizes)
+    o = oracle.OracleSet(sizes)
+    forms = {m: make_set(bufs, restore_mode=m) for m in
+             (crum.RESTORE_DELTA, crum.RESTORE_MERGED, crum.RESTORE_REPLAY)}
+    s = forms[crum.RESTORE_DELTA]
+    chain = []
+    for step in range(3):
+        if step:
+            mutate(bufs, sizes, 0.3, seed=670 + step)
+        img = s.checkpoint(stream_handle())
+        img.wait()
+        chain.append(img)
+    state = host_copies(bufs)
+    _, _, h_end, _ = o.checkpoint(state)
+    slots = sum(c.info()["n_dirty"] for c in chain)
+    for m, r in forms.items():
+        touched = mutate(bufs, sizes, 0.1, seed=690 + m)
+        r.restore(chain[-1], stream_handle())
+        torch().cuda.synchronize()
+        assert all(np.array_equal(g, w) for g, w in zip(host_copies(bufs), state)), m
+        assert np.array_equal(r.hashes(), h_end), m
+        want = {crum.RESTORE_DELTA: len(touched), crum.RESTORE_MERGED: n_pages,
+                crum.RESTORE_REPLAY: slots}[m]
+        assert r.restore_pages() == want, m
+    # nothing changed since: a delta restore copies nothing
+    s.restore(chain[-1], stream_handle())
+    assert s.restore_pages() == 0
+    for c in chain:
+        c.release()
+    for r in forms.values():
+        r.destroy()

@@ -24,16 +24,17 @@ def _cuda():
 
 
 class Client:
-    def __init__(self, server, idx, size):
+    def __init__(self, server, idx, size, restore_mode=crum.RESTORE_AUTO):
         t = torch()
         self.idx, self.size = idx, size
         self.stream = t.cuda.Stream()
         self.buf = t.empty(size, dtype=t.uint8, device="cuda")
         W.fill_(self.buf, 600 + idx, "fp32")
         t.cuda.synchronize()
-        self.set = crum.CheckpointSet(external_staging=1)
+        self.set = crum.CheckpointSet(external_staging=1, restore_mode=restore_mode)
         self.set.register(self.buf.data_ptr(), size)
         self.cid = server.add_client(self.set, self.stream.cuda_stream)
+        self.restore_mode = restore_mode
         self.oracle = oracle.OracleSet([size])
         self.step = 0
         self.states = []
@@ -73,9 +74,13 @@ def run_sequence(server, clients, rounds, restore_at):
             pending.append((c, rid))
         if rnd == restore_at:
             for c in clients:
-                # scribble, then restore the newest chain: memory must come back
-                with torch().cuda.stream(c.stream):
-                    W.fill_(c.buf, 999, "u32")
+                # scribble (all of it, or a third of the pages for a delta
+                # restore), then restore the newest chain: memory must come back
+                if c.restore_mode == crum.RESTORE_DELTA:
+                    c.mutate()
+                else:
+                    with torch().cuda.stream(c.stream):
+                        W.fill_(c.buf, 999, "u32")
                 rid = server.submit(c.cid, crum.REQ_RESTORE)
                 info = server.wait(rid)
                 assert info["done"] and info["status"] == crum.OK
@@ -87,11 +92,12 @@ def run_sequence(server, clients, rounds, restore_at):
     return got, exp
 
 
-@pytest.mark.parametrize("lanes", [(-1, -1), (1, 1)])
-def test_same_alone_and_in_the_mix(lanes):
+@pytest.mark.parametrize("lanes,mode", [((-1, -1), crum.RESTORE_AUTO), ((1, 1), crum.RESTORE_AUTO),
+                                        ((1, 1), crum.RESTORE_DELTA)])
+def test_same_alone_and_in_the_mix(lanes, mode):
     srv = crum.Server(staging_budget=1 << 30, max_inflight=3, max_checkpoints=lanes[0],
                       max_restores=lanes[1])
-    mix = [Client(srv, i, s) for i, s in enumerate(SIZES)]
+    mix = [Client(srv, i, s, mode) for i, s in enumerate(SIZES)]
     got_mix, exp = run_sequence(srv, mix, rounds=4, restore_at=2)
     stats = srv.drain()
     assert stats["failed"] == 0 and stats["completed"] == 4 * len(SIZES) + len(SIZES)
@@ -103,7 +109,7 @@ def test_same_alone_and_in_the_mix(lanes):
     # each client alone, same seeds: same images
     for i, s in enumerate(SIZES):
         srv1 = crum.Server(staging_budget=1 << 30, max_inflight=3)
-        alone = Client(srv1, i, s)
+        alone = Client(srv1, i, s, mode)
         got_alone, _ = run_sequence(srv1, [alone], rounds=4, restore_at=2)
         assert got_alone[i] == got_mix[i], f"client {i} alone differs from the mix"
         srv1.destroy()
