@@ -210,15 +210,28 @@ def measured_peaks() -> dict:
         return {"hbm_gbs": FALLBACK_HBM_GBS, "source": "fallback"}
 
 
+def kernel_code_digest() -> str:
+    """First 16 hex digits of the sha256 of the device code (kernels.cu and
+    device.cuh) with comments and whitespace removed, so that editing a
+    comment keeps a recorded profile valid and editing code does not."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for name in ("kernels.cu", "device.cuh"):
+        text = open(os.path.join(ROOT, "paper_1808_00117_b300", "csrc", name)).read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
+    return h.hexdigest()[:16]
+
+
 def traffic_from_profile(kernel: str, workload: str):
     """DRAM bytes per launch recorded from ncu in profiles/, if the recorded
-    kernel source digest still matches the source being benchmarked."""
-    import hashlib
+    device-code digest still matches the code being benchmarked."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
-    src = os.path.join(ROOT, "paper_1808_00117_b300", "csrc", "kernels.cu")
     try:
         text = open(path).read()
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        digest = kernel_code_digest()
     except OSError:
         return None
     vals = {}
@@ -226,7 +239,7 @@ def traffic_from_profile(kernel: str, workload: str):
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("kernels_cu_sha256_16") != digest:
+    if vals.get("device_code_sha256_16") != digest:
         return None
     try:
         return int(vals["traffic_bytes_per_launch_full_size"])

@@ -11,7 +11,13 @@
 //                 3.3-3.4), plus the image checksum of everything it writes
 //   k_restore     inverse scatter of image slots onto the allocations and
 //                 installation of the image hashes (Section 3.4 restart)
+//   k_chain_owner newest (image, slot) of every page over a restore chain
+//   k_restore_merged  every page once from that image, read from the
+//                 image's pinned host memory (optionally only pages whose
+//                 current hash differs: delta restore)
 //   k_hash_bytes  the hash over an arbitrary byte string (image checksum)
+//   k_hash_dirty_bulk  k_hash_dirty with pages staged into shared memory by
+//                 cp.async.bulk (warp-specialised; bounded mbarrier waits)
 #include <cuda_runtime.h>
 
 #include <algorithm>
