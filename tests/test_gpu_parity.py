@@ -640,3 +640,32 @@ def test_delta_restore_moves_only_changed_pages():
         c.release()
     for r in forms.values():
         r.destroy()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("staging", [None, 8 * P])
+def test_no_payload_keeps_checksum_and_chain(staging):
+    """CRUM_NO_PAYLOAD on a footprint larger than the 256 MiB bounce region,
+    through the one-pass and the chunked capture: the image's checksum and
+    size equal the oracle's (its payload crossed the link, through several
+    bounce copies, and was dropped), and the next incremental, which keeps
+    its payload, is byte-exact."""
+    sizes = [300 * (1 << 20) + 24]
+    bufs = device_buffers(sizes, seed=19)
+    s = make_set(bufs, **({} if staging is None else {"staging_bytes": staging}))
+    o = oracle.OracleSet(sizes)
+    img = s.checkpoint(stream_handle(), crum.FULL | crum.NO_PAYLOAD)
+    img.wait()
+    exp, *_ = o.checkpoint(host_copies(bufs))
+    info = img.info()
+    assert info["checksum"] == int(np.frombuffer(exp[-8:], dtype=np.uint64)[0])
+    assert info["image_bytes"] == len(exp) and info["n_dirty"] == W.pages_of(sizes[0])
+    with pytest.raises(crum.CrumError):
+        img.to_bytes()
+    mutate(bufs, sizes, 0.05, seed=20)
+    img2, got = _checkpoint_bytes(s)
+    exp2, *_ = o.checkpoint(host_copies(bufs))
+    assert first_diff(got, exp2) is None
+    img.release()
+    img2.release()
+    s.destroy()
