@@ -90,10 +90,13 @@ typedef struct crum_config {
     int verify;                /* 1: keep a device copy of the last checkpointed
                                   contents so CRUM_VERIFY checkpoints can byte-compare */
     int fsync;                 /* 1: fsync image files before reporting PERSISTED */
-    int hash_mapping;          /* thread mapping of the hash kernel, 0..11; -1 default.
-                                  0-5: register mappings (one warp or one CTA per
-                                  page), 6-8: shared-memory bulk-copy mappings,
-                                  9-11: register mappings capped at 32 registers */
+    int hash_mapping;          /* thread mapping of the hash kernel,
+                                  0..CRUM_NUM_HASH_MAPPINGS-1; -1 default.
+                                  0-5: register mappings (one warp or one CTA of
+                                  256 per page), 6-8: shared-memory bulk-copy
+                                  mappings, 9-11: register mappings capped at 32
+                                  registers, 12-14: one CTA of 64 or 128 threads
+                                  per page */
     int gather_mapping;        /* thread mapping of the gather kernel, 0..5; -1 default */
     int external_staging;      /* 1: allocate no staging; a crum_server lends staging
                                   to the set for each request it admits */
@@ -163,14 +166,18 @@ crum_status crum_unregister(crum_set *set, uint32_t alloc_id);
 /* Number of registrations and total pages of the set. */
 crum_status crum_set_info(const crum_set *set, uint32_t *n_allocs, uint64_t *n_pages);
 
-/* Autotuner: time every hash mapping (0..11) and every gather mapping (0..5)
+#define CRUM_NUM_HASH_MAPPINGS 15
+#define CRUM_NUM_GATHER_MAPPINGS 6
+
+/* Autotuner: time every hash mapping and every gather mapping
    on the set's current registrations and keep the fastest of each for its
    later checkpoints.  Every candidate's page hashes must be bit-identical
    (else ECORRUPT and nothing changes).  Waits for in-flight checkpoints;
    leaves committed hashes and images untouched (it hashes into scratch and
    gathers a synthetic 1-in-8 page set into idle staging).  *hash_mapping and
    *gather_mapping (either may be NULL) receive the choice; *hash_ms and
-   *gather_ms (may be NULL) arrays of 12 and 6 doubles receive the mean
+   *gather_ms (may be NULL) arrays of CRUM_NUM_HASH_MAPPINGS and
+   CRUM_NUM_GATHER_MAPPINGS doubles receive the mean
    device time of each candidate.  Errors: EINVAL (no registrations), ECUDA. */
 crum_status crum_autotune(crum_set *set, int *hash_mapping, int *gather_mapping,
                           double *hash_ms, double *gather_ms);

@@ -27,6 +27,7 @@ INCR, FULL, VERIFY, NO_PAYLOAD = 0, 1, 2, 4
 WAIT_CAPTURED, WAIT_DRAINED, WAIT_PERSISTED = 1, 2, 3
 SINK_MEMORY, SINK_FILE, SINK_NULL = 0, 1, 2
 RESTORE_AUTO, RESTORE_REPLAY, RESTORE_MERGED, RESTORE_DELTA = 0, 1, 2, 3
+NUM_HASH_MAPPINGS, NUM_GATHER_MAPPINGS = 15, 6  # CRUM_NUM_HASH_MAPPINGS, CRUM_NUM_GATHER_MAPPINGS
 
 STATUS = {0: "CRUM_OK", 1: "CRUM_EINVAL", 2: "CRUM_ENOMEM", 3: "CRUM_EBUSY", 4: "CRUM_ECUDA",
           5: "CRUM_EIO", 6: "CRUM_EMISMATCH", 7: "CRUM_ECOLLISION", 8: "CRUM_ETIMEOUT",
@@ -276,7 +277,7 @@ class CheckpointSet:
     def autotune(self) -> dict:
         """Pick the fastest hash and gather mappings for the registrations."""
         hm, gm = _I(), _I()
-        ht, gt = (ctypes.c_double * 12)(), (ctypes.c_double * 6)()
+        ht, gt = (ctypes.c_double * NUM_HASH_MAPPINGS)(), (ctypes.c_double * NUM_GATHER_MAPPINGS)()
         _check(load().crum_autotune(self.handle, ctypes.byref(hm), ctypes.byref(gm), ht, gt),
                "crum_autotune")
         return {"hash_mapping": hm.value, "gather_mapping": gm.value,

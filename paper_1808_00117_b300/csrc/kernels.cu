@@ -27,6 +27,7 @@
 #include <mutex>
 #include <tuple>
 
+#include "crum.h"
 #include "device.cuh"
 #include "kernels.h"
 
@@ -800,17 +801,20 @@ int resident_ctas(K kernel, int threads) {
 // Grid for `units` groups of a kernel with `groups_per_cta` groups per CTA:
 // enough CTAs for every unit, at most what is resident at once.
 template <typename K>
-unsigned grid_for(K kernel, uint64_t units, int groups_per_cta) {
+unsigned grid_for(K kernel, uint64_t units, int groups_per_cta, int threads = 256) {
   const uint64_t need = (units + groups_per_cta - 1) / groups_per_cta;
-  const uint64_t cap = static_cast<uint64_t>(resident_ctas(kernel, 256));
+  const uint64_t cap = static_cast<uint64_t>(resident_ctas(kernel, threads));
   return static_cast<unsigned>(std::max<uint64_t>(1, std::min(need, cap)));
 }
 
+// G == 32: eight one-warp groups in a 256-thread CTA; G > 32: one group
+// per CTA of G threads.
 template <int G, int U, bool V, int MINB = 1>
 KernelSpec hash_spec_t(uint64_t n_pages) {
   auto kern = k_hash_dirty<G, U, V, MINB>;
-  return KernelSpec{reinterpret_cast<const void*>(kern), grid_for(kern, n_pages, G == 32 ? 8 : 1),
-                    256, 0};
+  constexpr int kThreads = G == 32 ? 256 : G;
+  return KernelSpec{reinterpret_cast<const void*>(kern),
+                    grid_for(kern, n_pages, G == 32 ? 8 : 1, kThreads), kThreads, 0};
 }
 
 template <int STAGES, int CW>
@@ -844,13 +848,16 @@ KernelSpec gather_spec_t(uint64_t max_slots) {
 const Mapping kMappings[] = {
     {32, 4, 0},  {32, 8, 0},  {32, 16, 0},  {256, 2, 0}, {256, 4, 0}, {256, 8, 0},
     {256, 0, 4}, {256, 0, 6}, {512, 0, 4},  {32, 4, 0},  {32, 8, 0},  {256, 4, 0},
+    {64, 8, 0},  {128, 4, 0}, {128, 8, 0},
 };
+static_assert(sizeof(kMappings) / sizeof(kMappings[0]) == CRUM_NUM_HASH_MAPPINGS,
+              "the header's mapping count");
 const int kNumMappings = sizeof(kMappings) / sizeof(kMappings[0]);
 
 cudaError_t hash_spec(uint64_t n_pages, int mapping, bool verify, KernelSpec* out) {
   // verify mode compares pages against the shadow copy, which only the
   // register mappings do; bulk-copy mappings fall back to mapping 1 there
-  if (verify && mapping >= 6) mapping = 1;
+  if (verify && mapping >= 6 && mapping <= 11) mapping = 1;
 #define CRUM_HASH_CASE(i, G, U)                                                       \
   case i:                                                                             \
     *out = verify ? hash_spec_t<G, U, true>(n_pages) : hash_spec_t<G, U, false>(n_pages); \
@@ -877,6 +884,9 @@ cudaError_t hash_spec(uint64_t n_pages, int mapping, bool verify, KernelSpec* ou
     case 11:
       *out = hash_spec_t<256, 4, false, 8>(n_pages);
       return cudaSuccess;
+    CRUM_HASH_CASE(12, 64, 8)
+    CRUM_HASH_CASE(13, 128, 4)
+    CRUM_HASH_CASE(14, 128, 8)
     default:
       return cudaErrorInvalidValue;
   }

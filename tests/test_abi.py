@@ -88,3 +88,10 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert got[(cname, f)] == getattr(py, f).offset, f"{cname}.{f}"
+
+
+def test_mapping_counts_match_the_header():
+    src = open(os.path.join(ROOT, "include", "crum.h")).read()
+    h = int(re.search(r"#define CRUM_NUM_HASH_MAPPINGS (\d+)", src).group(1))
+    g = int(re.search(r"#define CRUM_NUM_GATHER_MAPPINGS (\d+)", src).group(1))
+    assert (crum.NUM_HASH_MAPPINGS, crum.NUM_GATHER_MAPPINGS) == (h, g)

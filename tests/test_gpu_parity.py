@@ -319,7 +319,7 @@ def test_kernels_are_launched():
     s.destroy()
 
 
-@pytest.mark.parametrize("hm", range(12))
+@pytest.mark.parametrize("hm", range(crum.NUM_HASH_MAPPINGS))
 def test_every_mapping_is_bit_exact(hm):
     """Every autotuner candidate (hash mappings 0-8, gather mappings 0-5)
     gives the oracle's images bit for bit, over ragged allocations."""
@@ -346,7 +346,7 @@ def test_autotune_keeps_parity():
     e0, *_ = o.checkpoint(host_copies(bufs))
     assert first_diff(b0, e0) is None
     t = s.autotune()
-    assert 0 <= t["hash_mapping"] < 12 and 0 <= t["gather_mapping"] < 6
+    assert 0 <= t["hash_mapping"] < crum.NUM_HASH_MAPPINGS and 0 <= t["gather_mapping"] < 6
     assert all(x > 0 for x in t["hash_ms"]) and all(x > 0 for x in t["gather_ms"])
     # autotuning hashed into scratch: the committed hashes are untouched
     assert np.array_equal(s.hashes(), oracle.hash_all(host_copies(bufs)))
@@ -568,7 +568,7 @@ def test_merged_restore_of_images_from_bytes():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("hm", [0, 1, 2, 3, 4, 5, 9, 10, 11])
+@pytest.mark.parametrize("hm", [0, 1, 2, 3, 4, 5, 9, 10, 11, 12, 13, 14])
 def test_verify_mode_collisions_every_mapping(hm):
     """Verify mode over full and tail pages with each register mapping: two
     injected collisions (a full page and a tail page whose committed hash is
