@@ -56,6 +56,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-verify", action="store_true", help="skip the verify-mode measurement")
+    ap.add_argument("--sink", choices=["memory", "file"], default="memory",
+                    help="uint32 workload: where the writer persists images (file: a "
+                         "temporary directory on the host's disk, fsync per image)")
     ap.add_argument("--cpu-sample-mib", type=int, default=512)
     ap.add_argument("--requests", type=int, default=2000, help="serving workload: request count")
     ap.add_argument("--mapping", default="",
@@ -392,10 +395,15 @@ def run_ours(args):
     staging = 2 * ((n_pages + 1) * W.PAGE)  # two halves that each hold every page
     pool = full_image + (warmup + steps + 2) * incr_image
     fixed = [int(x) for x in args.mapping.split(",")] if args.mapping else None
+    sink_dir = None
+    if args.sink == "file":
+        sink_dir = tempfile.mkdtemp(prefix="crum_sink_")
     s = crum.CheckpointSet(device=local, staging_bytes=staging, host_pool_bytes=pool,
                            use_graph=int(args.graph),
                            hash_mapping=fixed[0] if fixed else -1,
-                           gather_mapping=fixed[1] if fixed else -1)
+                           gather_mapping=fixed[1] if fixed else -1,
+                           sink=crum.SINK_FILE if sink_dir else crum.SINK_MEMORY,
+                           sink_dir=sink_dir, fsync=int(bool(sink_dir)))
     for b in bufs:
         s.register(b.data_ptr(), b.numel())
     stream = torch.cuda.current_stream()
@@ -441,6 +449,7 @@ def run_ours(args):
     clocks.mark("t0")
     e0.record(stream)
     timed = []
+    t_loop0 = time.perf_counter()
     for step in range(steps):
         app_update(warmup + 1 + step)
         timed.append(s.checkpoint(sh))
@@ -454,6 +463,7 @@ def run_ours(args):
     clk = clocks.stop()
     for img in timed:
         img.wait()
+    writer_s = time.perf_counter() - t_loop0
     chain.extend(timed)
     total_ms = max_over_ranks(dist, e0.elapsed_time(e1), dev)
 
@@ -612,6 +622,10 @@ def run_ours(args):
         "plain_p0": {"ms": round(plain_ms, 3), "gbs": round(S / (plain_ms * 1e-3) / 1e9, 2),
                      "what": "synchronize + full device->host copy of the footprint"},
         "verify": verify,
+        "writer": {"sink": args.sink, "fsync": args.sink == "file",
+                   "persisted_gbs": round(sum(drained_bytes) / writer_s / 1e9, 2),
+                   "what": "image bytes of the timed steps / host time from the first "
+                           "submit until every image is persisted"},
         "whole_step": {"gbs": round(world * S / (total_ms / steps * 1e-3) / 1e9, 2),
                        "what": "footprint bytes / wall-clock ms per step; each step also drains "
                                "its dirty pages over the host link"},
@@ -623,6 +637,9 @@ def run_ours(args):
     for img in chain:
         img.release()
     s.destroy()
+    if sink_dir:
+        import shutil
+        shutil.rmtree(sink_dir, ignore_errors=True)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

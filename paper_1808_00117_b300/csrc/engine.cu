@@ -287,8 +287,8 @@ void planner_main(crum_set* s) {
         s->needs_full = true;
         --s->inflight;
       } else {
-        s->write_q.push_back(img);
-        s->write_cv.notify_one();
+        s->done_q.push_back(img);
+        s->done_cv.notify_one();
       }
       s->cv.notify_all();
     }
@@ -319,8 +319,71 @@ crum_status write_file(const uint8_t* data, uint64_t n, const char* path, bool d
   return CRUM_OK;
 }
 
-void writer_main(crum_set* s) {
+// Last step of every image: PERSISTED (or the error), and its in-flight
+// reference dropped.
+void finish_image(crum_set* s, crum_image* img, crum_status st, const std::string& err) {
+  img->t_persisted_ms = std::chrono::duration<double, std::milli>(
+                            std::chrono::steady_clock::now() - img->t_submit)
+                            .count();
+  image_set_stage(img, CRUM_WAIT_PERSISTED, st, err);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (st != CRUM_OK) s->needs_full = true;
+    --s->inflight;
+    s->cv.notify_all();
+  }
+  image_unref(img);
+}
+
+// Drain watcher: marks each image DRAINED as soon as its device->host copies
+// are done (in drain order), whatever its sink, then hands images with a
+// file to write to the writer and finishes the others.
+void drainer_main(crum_set* s) {
   DeviceGuard dg(s->device);
+  for (;;) {
+    crum_image* img;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->done_cv.wait(lk, [&] { return s->stop || !s->done_q.empty(); });
+      if (s->done_q.empty()) return;
+      img = s->done_q.front();
+      s->done_q.pop_front();
+    }
+    crum_status st = wait_event(img->ev_drained, kBackgroundLimitNs);
+    if (st != CRUM_OK) {
+      finish_image(s, img, st, t_err);
+      continue;
+    }
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, img->ev_submit, img->ev_captured) == cudaSuccess)
+      img->t_captured_ms = ms;
+    if (cudaEventElapsedTime(&ms, img->ev_submit, img->ev_drained) == cudaSuccess)
+      img->t_drained_ms = ms;
+    if (cudaEventElapsedTime(&ms, img->ev_k0, img->ev_k1) == cudaSuccess) img->t_hash_ms = ms;
+    if (cudaEventElapsedTime(&ms, img->ev_k2, img->ev_captured) == cudaSuccess)
+      img->t_compact_ms = ms;
+    if (cudaEventElapsedTime(&ms, img->ev_d0, img->ev_drained) == cudaSuccess)
+      img->t_drain_ms = ms;
+    std::memcpy(&img->checksum, trailer_dst(img), 8);
+    image_set_stage(img, CRUM_WAIT_DRAINED, img->collisions ? CRUM_ECOLLISION : CRUM_OK, "");
+    if (img->drop_payload) {
+      std::lock_guard<std::mutex> lk(img->mu);
+      img->pool->free(img->host, img->host_len);
+      img->host = nullptr;
+      img->host_len = 0;
+    } else if (!img->sink_path.empty()) {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->write_q.push_back(img);
+      s->write_cv.notify_one();
+      continue;
+    }
+    finish_image(s, img, CRUM_OK, "");
+  }
+}
+
+// Writer: persists drained images to their files, one at a time, while
+// later images keep draining (the forked child's role, Section 3.3).
+void writer_main(crum_set* s) {
   for (;;) {
     crum_image* img;
     {
@@ -330,42 +393,8 @@ void writer_main(crum_set* s) {
       img = s->write_q.front();
       s->write_q.pop_front();
     }
-    crum_status st = wait_event(img->ev_drained, kBackgroundLimitNs);
-    std::string err = st == CRUM_OK ? "" : t_err;
-    if (st == CRUM_OK) {
-      float ms = 0;
-      if (cudaEventElapsedTime(&ms, img->ev_submit, img->ev_captured) == cudaSuccess)
-        img->t_captured_ms = ms;
-      if (cudaEventElapsedTime(&ms, img->ev_submit, img->ev_drained) == cudaSuccess)
-        img->t_drained_ms = ms;
-      if (cudaEventElapsedTime(&ms, img->ev_k0, img->ev_k1) == cudaSuccess) img->t_hash_ms = ms;
-      if (cudaEventElapsedTime(&ms, img->ev_k2, img->ev_captured) == cudaSuccess)
-        img->t_compact_ms = ms;
-      if (cudaEventElapsedTime(&ms, img->ev_d0, img->ev_drained) == cudaSuccess)
-        img->t_drain_ms = ms;
-      std::memcpy(&img->checksum, trailer_dst(img), 8);
-      image_set_stage(img, CRUM_WAIT_DRAINED, img->collisions ? CRUM_ECOLLISION : CRUM_OK, "");
-      if (img->drop_payload) {
-        std::lock_guard<std::mutex> lk(img->mu);
-        img->pool->free(img->host, img->host_len);
-        img->host = nullptr;
-        img->host_len = 0;
-      } else if (!img->sink_path.empty()) {
-        st = write_file(img->host, img->image_bytes, img->sink_path.c_str(), img->do_fsync);
-        if (st != CRUM_OK) err = t_err;
-      }
-    }
-    img->t_persisted_ms = std::chrono::duration<double, std::milli>(
-                              std::chrono::steady_clock::now() - img->t_submit)
-                              .count();
-    image_set_stage(img, CRUM_WAIT_PERSISTED, st, err);
-    {
-      std::lock_guard<std::mutex> lk(s->mu);
-      if (st != CRUM_OK) s->needs_full = true;
-      --s->inflight;
-      s->cv.notify_all();
-    }
-    image_unref(img);
+    const crum_status st = write_file(img->host, img->image_bytes, img->sink_path.c_str(), img->do_fsync);
+    finish_image(s, img, st, st == CRUM_OK ? "" : t_err);
   }
 }
 
@@ -764,6 +793,7 @@ crum_status crum_set_create(const crum_config* cfg_in, crum_set** out) {
   }
   crum_set* raw = s.release();
   raw->planner = std::thread(planner_main, raw);
+  raw->drainer = std::thread(drainer_main, raw);
   raw->writer = std::thread(writer_main, raw);
   *out = raw;
   return CRUM_OK;
@@ -778,9 +808,11 @@ crum_status crum_set_destroy(crum_set* s) {
     s->cv.wait_for(lk, std::chrono::seconds(600), [&] { return s->inflight == 0; });
     s->stop = true;
     s->plan_cv.notify_all();
+    s->done_cv.notify_all();
     s->write_cv.notify_all();
   }
   if (s->planner.joinable()) s->planner.join();
+  if (s->drainer.joinable()) s->drainer.join();
   if (s->writer.joinable()) s->writer.join();
   cudaStreamSynchronize(s->cap_stream);
   cudaStreamSynchronize(s->drain_stream);
@@ -1121,7 +1153,7 @@ crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, cr
     ga.s_end = s->n_pages;
   }
 
-  image_ref(img);  // in-flight reference, dropped by the writer
+  image_ref(img);  // in-flight reference, dropped when the image is finished
   s->inflight++;
   H.drain_enqueued = false;
   auto unwind = [&](crum_status e) {
@@ -1170,8 +1202,8 @@ crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, cr
       image_unref(img);
       return bail(st);
     }
-    s->write_q.push_back(img);
-    s->write_cv.notify_one();
+    s->done_q.push_back(img);
+    s->done_cv.notify_one();
   }
   image_ref(img);  // the set's reference as the newest chain link
   image_unref(s->last);

@@ -3,11 +3,13 @@
 // The paper's checkpoint (Section 3.4) copies every region device -> host
 // after draining the device, and its forked checkpoint (Section 3.3) lets a
 // child process write the image while the application continues.  Here the
-// "child" is a pair of host threads per set:
+// "child" is three host threads per set:
 //   planner  learns each capture's dirty count from a mapped pinned mailbox,
 //            sizes the image and queues the device->host drain on the drain
 //            stream;
-//   writer   waits for the drain, then hands the image to its sink.
+//   drainer  marks each image DRAINED when its copies are done;
+//   writer   persists drained images to files (memory and null sinks need
+//            no writer), so slow storage never delays DRAINED.
 // The application's stream only waits for the device-side capture (hash,
 // scan, gather into staging); the staging buffer is split in two halves
 // that alternate between consecutive checkpoints so a capture never waits
@@ -179,9 +181,9 @@ struct crum_set {
   // copies on the drain stream, and are overwritten by the next copy
   uint8_t* bounce = nullptr;
   std::mutex bounce_mu;
-  std::deque<crum_image*> plan_q, write_q;
-  std::condition_variable plan_cv, write_cv;
-  std::thread planner, writer;
+  std::deque<crum_image*> plan_q, done_q, write_q;
+  std::condition_variable plan_cv, done_cv, write_cv;
+  std::thread planner, drainer, writer;
   bool stop = false;
   int inflight = 0;
 };
