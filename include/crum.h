@@ -119,6 +119,10 @@ typedef struct crum_config {
                                   not copied (a rollback moves only what changed;
                                   a changed page with an equal hash, probability
                                   2^-64, is left as it is, as a checkpoint would) */
+    int max_pending;           /* > 0: crum_checkpoint waits until fewer than this
+                                  many of the set's images are not yet PERSISTED,
+                                  so a sink slower than the checkpoints bounds the
+                                  pinned host memory they hold; 0: no bound */
 } crum_config;
 
 typedef enum crum_restore_mode {

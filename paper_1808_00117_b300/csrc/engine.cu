@@ -752,6 +752,7 @@ crum_status crum_set_create(const crum_config* cfg_in, crum_set** out) {
       cfg.gather_mapping < -1 || cfg.gather_mapping > 5)
     return fail(CRUM_EINVAL, "mapping out of range");
   if (cfg.restore_mode < 0 || cfg.restore_mode > 3) return fail(CRUM_EINVAL, "bad restore_mode");
+  if (cfg.max_pending < 0) return fail(CRUM_EINVAL, "bad max_pending");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg.device < 0 || cfg.device >= ndev) {
     cudaGetLastError();
@@ -1055,6 +1056,9 @@ crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, cr
   if (s->half_slots == 0) return fail(CRUM_EINVAL, "no staging bound to this set");
   crum_status st = ensure_capacity(s, lk);
   if (st != CRUM_OK) return st;
+  if (s->cfg.max_pending > 0 &&
+      !s->cv.wait_for(lk, std::chrono::seconds(600), [&] { return s->inflight < s->cfg.max_pending; }))
+    return fail(CRUM_ETIMEOUT, "timed out waiting for earlier images to be persisted");
   const int h = s->next_half;
   Half& H = s->half[h];
   if (!s->cv.wait_for(lk, std::chrono::seconds(600), [&] { return H.drain_enqueued; }))

@@ -669,3 +669,29 @@ def test_no_payload_keeps_checksum_and_chain(staging):
     img.release()
     img2.release()
     s.destroy()
+
+
+@pytest.mark.gpu
+def test_max_pending_bounds_unpersisted_images(tmp_path):
+    """With max_pending = 1 and a file sink, a checkpoint call returns only
+    after the previous image is persisted; every file is the oracle's image."""
+    sizes = [6 * P + 8]
+    bufs = device_buffers(sizes, seed=23)
+    s = make_set(bufs, sink=crum.SINK_FILE, sink_dir=str(tmp_path), max_pending=1)
+    o = oracle.OracleSet(sizes)
+    imgs, exps = [], []
+    for step in range(4):
+        if step:
+            mutate(bufs, sizes, 0.5, seed=230 + step)
+        img = s.checkpoint(stream_handle())
+        if imgs:
+            assert imgs[-1].info()["stage"] == crum.WAIT_PERSISTED
+        imgs.append(img)
+        exps.append(o.checkpoint(host_copies(bufs))[0])
+    for img, exp in zip(imgs, exps):
+        img.wait()
+        assert first_diff(img.to_bytes(), exp) is None
+        img.release()
+    files = sorted(tmp_path.iterdir(), key=lambda x: int(x.stem.rsplit("_", 1)[1]))
+    assert [f.read_bytes() for f in files] == exps
+    s.destroy()
