@@ -355,13 +355,18 @@ typedef struct crum_server_config {
     int device;
     uint64_t staging_budget;  /* device bytes lent to admitted requests; 0: 16 GiB */
     int max_inflight;         /* requests on the device at once; 0: 8 */
-    int max_checkpoints;      /* of those, checkpoint requests at once (their drains share
-                                 the device->host link); 0: 1; negative: no separate limit */
+    int max_checkpoints;      /* of those, checkpoint requests at once; 0: 2 with
+                                 serialized drains, else 1; negative: no separate limit */
     int max_restores;         /* of those, restore requests at once (host->device link);
                                  0: 1; negative: no separate limit.  One of each, in
                                  arrival order, keeps large requests from being slowed by
                                  later arrivals while the two link directions and the
                                  device overlap */
+    int serialize_drains;     /* 0 (default) or 1: the clients' checkpoint drains cross
+                                 the link one at a time, in admission order, while their
+                                 captures overlap, so max_checkpoints > 1 keeps the link
+                                 busy without sharing it; negative: each drain starts as
+                                 soon as its capture is done */
 } crum_server_config;
 
 #define CRUM_REQ_CHECKPOINT 0      /* incremental checkpoint of the client's set */

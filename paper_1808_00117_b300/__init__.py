@@ -52,7 +52,7 @@ class Config(ctypes.Structure):
 class ServerConfig(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("staging_budget", ctypes.c_uint64),
                 ("max_inflight", ctypes.c_int), ("max_checkpoints", ctypes.c_int),
-                ("max_restores", ctypes.c_int)]
+                ("max_restores", ctypes.c_int), ("serialize_drains", ctypes.c_int)]
 
 
 class RequestInfo(ctypes.Structure):
@@ -338,8 +338,9 @@ class Server:
     """Checkpoint/restore request server (``crum_server``)."""
 
     def __init__(self, device: int = 0, staging_budget: int = 16 << 30, max_inflight: int = 8,
-                 max_checkpoints: int = 0, max_restores: int = 0):
-        cfg = ServerConfig(device, staging_budget, max_inflight, max_checkpoints, max_restores)
+                 max_checkpoints: int = 0, max_restores: int = 0, serialize_drains: int = 0):
+        cfg = ServerConfig(device, staging_budget, max_inflight, max_checkpoints, max_restores,
+                           serialize_drains)
         h = _VP()
         _check(load().crum_server_create(ctypes.byref(cfg), ctypes.byref(h)), "crum_server_create")
         self.handle = h.value

@@ -230,6 +230,11 @@ uint8_t* trailer_dst(crum_image* img) { return img->host + img->host_len - 8; }
 crum_status enqueue_drain(crum_set* s, crum_image* img, Half& H) {
   const uint64_t A = img->n_allocs, n = img->n_dirty;
   CK(cudaStreamWaitEvent(s->drain_stream, img->ev_captured, 0));
+  if (img->ticket >= 0 && s->sequencer) {
+    crum::DrainSequencer* q = s->sequencer.get();
+    std::lock_guard<std::mutex> lk(q->mu);
+    if (q->tail_recorded) CK(cudaStreamWaitEvent(s->drain_stream, q->tail, 0));
+  }
   CK(cudaEventRecord(img->ev_d0, s->drain_stream));
   CK(cudaMemcpyAsync(img->host, H.meta, meta_bytes(A, n), cudaMemcpyDeviceToHost, s->drain_stream));
   // the null sink drains too (the bytes cross the link); the writer drops them
@@ -252,6 +257,27 @@ crum_status alloc_image_host(crum_set* s, crum_image* img) {
   return CRUM_OK;
 }
 
+// Waits (host) until it is this image's turn to queue its drain.
+crum_status sequencer_turn(crum::DrainSequencer* q, crum_image* img) {
+  std::unique_lock<std::mutex> lk(q->mu);
+  const bool ok = q->cv.wait_for(lk, std::chrono::seconds(600), [&] {
+    return q->next == static_cast<uint64_t>(img->ticket);
+  });
+  return ok ? CRUM_OK : fail(CRUM_ETIMEOUT, "timed out waiting for the drain order");
+}
+
+// Marks the image's drain queued (or skipped): later drains wait for it.
+void sequencer_done(crum::DrainSequencer* q, crum_image* img, cudaStream_t drain, bool queued) {
+  std::lock_guard<std::mutex> lk(q->mu);
+  (void)img;
+  if (queued) {
+    if (q->tail == nullptr) cudaEventCreateWithFlags(&q->tail, cudaEventDisableTiming);
+    if (q->tail != nullptr && cudaEventRecord(q->tail, drain) == cudaSuccess) q->tail_recorded = true;
+  }
+  q->next++;
+  q->cv.notify_all();
+}
+
 void planner_main(crum_set* s) {
   DeviceGuard dg(s->device);
   for (;;) {
@@ -266,6 +292,16 @@ void planner_main(crum_set* s) {
     Half& H = s->half[img->half];
     crum_status st = wait_event(H.ev_scanned, kBackgroundLimitNs);
     std::string err = st == CRUM_OK ? "" : t_err;
+    crum::DrainSequencer* q = img->ticket >= 0 ? s->sequencer.get() : nullptr;
+    bool my_turn = false;  // a failed capture still takes (and passes) its turn
+    if (q != nullptr) {
+      const crum_status t = sequencer_turn(q, img);
+      my_turn = t == CRUM_OK;
+      if (st == CRUM_OK && !my_turn) {
+        st = t;
+        err = t_err;
+      }
+    }
     if (st == CRUM_OK) {
       img->n_dirty = reinterpret_cast<volatile uint64_t*>(H.mailbox)[0];
       img->collisions = reinterpret_cast<volatile uint64_t*>(H.mailbox)[1];
@@ -275,6 +311,7 @@ void planner_main(crum_set* s) {
       if (st == CRUM_OK) st = enqueue_drain(s, img, H);
       if (st != CRUM_OK) err = t_err;
     }
+    if (my_turn) sequencer_done(q, img, s->drain_stream, st == CRUM_OK);
     if (st != CRUM_OK) {
       // keep later users of this half ordered after the capture
       cudaEventRecord(H.ev_drained, s->cap_stream);
@@ -1195,6 +1232,10 @@ crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, cr
     ce = cudaStreamWaitEvent(app, img->ev_captured, 0);
     if (ce != cudaSuccess) return unwind(fail(CRUM_ECUDA, "app wait: %s", cudaGetErrorString(ce)));
     s->next_half = h ^ 1;
+    if (s->sequencer) {
+      std::lock_guard<std::mutex> qlk(s->sequencer->mu);
+      img->ticket = static_cast<int64_t>(s->sequencer->issued++);
+    }
     s->plan_q.push_back(img);
     s->plan_cv.notify_one();
   } else {
@@ -1660,6 +1701,16 @@ namespace crum {
 // Point both staging halves of an external-staging set at `payload`
 // (`slots` pages), or detach them (payload == nullptr).  The caller (the
 // server) guarantees the set has nothing in flight.
+// A server's clients share one drain order (see DrainSequencer); nullptr
+// detaches the set.
+crum_status set_drain_sequencer(crum_set* s, std::shared_ptr<DrainSequencer> q) {
+  std::unique_lock<std::mutex> lk(s->mu);
+  crum_status st = quiesce(s, lk);
+  if (st != CRUM_OK) return st;
+  s->sequencer = std::move(q);
+  return CRUM_OK;
+}
+
 crum_status bind_staging(crum_set* s, uint8_t* payload, uint64_t slots) {
   std::unique_lock<std::mutex> lk(s->mu);
   if (!s->cfg.external_staging) return fail(CRUM_EINVAL, "set owns its staging");

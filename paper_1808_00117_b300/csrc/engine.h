@@ -95,6 +95,23 @@ struct CaptureGraph {
   uint64_t epoch = 0;
 };
 
+// Orders the device->host drains of several sets (a server's clients) so
+// they cross the link one at a time, in the order the checkpoints were
+// submitted, while their captures may overlap.  Each drain waits on the
+// device for the previous one (one event, re-recorded by each drain) and,
+// on the host, for its turn to be queued.
+struct DrainSequencer {
+  std::mutex mu;
+  std::condition_variable cv;
+  uint64_t issued = 0;  // tickets handed out
+  uint64_t next = 0;    // ticket whose drain may be queued now
+  cudaEvent_t tail = nullptr;  // recorded after the last queued drain
+  bool tail_recorded = false;
+  ~DrainSequencer() {
+    if (tail) cudaEventDestroy(tail);
+  }
+};
+
 }  // namespace crum
 
 struct crum_image {
@@ -124,6 +141,7 @@ struct crum_image {
   double t_hash_ms = 0, t_compact_ms = 0, t_drain_ms = 0;
   int half = 0;
   bool drop_payload = false;  // null sink
+  int64_t ticket = -1;        // drain order under a DrainSequencer
   std::string sink_path;
   bool do_fsync = false;
 };
@@ -181,6 +199,7 @@ struct crum_set {
   // copies on the drain stream, and are overwritten by the next copy
   uint8_t* bounce = nullptr;
   std::mutex bounce_mu;
+  std::shared_ptr<crum::DrainSequencer> sequencer;  // set by a server
   std::deque<crum_image*> plan_q, done_q, write_q;
   std::condition_variable plan_cv, done_cv, write_cv;
   std::thread planner, drainer, writer;

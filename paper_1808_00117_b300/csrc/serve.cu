@@ -27,6 +27,7 @@
 
 namespace crum {
 crum_status bind_staging(crum_set* s, uint8_t* payload, uint64_t slots);
+crum_status set_drain_sequencer(crum_set* s, std::shared_ptr<DrainSequencer> q);
 void set_last_error(const char* msg);
 }  // namespace crum
 
@@ -82,6 +83,7 @@ struct crum_server {
   Clock::time_point t_first{}, t_last{};
   bool have_first = false;
   uint32_t peak_inflight = 0;
+  std::shared_ptr<crum::DrainSequencer> sequencer;  // cfg.serialize_drains
 };
 
 namespace {
@@ -322,8 +324,10 @@ crum_status crum_server_create(const crum_server_config* cfg, crum_server** out)
   if (cfg) S->cfg = *cfg;
   if (S->cfg.staging_budget == 0) S->cfg.staging_budget = 16ull << 30;
   if (S->cfg.max_inflight <= 0) S->cfg.max_inflight = 8;
-  // per-kind limits: 0 means the default of one, negative means none
-  if (S->cfg.max_checkpoints == 0) S->cfg.max_checkpoints = 1;
+  S->cfg.serialize_drains = S->cfg.serialize_drains >= 0 ? 1 : 0;
+  // per-kind limits: 0 means the default (two checkpoints when their drains
+  // are serialized, else one; one restore), negative means none
+  if (S->cfg.max_checkpoints == 0) S->cfg.max_checkpoints = S->cfg.serialize_drains ? 2 : 1;
   if (S->cfg.max_restores == 0) S->cfg.max_restores = 1;
   if (S->cfg.max_checkpoints < 0) S->cfg.max_checkpoints = 0;
   if (S->cfg.max_restores < 0) S->cfg.max_restores = 0;
@@ -343,6 +347,7 @@ crum_status crum_server_create(const crum_server_config* cfg, crum_server** out)
     return srv_fail(CRUM_ENOMEM, "cannot allocate the staging budget");
   }
   S->free_list.emplace(0, S->cfg.staging_budget);
+  if (S->cfg.serialize_drains) S->sequencer = std::make_shared<crum::DrainSequencer>();
   crum_server* raw = S.release();
   raw->th = std::thread(server_main, raw);
   *out = raw;
@@ -357,8 +362,10 @@ crum_status crum_server_destroy(crum_server* S) {
     S->wake.notify_all();
   }
   if (S->th.joinable()) S->th.join();
-  for (Client& c : S->clients)
+  for (Client& c : S->clients) {
     if (c.newest) crum_image_release(c.newest);
+    if (S->sequencer) crum::set_drain_sequencer(c.set, nullptr);
+  }
   cudaFree(S->pool);
   delete S;
   return CRUM_OK;
@@ -375,6 +382,8 @@ crum_status crum_server_add_client(crum_server* S, crum_set* set, crum_stream_t 
   std::lock_guard<std::mutex> lk(S->mu);
   if (pages * crum::kPage > S->cfg.staging_budget)
     return srv_fail(CRUM_EINVAL, "client footprint exceeds the whole staging budget");
+  if (S->sequencer && crum::set_drain_sequencer(set, S->sequencer) != CRUM_OK)
+    return srv_fail(CRUM_EBUSY, "client set has checkpoints in flight");
   Client c;
   c.set = set;
   c.stream = static_cast<cudaStream_t>(app_stream);

@@ -92,11 +92,14 @@ def run_sequence(server, clients, rounds, restore_at):
     return got, exp
 
 
-@pytest.mark.parametrize("lanes,mode", [((-1, -1), crum.RESTORE_AUTO), ((1, 1), crum.RESTORE_AUTO),
-                                        ((1, 1), crum.RESTORE_DELTA)])
-def test_same_alone_and_in_the_mix(lanes, mode):
+@pytest.mark.parametrize("lanes,mode,serial", [((-1, -1), crum.RESTORE_AUTO, -1),
+                                               ((1, 1), crum.RESTORE_AUTO, -1),
+                                               ((1, 1), crum.RESTORE_DELTA, -1),
+                                               ((3, 1), crum.RESTORE_DELTA, 1),
+                                               ((0, 0), crum.RESTORE_AUTO, 0)])
+def test_same_alone_and_in_the_mix(lanes, mode, serial):
     srv = crum.Server(staging_budget=1 << 30, max_inflight=3, max_checkpoints=lanes[0],
-                      max_restores=lanes[1])
+                      max_restores=lanes[1], serialize_drains=serial)
     mix = [Client(srv, i, s, mode) for i, s in enumerate(SIZES)]
     got_mix, exp = run_sequence(srv, mix, rounds=4, restore_at=2)
     stats = srv.drain()
@@ -108,7 +111,7 @@ def test_same_alone_and_in_the_mix(lanes, mode):
     srv.destroy()
     # each client alone, same seeds: same images
     for i, s in enumerate(SIZES):
-        srv1 = crum.Server(staging_budget=1 << 30, max_inflight=3)
+        srv1 = crum.Server(staging_budget=1 << 30, max_inflight=3, serialize_drains=serial)
         alone = Client(srv1, i, s, mode)
         got_alone, _ = run_sequence(srv1, [alone], rounds=4, restore_at=2)
         assert got_alone[i] == got_mix[i], f"client {i} alone differs from the mix"
