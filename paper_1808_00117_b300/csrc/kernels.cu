@@ -247,39 +247,69 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(ScanArgs a) {
   __shared__ uint64_t red[32];
   __shared__ uint32_t total_sh;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint64_t per = (a.n_words + kScanThreads - 1) / kScanThreads;
-  const uint64_t w0 = min(static_cast<uint64_t>(tid) * per, a.n_words);
-  const uint64_t w1 = min(w0 + per, a.n_words);
+  // Each warp owns a contiguous segment of bitmap words and walks it 32
+  // words at a time, lane l reading word base + l, so every load of the
+  // warp is one contiguous 128-byte line (a thread-contiguous split made
+  // each warp load touch 32 lines).
+  constexpr int kWarps = kScanThreads / 32;
+  const uint64_t seg = (a.n_words + kWarps - 1) / kWarps;
+  const uint64_t s0 = min(static_cast<uint64_t>(warp) * seg, a.n_words);
+  const uint64_t s1 = min(s0 + seg, a.n_words);
+  // kB lines per batch are loaded before any is used: one CTA has to keep
+  // enough loads in flight on its own
+  constexpr int kB = 16;
   uint32_t cnt = 0;
-  for (uint64_t w = w0; w < w1; ++w) cnt += __popc(a.mask[w]);
-  uint32_t incl = cnt;
+  for (uint64_t base = s0; base < s1; base += 32 * kB) {
+    uint32_t m[kB];
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
+    for (int j = 0; j < kB; ++j) {
+      const uint64_t w = base + 32 * j + lane;
+      m[j] = w < s1 ? __ldg(a.mask + w) : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < kB; ++j) cnt += __popc(m[j]);
   }
-  if (lane == 31) wsum[warp] = incl;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if (lane == 0) wsum[warp] = cnt;
   __syncthreads();
   if (warp == 0) {
     const uint32_t x = wsum[lane];
-    uint32_t s = x;
+    uint32_t incl = x;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
-      if (lane >= o) s += y;
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
     }
-    wsum[lane] = s - x;  // exclusive prefix of warp totals
+    wsum[lane] = incl - x;  // exclusive prefix of the segments' totals
+    if (lane == 31) total_sh = incl;
   }
   __syncthreads();
-  uint32_t run = wsum[warp] + incl - cnt;
-  for (uint64_t w = w0; w < w1; ++w) {
-    a.word_offset[w] = run;
-    run += __popc(a.mask[w]);
+  uint32_t carry = wsum[warp];
+  for (uint64_t base = s0; base < s1; base += 32 * kB) {
+    uint32_t c[kB];
+#pragma unroll
+    for (int j = 0; j < kB; ++j) {
+      const uint64_t w = base + 32 * j + lane;
+      c[j] = w < s1 ? __popc(__ldg(a.mask + w)) : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < kB; ++j) {
+      const uint64_t w = base + 32 * j + lane;
+      uint32_t incl = c[j];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      if (w < s1) a.word_offset[w] = carry + incl - c[j];
+      carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
   }
+  const uint32_t run = total_sh;
   if (tid == kScanThreads - 1) {
     a.word_offset[a.n_words] = run;
     *a.n_dirty_out = run;
-    total_sh = run;
     if (a.mailbox != nullptr) {
       a.mailbox[0] = run;
       a.mailbox[1] = a.collisions != nullptr ? *a.collisions : 0ull;
@@ -310,7 +340,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(ScanArgs a) {
       }
     } else {
       const uint64_t e = (k - 8) >> 1;
-      w = ((k - 8) & 1) ? a.allocs[e].bytes : static_cast<uint64_t>(a.allocs[e].id);
+      w = ((k - 8) & 1) ? __ldg(&a.allocs[e].bytes) : static_cast<uint64_t>(__ldg(&a.allocs[e].id));
     }
     meta[k] = w;
     cks += mix(w ^ (k * kPhi));
