@@ -115,3 +115,62 @@ def test_random_scenario(seed):
     for im in images:
         im.release()
     s.destroy()
+
+
+def test_sets_used_from_several_host_threads():
+    """Four host threads, each with its own set, stream and allocations,
+    checkpoint and restore at the same time; every image matches the
+    oracle's and every restore returns its thread's memory."""
+    import threading
+    t = torch()
+    errors = []
+
+    def worker(k):
+        try:
+            rng = np.random.default_rng(500 + k)
+            sizes = [int(rng.integers(1, 20)) * P + int(rng.integers(0, P)), 3 * P]
+            stream = t.cuda.Stream()
+            with t.cuda.stream(stream):
+                bufs = [t.empty(n, dtype=t.uint8, device="cuda") for n in sizes]
+                for i, b in enumerate(bufs):
+                    W.fill_(b, 900 + 10 * k + i, "u32")
+            stream.synchronize()
+            s = crum.CheckpointSet(restore_mode=int(k % 4))
+            for b in bufs:
+                s.register(b.data_ptr(), b.numel())
+            o = oracle.OracleSet(sizes)
+            imgs = []
+            for step in range(5):
+                if step:
+                    with t.cuda.stream(stream):
+                        for i, (b, n) in enumerate(zip(bufs, sizes)):
+                            pages = W.pages_of(n)
+                            W.mutate_pages_(b, np.sort(rng.choice(pages, size=max(1, pages // 3), replace=False)),
+                                            100 * k + 10 * step + i)
+                img = s.checkpoint(stream.cuda_stream)
+                img.wait()
+                stream.synchronize()
+                state = [b.cpu().numpy().copy() for b in bufs]
+                exp, *_ = o.checkpoint(state)
+                if first_diff(img.to_bytes(), exp) is not None:
+                    errors.append(f"thread {k} step {step}: image differs")
+                imgs.append(img)
+            with t.cuda.stream(stream):
+                for b in bufs:
+                    b.fill_(0xAB)
+            s.restore(imgs[-1], stream.cuda_stream)
+            stream.synchronize()
+            if not all(np.array_equal(b.cpu().numpy(), w) for b, w in zip(bufs, state)):
+                errors.append(f"thread {k}: restore differs")
+            for im in imgs:
+                im.release()
+            s.destroy()
+        except Exception as e:  # reported below, on the main thread
+            errors.append(f"thread {k}: {e!r}")
+
+    threads = [threading.Thread(target=worker, args=(k,)) for k in range(4)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    assert not errors, errors
