@@ -983,7 +983,7 @@ def run_serving(args):
     torch.cuda.set_device(0)
     crum.load()
     n_clients, n_req = 32, args.requests
-    sizes = W.loguniform_sizes(0x5EED + 3, n_clients, 1 << 20, 4 << 30, total=None, round_to=W.PAGE)
+    sizes = W.workload("serving").sizes
     kinds = ["i32", "fp32", "fp64"]
     rng = np.random.default_rng(0x5EED + 3)
     req_client = rng.integers(0, n_clients, size=n_req)

@@ -90,6 +90,11 @@ def workload(name: str) -> Workload:
     if name == "large":
         sizes = loguniform_sizes(0x5EED + 4, 4096, 64 * KiB, 2 * GiB, 140 * GiB)
         return Workload(name, sizes, "fp32", 0.02, 50, "uniform", 0x5EED + 4)
+    if name == "serving":
+        # 32 clients, footprints log-uniform 1 MiB .. 4 GiB (not rescaled);
+        # the mean of the per-request U[1 %, 50 %] rewrite as the dirty share
+        sizes = loguniform_sizes(0x5EED + 3, 32, 1 * MiB, 4 * GiB, None, round_to=PAGE)
+        return Workload(name, sizes, "u32", 0.255, 2000, "uniform", 0x5EED + 3)
     raise KeyError(name)
 
 
