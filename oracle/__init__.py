@@ -66,6 +66,13 @@ def lib():
         L.oracle_check_image.argtypes, L.oracle_check_image.restype = [vp, u64], i32
         L.oracle_apply_image.argtypes = [vp, u64, vp, vp, u32, vp]
         L.oracle_apply_image.restype = i32
+        L.oracle_bpd_encode.argtypes, L.oracle_bpd_encode.restype = [vp, vp], u64
+        L.oracle_bpd_decode.argtypes, L.oracle_bpd_decode.restype = [vp, u64, vp], i32
+        L.oracle_build_cimage.argtypes = [vp, vp, vp, u32, vp, vp, i32, u64, u64, vp, vp, vp, u64]
+        L.oracle_build_cimage.restype = u64
+        L.oracle_check_cimage.argtypes, L.oracle_check_cimage.restype = [vp, u64], i32
+        L.oracle_apply_cimage.argtypes = [vp, u64, vp, vp, u32, vp, vp]
+        L.oracle_apply_cimage.restype = i32
         _lib = L
     return _lib
 
@@ -150,7 +157,32 @@ def image_size(n_allocs: int, n_dirty: int) -> int:
     return int(lib().oracle_image_size(n_allocs, n_dirty))
 
 
-def build_image(allocs, ids, h, dirty_flags, full: bool, seq: int, parent_seq: int) -> bytes:
+def bpd_encode(slot) -> bytes:
+    """Byte-plane dictionary code of one 65,536-byte slot (65,536 bytes back
+    means stored as is)."""
+    b = _u8(np.frombuffer(slot, dtype=np.uint8) if isinstance(slot, (bytes, bytearray)) else slot)
+    assert b.size == PAGE
+    out = np.zeros(PAGE, dtype=np.uint8)
+    n = int(lib().oracle_bpd_encode(_ptr(b), _ptr(out)))
+    return out[:n].tobytes()
+
+
+def bpd_decode(enc: bytes):
+    """(status, 65,536-byte slot) of an encoded slot."""
+    b = np.frombuffer(enc, dtype=np.uint8)
+    out = np.zeros(PAGE, dtype=np.uint8)
+    st = int(lib().oracle_bpd_decode(_ptr(b) if b.size else 0, b.size, _ptr(out)))
+    return st, out.tobytes()
+
+
+def image_version(img) -> int:
+    return int(np.frombuffer(img[8:12], dtype=np.uint32)[0])
+
+
+def build_image(allocs, ids, h, dirty_flags, full: bool, seq: int, parent_seq: int,
+                compress: bool = False) -> bytes:
+    if compress:
+        return build_cimage(allocs, ids, h, dirty_flags, full, seq, parent_seq)
     allocs = [_u8(a) for a in allocs]
     sizes = np.array([a.size for a in allocs], dtype=np.uint64)
     ids = np.asarray(ids, dtype=np.uint32)
@@ -166,14 +198,48 @@ def build_image(allocs, ids, h, dirty_flags, full: bool, seq: int, parent_seq: i
     return out.tobytes()
 
 
+def build_cimage(allocs, ids, h, dirty_flags, full: bool, seq: int, parent_seq: int) -> bytes:
+    """The compressed (version 2) image of the dirty pages."""
+    allocs = [_u8(a) for a in allocs]
+    sizes = np.array([a.size for a in allocs], dtype=np.uint64)
+    ids = np.asarray(ids, dtype=np.uint32)
+    h = np.ascontiguousarray(h, dtype=np.uint64)
+    d = np.ascontiguousarray(dirty_flags, dtype=np.uint8)
+    n = int(d.astype(np.uint64).sum())
+    scratch = np.zeros(max(n, 1) * PAGE, dtype=np.uint8)
+    lens = np.zeros(max(n, 1), dtype=np.uint64)
+    ptrs = _ptr_array(allocs)
+    args = (_ptr(ptrs), _ptr(sizes), _ptr(ids), len(allocs), _ptr(h), _ptr(d), int(bool(full)),
+            seq, parent_seq, _ptr(scratch), _ptr(lens))
+    size = int(lib().oracle_build_cimage(*args, None, 0))
+    out = np.zeros(size, dtype=np.uint8)
+    got = lib().oracle_build_cimage(*args, _ptr(out), size)
+    assert got == size
+    return out.tobytes()
+
+
 def check_image(img) -> int:
     b = np.frombuffer(img, dtype=np.uint8)
+    if b.size >= 12 and image_version(img) == 2:
+        return int(lib().oracle_check_cimage(_ptr(b), b.size))
     return int(lib().oracle_check_image(_ptr(b), b.size))
 
 
 def apply_image(img, allocs, h_prev: np.ndarray | None) -> int:
     """Restore one image onto writable host arrays; updates h_prev in place."""
     b = np.frombuffer(img, dtype=np.uint8)
+    if b.size >= 12 and image_version(img) == 2:
+        allocs = [_u8(a) for a in allocs]
+        sizes = np.array([a.size for a in allocs], dtype=np.uint64)
+        hp = None
+        if h_prev is not None:
+            assert h_prev.dtype == np.uint64 and h_prev.flags["C_CONTIGUOUS"]
+            hp = _ptr(h_prev)
+        n = int(np.frombuffer(img[40:48], dtype=np.uint64)[0])
+        scratch = np.zeros(max(n, 1) * PAGE, dtype=np.uint8)
+        ptrs = _ptr_array(allocs)
+        return int(lib().oracle_apply_cimage(_ptr(b), b.size, _ptr(ptrs), _ptr(sizes),
+                                             len(allocs), hp, _ptr(scratch)))
     allocs = [_u8(a) for a in allocs]
     sizes = np.array([a.size for a in allocs], dtype=np.uint64)
     hp = None
@@ -194,7 +260,9 @@ class OracleSet:
     a chain base-to-end and installs the image hashes.
     """
 
-    def __init__(self, sizes: Sequence[int], ids: Sequence[int] | None = None):
+    def __init__(self, sizes: Sequence[int], ids: Sequence[int] | None = None,
+                 compress: bool = False):
+        self.compress = compress
         self.sizes = [int(s) for s in sizes]
         self.ids = list(ids) if ids is not None else list(range(len(self.sizes)))
         n = total_pages(self.sizes)
@@ -211,7 +279,7 @@ class OracleSet:
             d, collisions = verify(allocs, verify_prev, d)
         parent = self.last_seq if self.last_seq is not None else 0xFFFFFFFFFFFFFFFF
         is_full = full or self.last_seq is None
-        img = build_image(allocs, self.ids, h, d, is_full, self.seq, parent)
+        img = build_image(allocs, self.ids, h, d, is_full, self.seq, parent, self.compress)
         self.h_prev = h
         self.force[:] = 0
         self.last_seq = self.seq

@@ -60,6 +60,28 @@
  *   payload, n x 65536 bytes: the page's valid bytes, then zeros
  *   trailer: u64 checksum = the hash above applied to every preceding byte
  *            of the image, with word indices counted from the image start.
+ *
+ * Compressed form (version 2, flags bit 1 set): the same header fields,
+ * then the allocation table, page table and page hashes as above, then a
+ * slot-offset table, n x u64 (offset of each encoded slot from the payload
+ * start, ascending from 0), zeros up to the payload offset
+ * 64 + 16 A + 24 n rounded up to a multiple of 16, the encoded slots back to
+ * back, and the trailer.  A slot is the 65,536-byte payload slot above
+ * (valid bytes, then zeros), encoded by oracle_bpd_encode; an encoded length
+ * of 65,536 means the slot is stored as is.
+ *
+ * Byte-plane dictionary code of one slot (this build's compression of the
+ * drained bytes; the paper compresses whole images with gzip or LZ4 on the
+ * host, Section 4.4): plane j (j = 0..7) is the 8,192 bytes at offsets
+ * 8i + j.  For each plane let D be its distinct byte values in ascending
+ * order, k = |D| and b = ceil(log2 k) (b = 0 when k = 1).  A plane with
+ * b = 8 is stored as its 8,192 bytes; otherwise as D (k bytes, zero-padded
+ * to a multiple of 16) followed by 1,024 b bytes holding, for i = 0..8191,
+ * the position of plane byte i in D as b bits at bit offset i b (bit t of
+ * the stream is bit t mod 8 of byte t / 8).  The encoded slot is a 16-byte
+ * head (b of each plane, then k - 1 of each plane, 255 for a stored plane)
+ * and the eight plane sections in order; if that would not be shorter than
+ * 65,536 bytes the slot is stored as is.
  */
 #include <stdint.h>
 #include <stddef.h>
@@ -342,6 +364,280 @@ int oracle_apply_image(const uint8_t *img, uint64_t size,
         for (uint32_t b = 0; b < a; ++b)
             first += oracle_pages_of(bytes[b]);
         memcpy(data[a] + (uint64_t)p * OR_PAGE, payload + OR_PAGE * s,
+               oracle_valid_bytes(bytes[a], p));
+        if (h_prev)
+            h_prev[first + p] = get64(htab + 8 * s);
+    }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------ compressed form --- */
+
+#define OR_PLANE 8192ull
+
+static uint64_t round16(uint64_t x)
+{
+    return (x + 15) / 16 * 16;
+}
+
+/* Encode one 65,536-byte slot into out (room for 65,536 bytes); returns the
+ * encoded length, 65,536 meaning stored as is. */
+uint64_t oracle_bpd_encode(const uint8_t *slot, uint8_t *out)
+{
+    uint8_t dict[8][256];
+    int k[8], b[8];
+    uint64_t len = 16;
+    for (int j = 0; j < 8; ++j) {
+        uint8_t present[256];
+        memset(present, 0, sizeof present);
+        for (uint64_t i = 0; i < OR_PLANE; ++i)
+            present[slot[8 * i + j]] = 1;
+        k[j] = 0;
+        for (int v = 0; v < 256; ++v)
+            if (present[v])
+                dict[j][k[j]++] = (uint8_t)v;
+        b[j] = 0;
+        while ((1 << b[j]) < k[j])
+            b[j] = b[j] + 1;
+        if (b[j] == 8)
+            len += OR_PLANE;
+        else
+            len += round16((uint64_t)k[j]) + 1024ull * (uint64_t)b[j];
+    }
+    if (len >= OR_PAGE) {
+        memcpy(out, slot, OR_PAGE);
+        return OR_PAGE;
+    }
+    memset(out, 0, len);
+    for (int j = 0; j < 8; ++j) {
+        out[j] = (uint8_t)b[j];
+        out[8 + j] = b[j] == 8 ? 255 : (uint8_t)(k[j] - 1);
+    }
+    uint64_t pos = 16;
+    for (int j = 0; j < 8; ++j) {
+        if (b[j] == 8) {
+            for (uint64_t i = 0; i < OR_PLANE; ++i)
+                out[pos + i] = slot[8 * i + j];
+            pos += OR_PLANE;
+            continue;
+        }
+        memcpy(out + pos, dict[j], (size_t)k[j]);
+        pos += round16((uint64_t)k[j]);
+        for (uint64_t i = 0; i < OR_PLANE; ++i) {
+            int rank = 0;
+            while (dict[j][rank] != slot[8 * i + j])
+                rank = rank + 1;
+            for (int t = 0; t < b[j]; ++t) {
+                uint64_t bit = i * (uint64_t)b[j] + (uint64_t)t;
+                out[pos + bit / 8] |= (uint8_t)(((rank >> t) & 1) << (bit % 8));
+            }
+        }
+        pos += 1024ull * (uint64_t)b[j];
+    }
+    return len;
+}
+
+/* Decode `len` encoded bytes into a 65,536-byte slot.  OR_OK, or
+ * OR_CORRUPT for anything the encoder cannot have written. */
+int oracle_bpd_decode(const uint8_t *in, uint64_t len, uint8_t *slot)
+{
+    if (len == OR_PAGE) {
+        memcpy(slot, in, OR_PAGE);
+        return OR_OK;
+    }
+    if (len < 16 || len > OR_PAGE || len % 16 != 0)
+        return OR_CORRUPT;
+    uint64_t pos = 16;
+    for (int j = 0; j < 8; ++j) {
+        int b = in[j];
+        if (b == 8) {
+            if (in[8 + j] != 255 || pos + OR_PLANE > len)
+                return OR_CORRUPT;
+            for (uint64_t i = 0; i < OR_PLANE; ++i)
+                slot[8 * i + j] = in[pos + i];
+            pos += OR_PLANE;
+            continue;
+        }
+        if (b > 7)
+            return OR_CORRUPT;
+        int k = in[8 + j] + 1;
+        int canon = 0;
+        while ((1 << canon) < k)
+            canon = canon + 1;
+        if (canon != b)
+            return OR_CORRUPT;
+        const uint8_t *dict = in + pos;
+        if (pos + round16((uint64_t)k) + 1024ull * (uint64_t)b > len)
+            return OR_CORRUPT;
+        for (int v = 1; v < k; ++v)
+            if (dict[v] <= dict[v - 1])
+                return OR_CORRUPT;
+        pos += round16((uint64_t)k);
+        for (uint64_t i = 0; i < OR_PLANE; ++i) {
+            int rank = 0;
+            for (int t = 0; t < b; ++t) {
+                uint64_t bit = i * (uint64_t)b + (uint64_t)t;
+                rank |= ((in[pos + bit / 8] >> (bit % 8)) & 1) << t;
+            }
+            if (rank >= k)
+                return OR_CORRUPT;
+            slot[8 * i + j] = dict[rank];
+        }
+        pos += 1024ull * (uint64_t)b;
+    }
+    return pos == len ? OR_OK : OR_CORRUPT;
+}
+
+static uint64_t cimage_payload_off(uint32_t A, uint64_t n)
+{
+    return round16(OR_HDR + 16ull * A + 24ull * n);
+}
+
+/*
+ * Compressed image (version 2) of the pages with dirty[g] set into out;
+ * `scratch` holds n x 65,536 bytes (the encoded slots are made there
+ * first).  Returns the image size, 0 if out_size is too small.  With out
+ * NULL it only returns the size.
+ */
+uint64_t oracle_build_cimage(const uint8_t *const *data, const uint64_t *bytes,
+                             const uint32_t *ids, uint32_t n_allocs,
+                             const uint64_t *h, const uint8_t *dirty,
+                             int full, uint64_t seq, uint64_t parent_seq,
+                             uint8_t *scratch, uint64_t *lens,
+                             uint8_t *out, uint64_t out_size)
+{
+    uint64_t n_pages = oracle_total_pages(bytes, n_allocs);
+    uint64_t n = 0;
+    for (uint64_t g = 0; g < n_pages; ++g)
+        n += dirty[g] ? 1 : 0;
+    /* encode every dirty slot (valid bytes, then zeros) */
+    uint8_t slot[65536];
+    uint64_t g = 0, s = 0, total = 0;
+    for (uint32_t a = 0; a < n_allocs; ++a)
+        for (uint64_t p = 0; p < oracle_pages_of(bytes[a]); ++p) {
+            if (dirty[g]) {
+                memset(slot, 0, sizeof slot);
+                memcpy(slot, data[a] + p * OR_PAGE, oracle_valid_bytes(bytes[a], p));
+                lens[s] = oracle_bpd_encode(slot, scratch + OR_PAGE * s);
+                total += lens[s];
+                s = s + 1;
+            }
+            g = g + 1;
+        }
+    uint64_t payload_off = cimage_payload_off(n_allocs, n);
+    uint64_t size = payload_off + total + 8;
+    if (out == NULL)
+        return size;
+    if (out_size < size)
+        return 0;
+    memset(out, 0, size);
+    memcpy(out, "CRUMIMG1", 8);
+    put32(out + 8, 2);
+    put32(out + 12, (full ? 1u : 0u) | 2u);
+    put64(out + 16, seq);
+    put64(out + 24, full ? OR_NONE : parent_seq);
+    put32(out + 32, (uint32_t)OR_PAGE);
+    put32(out + 36, n_allocs);
+    put64(out + 40, n);
+    put64(out + 48, payload_off);
+    put64(out + 56, size);
+    uint8_t *atab = out + OR_HDR;
+    for (uint32_t a = 0; a < n_allocs; ++a) {
+        put32(atab + 16ull * a, ids[a]);
+        put64(atab + 16ull * a + 8, bytes[a]);
+    }
+    uint8_t *ptab = atab + 16ull * n_allocs;
+    uint8_t *htab = ptab + 8ull * n;
+    uint8_t *otab = htab + 8ull * n;
+    g = 0;
+    s = 0;
+    uint64_t off = 0;
+    for (uint32_t a = 0; a < n_allocs; ++a)
+        for (uint64_t p = 0; p < oracle_pages_of(bytes[a]); ++p) {
+            if (dirty[g]) {
+                put32(ptab + 8 * s, a);
+                put32(ptab + 8 * s + 4, (uint32_t)p);
+                put64(htab + 8 * s, h[g]);
+                put64(otab + 8 * s, off);
+                memcpy(out + payload_off + off, scratch + OR_PAGE * s, lens[s]);
+                off += lens[s];
+                s = s + 1;
+            }
+            g = g + 1;
+        }
+    put64(out + size - 8, oracle_hash_bytes(out, size - 8, 0));
+    return size;
+}
+
+/* Check a compressed image like oracle_check_image, plus its offset table
+ * (ascending from 0, each length a multiple of 16 in [16, 65536]). */
+int oracle_check_cimage(const uint8_t *img, uint64_t size)
+{
+    if (size < OR_HDR + 8 || memcmp(img, "CRUMIMG1", 8) != 0)
+        return OR_CORRUPT;
+    if (get32(img + 8) != 2 || (get32(img + 12) & 2u) == 0 || get32(img + 32) != (uint32_t)OR_PAGE)
+        return OR_CORRUPT;
+    uint32_t A = get32(img + 36);
+    uint64_t n = get64(img + 40);
+    if (n > size / 16)
+        return OR_CORRUPT;
+    uint64_t payload_off = get64(img + 48);
+    if (payload_off != cimage_payload_off(A, n) || get64(img + 56) != size || payload_off + 8 > size)
+        return OR_CORRUPT;
+    const uint8_t *otab = img + OR_HDR + 16ull * A + 16ull * n;
+    uint64_t total = size - 8 - payload_off;
+    for (uint64_t s = 0; s < n; ++s) {
+        uint64_t lo = get64(otab + 8 * s);
+        uint64_t hi = s + 1 < n ? get64(otab + 8 * (s + 1)) : total;
+        if ((s == 0 && lo != 0) || hi < lo || hi - lo < 16 || hi - lo > OR_PAGE || (hi - lo) % 16 != 0)
+            return OR_CORRUPT;
+    }
+    if (n == 0 && total != 0)
+        return OR_CORRUPT;
+    if (oracle_hash_bytes(img, size - 8, 0) != get64(img + size - 8))
+        return OR_CORRUPT;
+    return OR_OK;
+}
+
+/* Apply one compressed image, as oracle_apply_image does an uncompressed
+ * one (every slot is decoded first; nothing is written if any fails). */
+int oracle_apply_cimage(const uint8_t *img, uint64_t size,
+                        uint8_t *const *data, const uint64_t *bytes,
+                        uint32_t n_allocs, uint64_t *h_prev, uint8_t *scratch)
+{
+    int st = oracle_check_cimage(img, size);
+    if (st != OR_OK)
+        return st;
+    uint32_t A = get32(img + 36);
+    uint64_t n = get64(img + 40);
+    if (A != n_allocs)
+        return OR_MISMATCH;
+    const uint8_t *atab = img + OR_HDR;
+    for (uint32_t a = 0; a < A; ++a)
+        if (get64(atab + 16ull * a + 8) != bytes[a])
+            return OR_MISMATCH;
+    const uint8_t *ptab = atab + 16ull * A;
+    const uint8_t *htab = ptab + 8ull * n;
+    const uint8_t *otab = htab + 8ull * n;
+    uint64_t payload_off = get64(img + 48);
+    uint64_t total = size - 8 - payload_off;
+    for (uint64_t s = 0; s < n; ++s) {
+        uint32_t a = get32(ptab + 8 * s);
+        uint32_t p = get32(ptab + 8 * s + 4);
+        if (a >= A || (uint64_t)p >= oracle_pages_of(bytes[a]))
+            return OR_CORRUPT;
+        uint64_t lo = get64(otab + 8 * s);
+        uint64_t hi = s + 1 < n ? get64(otab + 8 * (s + 1)) : total;
+        if (oracle_bpd_decode(img + payload_off + lo, hi - lo, scratch + OR_PAGE * s) != OR_OK)
+            return OR_CORRUPT;
+    }
+    for (uint64_t s = 0; s < n; ++s) {
+        uint32_t a = get32(ptab + 8 * s);
+        uint32_t p = get32(ptab + 8 * s + 4);
+        uint64_t first = 0;
+        for (uint32_t b = 0; b < a; ++b)
+            first += oracle_pages_of(bytes[b]);
+        memcpy(data[a] + (uint64_t)p * OR_PAGE, scratch + OR_PAGE * s,
                oracle_valid_bytes(bytes[a], p));
         if (h_prev)
             h_prev[first + p] = get64(htab + 8 * s);
