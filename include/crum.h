@@ -41,6 +41,21 @@
  *   payload n x CRUM_PAGE_SIZE bytes (valid bytes, then zeros);
  *   trailer u64 = the hash formula above over every preceding image byte,
  *     word indices counted from the start of the image.
+ *
+ * Compressed form (crum_config.compress; version 2, flags bit 1): header,
+ * allocation table, page table and hashes as above, then n x u64 slot
+ * offsets (from the payload start, ascending from 0), zeros up to the
+ * payload offset round_up(64 + 16A + 24n, 16), the encoded slots back to
+ * back (slot s ends where slot s + 1 starts, the last at the trailer), the
+ * trailer.  A slot (64 KiB: valid bytes, then zeros) is split into 8 byte
+ * planes of 8,192 bytes (plane j = bytes 8i + j).  For a plane with k
+ * distinct values and b = ceil(log2 k) < 8 the code holds the values in
+ * ascending order (zero-padded to a multiple of 16 bytes) and 1,024 b bytes
+ * with the position of each plane byte among them, b bits each at bit
+ * offset i b, LSB first; a plane with b = 8 is stored as is.  An encoded
+ * slot is a 16-byte head (b of each plane, then k - 1, 255 for a stored
+ * plane) and the 8 plane sections in order, or, when that would not be
+ * shorter, the 65,536 slot bytes as they are (length 65,536).
  */
 #ifndef CRUM_H
 #define CRUM_H
@@ -123,6 +138,12 @@ typedef struct crum_config {
                                   many of the set's images are not yet PERSISTED,
                                   so a sink slower than the checkpoints bounds the
                                   pinned host memory they hold; 0: no bound */
+    int compress;              /* 1: images take the compressed form (version 2,
+                                  flags bit 1): each payload slot is encoded with
+                                  the byte-plane dictionary code below on the
+                                  device before it drains, so fewer bytes cross
+                                  the link; needs staging that holds every page of
+                                  the set and owned (not external) staging */
 } crum_config;
 
 typedef enum crum_restore_mode {

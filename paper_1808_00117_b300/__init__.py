@@ -46,7 +46,7 @@ class Config(ctypes.Structure):
                 ("hash_mapping", ctypes.c_int), ("gather_mapping", ctypes.c_int),
                 ("external_staging", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("max_chain", ctypes.c_int), ("restore_mode", ctypes.c_int),
-                ("max_pending", ctypes.c_int)]
+                ("max_pending", ctypes.c_int), ("compress", ctypes.c_int)]
 
 
 class ServerConfig(ctypes.Structure):

@@ -62,6 +62,11 @@ constexpr int64_t kBackgroundLimitNs = 600ll * 1000 * 1000 * 1000;  // 10 min
 uint64_t pages_of(uint64_t bytes) { return (bytes + kPage - 1) / kPage; }
 uint64_t meta_bytes(uint64_t A, uint64_t n) { return kHeaderBytes + 16 * A + 16 * n; }
 uint64_t image_size(uint64_t A, uint64_t n) { return meta_bytes(A, n) + n * kPage + 8; }
+// compressed form: tables with the slot offsets, padded to 16 bytes
+uint64_t cmeta_bytes(uint64_t A, uint64_t n) { return (kHeaderBytes + 16 * A + 24 * n + 15) & ~15ull; }
+uint64_t payload_offset(const crum_image* img) {
+  return img->compressed ? img->payload_off : meta_bytes(img->n_allocs, img->n_dirty);
+}
 
 std::atomic<uint32_t> g_set_ids{0};
 
@@ -141,7 +146,9 @@ crum_status grow_device(T** p, size_t* cap, size_t need, bool keep) {
 crum_status ensure_capacity(crum_set* s, std::unique_lock<std::mutex>& lk) {
   const size_t A = s->allocs.size();
   const uint64_t words = (s->n_pages + 31) / 32;
-  const size_t meta_need = meta_bytes(A, s->n_pages);
+  // room for the compressed form's tables, and for a replayed chunk of a
+  // compressed image (page table, hashes and offsets of a half's slots)
+  const size_t meta_need = cmeta_bytes(A, std::max<uint64_t>(s->n_pages, s->half_slots));
   const bool grow = A > s->alloc_cap || s->n_pages > s->h_cap || words + 1 > s->words_cap ||
                     meta_need > s->half[0].meta_cap || meta_need > s->half[1].meta_cap ||
                     (s->cfg.verify && s->n_pages > s->shadow_cap);
@@ -208,7 +215,7 @@ constexpr uint64_t kBounceBytes = 256ull << 20;  // 4,096 pages
 crum_status drain_payload(crum_set* s, crum_image* img, uint64_t s0, const uint8_t* src,
                           uint64_t bytes) {
   if (!img->drop_payload) {
-    CK(cudaMemcpyAsync(img->host + meta_bytes(img->n_allocs, img->n_dirty) + s0 * kPage, src, bytes,
+    CK(cudaMemcpyAsync(img->host + payload_offset(img) + s0 * kPage, src, bytes,
                        cudaMemcpyDeviceToHost, s->drain_stream));
     return CRUM_OK;
   }
@@ -228,18 +235,19 @@ uint8_t* trailer_dst(crum_image* img) { return img->host + img->host_len - 8; }
 // Queue the device->host copies of a captured image from half H into its
 // pinned host buffer, on the drain stream.
 crum_status enqueue_drain(crum_set* s, crum_image* img, Half& H) {
-  const uint64_t A = img->n_allocs, n = img->n_dirty;
-  CK(cudaStreamWaitEvent(s->drain_stream, img->ev_captured, 0));
+  const uint64_t n = img->n_dirty;
+  CK(cudaStreamWaitEvent(s->drain_stream, img->compressed ? H.ev_encoded : img->ev_captured, 0));
   if (img->ticket >= 0 && s->sequencer) {
     crum::DrainSequencer* q = s->sequencer.get();
     std::lock_guard<std::mutex> lk(q->mu);
     if (q->tail_recorded) CK(cudaStreamWaitEvent(s->drain_stream, q->tail, 0));
   }
   CK(cudaEventRecord(img->ev_d0, s->drain_stream));
-  CK(cudaMemcpyAsync(img->host, H.meta, meta_bytes(A, n), cudaMemcpyDeviceToHost, s->drain_stream));
+  CK(cudaMemcpyAsync(img->host, H.meta, payload_offset(img), cudaMemcpyDeviceToHost, s->drain_stream));
   // the null sink drains too (the bytes cross the link); the writer drops them
-  if (n > 0) {
-    const crum_status st = drain_payload(s, img, 0, H.payload, n * kPage);
+  const uint64_t payload = img->compressed ? img->payload_bytes : n * kPage;
+  if (payload > 0) {
+    const crum_status st = drain_payload(s, img, 0, img->compressed ? H.cpay : H.payload, payload);
     if (st != CRUM_OK) return st;
   }
   CK(cudaMemcpyAsync(trailer_dst(img), H.scalars + 1, 8, cudaMemcpyDeviceToHost, s->drain_stream));
@@ -249,9 +257,10 @@ crum_status enqueue_drain(crum_set* s, crum_image* img, Half& H) {
 }
 
 crum_status alloc_image_host(crum_set* s, crum_image* img) {
-  img->image_bytes = image_size(img->n_allocs, img->n_dirty);
+  img->image_bytes = img->compressed ? img->payload_off + img->payload_bytes + 8
+                                     : image_size(img->n_allocs, img->n_dirty);
   img->host_len = img->image_bytes;
-  if (img->drop_payload) img->host_len = meta_bytes(img->n_allocs, img->n_dirty) + 8;
+  if (img->drop_payload) img->host_len = payload_offset(img) + 8;
   img->host = s->pool->alloc(img->host_len);
   if (img->host == nullptr) return fail(CRUM_ENOMEM, "pinned host pool exhausted (%zu bytes)", img->host_len);
   return CRUM_OK;
@@ -290,7 +299,7 @@ void planner_main(crum_set* s) {
       s->plan_q.pop_front();
     }
     Half& H = s->half[img->half];
-    crum_status st = wait_event(H.ev_scanned, kBackgroundLimitNs);
+    crum_status st = wait_event(img->compressed ? H.ev_sized : H.ev_scanned, kBackgroundLimitNs);
     std::string err = st == CRUM_OK ? "" : t_err;
     crum::DrainSequencer* q = img->ticket >= 0 ? s->sequencer.get() : nullptr;
     bool my_turn = false;  // a failed capture still takes (and passes) its turn
@@ -305,6 +314,10 @@ void planner_main(crum_set* s) {
     if (st == CRUM_OK) {
       img->n_dirty = reinterpret_cast<volatile uint64_t*>(H.mailbox)[0];
       img->collisions = reinterpret_cast<volatile uint64_t*>(H.mailbox)[1];
+      if (img->compressed) {
+        img->payload_bytes = reinterpret_cast<volatile uint64_t*>(H.mailbox)[3];
+        img->payload_off = cmeta_bytes(img->n_allocs, img->n_dirty);
+      }
       if (reinterpret_cast<volatile uint64_t*>(H.mailbox)[2] != 0)
         st = fail(CRUM_ETIMEOUT, "hash kernel: a bounded device wait ran out");
       if (st == CRUM_OK) st = alloc_image_host(s, img);
@@ -447,7 +460,7 @@ crum_status new_image_events(crum_image* img) {
 // Restore of a whole chain in two launches (see k_chain_owner and
 // k_restore_merged): every page once, from the newest image holding it.
 crum_status restore_merged(crum_set* s, const std::vector<crum::ChainImage>& ci,
-                           uint64_t total_slots, bool delta) {
+                           uint64_t total_slots, bool delta, bool compressed) {
   if (s->owner_cap < s->n_pages) {
     cudaFree(s->d_owner);
     s->d_owner = nullptr;
@@ -462,7 +475,6 @@ crum_status restore_merged(crum_set* s, const std::vector<crum::ChainImage>& ci,
     CK(cudaMalloc(&s->d_chain, ci.size() * sizeof(crum::ChainImage)));
     s->chain_cap = ci.size();
   }
-  if (s->d_copied == nullptr) CK(cudaMalloc(&s->d_copied, sizeof(unsigned long long)));
   if (delta && s->cur_cap < s->n_pages) {
     cudaFree(s->d_cur);
     s->d_cur = nullptr;
@@ -473,7 +485,6 @@ crum_status restore_merged(crum_set* s, const std::vector<crum::ChainImage>& ci,
   // pageable source: staged by the runtime before the call returns
   CK(cudaMemcpyAsync(s->d_chain, ci.data(), ci.size() * sizeof(crum::ChainImage),
                      cudaMemcpyHostToDevice, s->cap_stream));
-  CK(cudaMemsetAsync(s->d_copied, 0, sizeof(unsigned long long), s->cap_stream));
   if (delta) {
     // the current contents' page hashes, to leave pages that already match
     crum::HashArgs ha{};
@@ -503,7 +514,8 @@ crum_status restore_merged(crum_set* s, const std::vector<crum::ChainImage>& ci,
   ma.h_table = s->d_h;
   ma.current = delta ? s->d_cur : nullptr;
   ma.copied = s->d_copied;
-  CK(crum::launch_restore_merged(ma, s->cap_stream));
+  ma.error = reinterpret_cast<unsigned int*>(s->d_copied + 1);
+  CK(crum::launch_restore_merged(ma, compressed, s->cap_stream));
   return CRUM_OK;
 }
 
@@ -790,6 +802,7 @@ crum_status crum_set_create(const crum_config* cfg_in, crum_set** out) {
     return fail(CRUM_EINVAL, "mapping out of range");
   if (cfg.restore_mode < 0 || cfg.restore_mode > 3) return fail(CRUM_EINVAL, "bad restore_mode");
   if (cfg.max_pending < 0) return fail(CRUM_EINVAL, "bad max_pending");
+  if (cfg.compress && cfg.external_staging) return fail(CRUM_EINVAL, "compression needs the set's own staging");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg.device < 0 || cfg.device >= ndev) {
     cudaGetLastError();
@@ -823,6 +836,17 @@ crum_status crum_set_create(const crum_config* cfg_in, crum_set** out) {
                   (unsigned long long)(s->half_slots * kPage));
     }
     CK(cudaMalloc(&H.scalars, 2 * sizeof(uint64_t)));
+    if (cfg.compress) {
+      if (cudaMalloc(&H.cpay, s->half_slots * kPage) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CRUM_ENOMEM, "cannot allocate %llu bytes of compressed staging",
+                    (unsigned long long)(s->half_slots * kPage));
+      }
+      CK(cudaMalloc(&H.enc_len, std::max<uint64_t>(s->half_slots, 1) * sizeof(uint32_t)));
+      CK(cudaMalloc(&H.ctotal, sizeof(uint64_t)));
+      CK(cudaEventCreateWithFlags(&H.ev_sized, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&H.ev_encoded, cudaEventDisableTiming));
+    }
     CK(cudaHostAlloc(reinterpret_cast<void**>(&H.mailbox), 4 * sizeof(uint64_t), cudaHostAllocMapped));
     CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&H.mailbox_dev), H.mailbox, 0));
     CK(cudaEventCreateWithFlags(&H.ev_scanned, cudaEventDisableTiming));
@@ -869,6 +893,11 @@ crum_status crum_set_destroy(crum_set* s) {
     cudaFreeHost(H.mailbox);
     cudaEventDestroy(H.ev_scanned);
     cudaEventDestroy(H.ev_drained);
+    cudaFree(H.cpay);
+    cudaFree(H.enc_len);
+    cudaFree(H.ctotal);
+    if (H.ev_sized) cudaEventDestroy(H.ev_sized);
+    if (H.ev_encoded) cudaEventDestroy(H.ev_encoded);
   }
   cudaFree(s->d_allocs);
   cudaFree(s->d_first_page);
@@ -1188,6 +1217,9 @@ crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, cr
   const bool fast = s->n_pages <= s->half_slots;
   if (!fast && gather_shadow)
     return bail(fail(CRUM_EINVAL, "verify mode needs staging that holds every page"));
+  if (!fast && s->cfg.compress)
+    return bail(fail(CRUM_EINVAL, "compression needs staging that holds every page"));
+  img->compressed = s->cfg.compress != 0;
   if (fast) {
     ga.payload = H.payload;
     ga.s_begin = 0;
@@ -1206,7 +1238,7 @@ crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, cr
     return bail(e);
   };
   cudaError_t ce = cudaSuccess;
-  if (fast && s->cfg.use_graph && !verify && !s->cfg.external_staging) {
+  if (fast && s->cfg.use_graph && !verify && !s->cfg.external_staging && !s->cfg.compress) {
     // one graph launch for the whole capture sequence
     st = graph_launch(s, h, img, ha, sa, ga);
     if (st != CRUM_OK) return unwind(st);
@@ -1225,6 +1257,24 @@ crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, cr
     if (ce == cudaSuccess && fast)
       ce = crum::launch_gather(ga, s->n_pages, s->map_gather, gather_shadow, s->cap_stream);
     if (ce == cudaSuccess && fast) ce = cudaEventRecord(img->ev_captured, s->cap_stream);
+    if (ce == cudaSuccess && img->compressed) {
+      // the application has its memory back; the staged slots are encoded
+      // behind it: sizes, offsets and header, then the code and checksum
+      crum::BpdSizeArgs za{H.payload, H.scalars, H.enc_len};
+      ce = crum::launch_bpd_size(za, s->n_pages, s->cap_stream);
+      crum::BpdScanArgs qa{H.enc_len, H.scalars, img->n_allocs, H.meta, H.ctotal, H.mailbox_dev};
+      if (ce == cudaSuccess) ce = crum::launch_bpd_scan(qa, s->cap_stream);
+      if (ce == cudaSuccess) ce = cudaEventRecord(H.ev_sized, s->cap_stream);
+      crum::BpdEncodeArgs ea{H.payload, H.scalars, H.meta, img->n_allocs, H.cpay};
+      if (ce == cudaSuccess) ce = crum::launch_bpd_encode(ea, s->n_pages, s->cap_stream);
+      if (ce == cudaSuccess) ce = cudaMemsetAsync(H.scalars + 1, 0, sizeof(uint64_t), s->cap_stream);
+      crum::BpdChecksumArgs ka{H.meta, H.cpay, H.scalars, H.ctotal, img->n_allocs,
+                               reinterpret_cast<unsigned long long*>(H.scalars + 1)};
+      if (ce == cudaSuccess)
+        ce = crum::launch_bpd_checksum(ka, cmeta_bytes(img->n_allocs, s->n_pages) + s->n_pages * kPage,
+                                       s->cap_stream);
+      if (ce == cudaSuccess) ce = cudaEventRecord(H.ev_encoded, s->cap_stream);
+    }
     if (ce != cudaSuccess)
       return unwind(fail(CRUM_ECUDA, "capture launch: %s", cudaGetErrorString(ce)));
   }
@@ -1374,11 +1424,33 @@ uint64_t rd64(const uint8_t* p) {
 // Structural check of a serialized image held in host memory.
 crum_status parse_image(const uint8_t* b, uint64_t n, crum_image* img) {
   if (n < kHeaderBytes + 8 || std::memcmp(b, "CRUMIMG1", 8) != 0) return fail(CRUM_ECORRUPT, "bad magic");
-  if (rd32(b + 8) != 1 || rd32(b + 32) != kPage) return fail(CRUM_ECORRUPT, "bad version or page size");
+  const uint32_t version = rd32(b + 8);
+  if ((version != 1 && version != 2) || rd32(b + 32) != kPage)
+    return fail(CRUM_ECORRUPT, "bad version or page size");
   const uint64_t A = rd32(b + 36), nd = rd64(b + 40);
-  if (nd > n / kPage || A > n / 16) return fail(CRUM_ECORRUPT, "counts exceed the image size");
-  if (rd64(b + 56) != n || image_size(A, nd) != n || rd64(b + 48) != meta_bytes(A, nd))
-    return fail(CRUM_ECORRUPT, "size fields disagree with the image length");
+  if (version == 1) {
+    if (nd > n / kPage || A > n / 16) return fail(CRUM_ECORRUPT, "counts exceed the image size");
+    if (rd64(b + 56) != n || image_size(A, nd) != n || rd64(b + 48) != meta_bytes(A, nd))
+      return fail(CRUM_ECORRUPT, "size fields disagree with the image length");
+    img->compressed = false;
+  } else {
+    if (nd > n / 16 || A > n / 16 || (rd32(b + 12) & 2u) == 0)
+      return fail(CRUM_ECORRUPT, "counts exceed the image size");
+    const uint64_t poff = rd64(b + 48);
+    if (rd64(b + 56) != n || poff != cmeta_bytes(A, nd) || poff + 8 > n)
+      return fail(CRUM_ECORRUPT, "size fields disagree with the image length");
+    const uint64_t total = n - 8 - poff;
+    const uint8_t* ot = b + kHeaderBytes + 16 * A + 16 * nd;
+    for (uint64_t s = 0; s < nd; ++s) {
+      const uint64_t lo = rd64(ot + 8 * s), hi = s + 1 < nd ? rd64(ot + 8 * (s + 1)) : total;
+      if ((s == 0 && lo != 0) || hi < lo + 16 || hi - lo > kPage || (hi - lo) % 16 != 0)
+        return fail(CRUM_ECORRUPT, "slot offsets out of order or out of range");
+    }
+    if (nd == 0 && total != 0) return fail(CRUM_ECORRUPT, "payload without slots");
+    img->compressed = true;
+    img->payload_off = poff;
+    img->payload_bytes = total;
+  }
   img->full = (rd32(b + 12) & 1u) != 0;
   img->seq = rd64(b + 16);
   img->parent_seq = rd64(b + 24);
@@ -1550,6 +1622,7 @@ crum_status crum_restore(crum_set* s, const crum_image* chain_end, crum_stream_t
                 (s->cfg.restore_mode == 0 && incr_pages * 100 > 8 * chain.front()->n_dirty);
   std::vector<crum::ChainImage> ci;
   uint64_t total_slots = 0;
+  bool any_compressed = false;
   for (size_t i = 0; merged && i < chain.size(); ++i) {
     cudaPointerAttributes pa{};
     if (cudaPointerGetAttributes(&pa, chain[i]->host) != cudaSuccess || pa.devicePointer == nullptr) {
@@ -1561,9 +1634,13 @@ crum_status crum_restore(crum_set* s, const crum_image* chain_end, crum_stream_t
       break;
     }
     const uint8_t* d = static_cast<const uint8_t*>(pa.devicePointer);
-    const uint64_t n = chain[i]->n_dirty;
-    ci.push_back(crum::ChainImage{d + kHeaderBytes + 16 * A, d + kHeaderBytes + 16 * A + 8 * n,
-                                  d + meta_bytes(A, n), total_slots});
+    const crum_image* im = chain[i];
+    const uint64_t n = im->n_dirty;
+    ci.push_back(crum::ChainImage{
+        d + kHeaderBytes + 16 * A, d + kHeaderBytes + 16 * A + 8 * n, d + payload_offset(im), total_slots,
+        im->compressed ? reinterpret_cast<const uint64_t*>(d + kHeaderBytes + 16 * A + 16 * n) : nullptr,
+        im->payload_bytes, n});
+    any_compressed = any_compressed || im->compressed;
     total_slots += n;
   }
   if (!merged && s->half_slots == 0) return fail(CRUM_EINVAL, "no staging bound to this set");
@@ -1572,7 +1649,9 @@ crum_status crum_restore(crum_set* s, const crum_image* chain_end, crum_stream_t
   CK(cudaEventRecord(s->ev_app, us));
   CK(cudaStreamWaitEvent(s->cap_stream, s->ev_app, 0));
   if ((st = upload_table(s)) != CRUM_OK) return st;
-  if (merged && (st = restore_merged(s, ci, total_slots, delta)) != CRUM_OK) return st;
+  if (s->d_copied == nullptr) CK(cudaMalloc(&s->d_copied, 2 * sizeof(unsigned long long)));
+  CK(cudaMemsetAsync(s->d_copied, 0, 2 * sizeof(unsigned long long), s->cap_stream));
+  if (merged && (st = restore_merged(s, ci, total_slots, delta, any_compressed)) != CRUM_OK) return st;
   s->restore_counted_on_device = merged;
   s->restore_pages = merged ? 0 : incr_pages + chain.front()->n_dirty;
   int h = s->next_half;
@@ -1580,7 +1659,8 @@ crum_status crum_restore(crum_set* s, const crum_image* chain_end, crum_stream_t
     const uint64_t n = img->n_dirty;
     const uint8_t* ptab = img->host + kHeaderBytes + 16 * A;
     const uint8_t* hashes = ptab + 8 * n;
-    const uint8_t* payload = img->host + meta_bytes(A, n);
+    const uint8_t* payload = img->host + payload_offset(img);
+    const uint64_t* offs = reinterpret_cast<const uint64_t*>(hashes + 8 * n);
     for (uint64_t s0 = 0; s0 < n; s0 += s->half_slots) {
       const uint64_t s1 = std::min(n, s0 + s->half_slots);
       Half& H = s->half[h];
@@ -1590,6 +1670,27 @@ crum_status crum_restore(crum_set* s, const crum_image* chain_end, crum_stream_t
       const uint64_t m = s1 - s0;
       CK(cudaMemcpyAsync(H.meta, ptab + 8 * s0, 8 * m, cudaMemcpyHostToDevice, s->cap_stream));
       CK(cudaMemcpyAsync(H.meta + 8 * m, hashes + 8 * s0, 8 * m, cudaMemcpyHostToDevice, s->cap_stream));
+      if (img->compressed) {
+        // encoded slots [s0, s1): their offsets, then their bytes
+        const uint64_t lo = offs[s0], hi = s1 < n ? offs[s1] : img->payload_bytes;
+        CK(cudaMemcpyAsync(H.meta + 16 * m, offs + s0, 8 * m, cudaMemcpyHostToDevice, s->cap_stream));
+        CK(cudaMemcpyAsync(H.payload, payload + lo, hi - lo, cudaMemcpyHostToDevice, s->cap_stream));
+        crum::BpdRestoreArgs ba{};
+        ba.allocs = s->d_allocs;
+        ba.n_allocs = static_cast<uint32_t>(A);
+        ba.ptab = reinterpret_cast<const uint32_t*>(H.meta);
+        ba.hashes = reinterpret_cast<const uint64_t*>(H.meta + 8 * m);
+        ba.offs = reinterpret_cast<const uint64_t*>(H.meta + 16 * m);
+        ba.enc = H.payload;
+        ba.enc_end = hi;
+        ba.n_slots = m;
+        ba.h_table = s->d_h;
+        ba.error = reinterpret_cast<unsigned int*>(s->d_copied + 1);
+        CK(crum::launch_bpd_restore(ba, s->cap_stream));
+        CK(cudaEventRecord(H.ev_drained, s->cap_stream));
+        h ^= 1;
+        continue;
+      }
       CK(cudaMemcpyAsync(H.payload, payload + kPage * s0, kPage * m, cudaMemcpyHostToDevice, s->cap_stream));
       crum::RestoreArgs ra{};
       ra.allocs = s->d_allocs;
@@ -1631,13 +1732,10 @@ crum_status crum_restore_pages(crum_set* s, uint64_t* pages) {
   }
   crum_status st = wait_event(s->ev_done, kBackgroundLimitNs);
   if (st != CRUM_OK) return st;
-  if (!on_device) {
-    *pages = host_count;
-    return CRUM_OK;
-  }
-  unsigned long long n = 0;
-  CK(cudaMemcpy(&n, s->d_copied, sizeof n, cudaMemcpyDeviceToHost));
-  *pages = n;
+  unsigned long long n[2] = {0, 0};  // pages copied by the kernels, decode failures
+  if (s->d_copied != nullptr) CK(cudaMemcpy(n, s->d_copied, sizeof n, cudaMemcpyDeviceToHost));
+  *pages = on_device ? n[0] : host_count;
+  if (n[1] != 0) return fail(CRUM_ECORRUPT, "a compressed slot did not decode (it was skipped)");
   return CRUM_OK;
 }
 

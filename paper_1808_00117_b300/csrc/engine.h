@@ -75,6 +75,12 @@ struct Half {
   cudaEvent_t ev_scanned = nullptr;
   cudaEvent_t ev_drained = nullptr;  // last device->host copy out of this half
   bool drain_enqueued = true;        // host: ev_drained is recorded for its last user
+  // compressed images (cfg.compress)
+  uint8_t* cpay = nullptr;           // encoded payload
+  uint32_t* enc_len = nullptr;       // encoded length of every slot
+  uint64_t* ctotal = nullptr;        // device: encoded payload bytes
+  cudaEvent_t ev_sized = nullptr;    // encoded sizes, offsets and header written
+  cudaEvent_t ev_encoded = nullptr;  // encoded payload and checksum written
 };
 
 // The capture sequence of one staging half as an instantiated CUDA graph:
@@ -142,6 +148,9 @@ struct crum_image {
   int half = 0;
   bool drop_payload = false;  // null sink
   int64_t ticket = -1;        // drain order under a DrainSequencer
+  bool compressed = false;    // version 2 image
+  uint64_t payload_off = 0;   // compressed: where the encoded payload starts
+  uint64_t payload_bytes = 0; // compressed: encoded payload bytes
   std::string sink_path;
   bool do_fsync = false;
 };

@@ -91,8 +91,11 @@ struct RestoreArgs {
 struct ChainImage {
   const uint8_t* ptab;     // 2 u32 per slot: allocation index, page index
   const uint8_t* hashes;   // u64 per slot
-  const uint8_t* payload;  // slot s at payload + s * 64 KiB
+  const uint8_t* payload;  // slot s at payload + s * 64 KiB (or encoded, see offs)
   uint64_t slot0;          // slots of the images before this one
+  const uint64_t* offs;    // compressed image: slot offsets in the payload, else nullptr
+  uint64_t payload_bytes;  // compressed image: encoded payload bytes
+  uint64_t n_slots;
 };
 
 // owner[g] = (image + 1) << 40 | slot of the newest chain image holding
@@ -116,6 +119,57 @@ struct MergedRestoreArgs {
   uint64_t* h_table;
   const uint64_t* current;          // delta mode: current hash of every page, else nullptr
   unsigned long long* copied;       // pages copied across the link (optional)
+  unsigned int* error;              // set when a compressed slot does not decode (optional)
+};
+
+// Compressed images (byte-plane dictionary code of each payload slot; the
+// format is stated with crum_config.compress in crum.h).
+struct BpdSizeArgs {
+  const uint8_t* payload;    // raw slots, slot s at payload + s * 64 KiB
+  const uint64_t* n_dirty;   // device
+  uint32_t* enc_len;         // out: encoded length of every slot
+};
+
+struct BpdScanArgs {
+  const uint32_t* enc_len;
+  const uint64_t* n_dirty;
+  uint32_t n_allocs;
+  uint8_t* meta;             // header words rewritten, offset table + padding written
+  uint64_t* total_out;       // device: encoded payload bytes
+  volatile uint64_t* mailbox;  // [3] = encoded payload bytes (optional)
+};
+
+struct BpdEncodeArgs {
+  const uint8_t* payload;    // raw slots
+  const uint64_t* n_dirty;
+  const uint8_t* meta;       // offset table at 64 + 16 A + 16 n
+  uint32_t n_allocs;
+  uint8_t* out;              // encoded payload
+};
+
+// Replay restore of a compressed image's slots [0, n_slots): slot s is
+// encoded at enc + offs[s] - offs[0] with length offs[s + 1] - offs[s]
+// (the last one ends at enc_end).
+struct BpdRestoreArgs {
+  const DevAlloc* allocs;
+  uint32_t n_allocs;
+  const uint32_t* ptab;
+  const uint64_t* hashes;
+  const uint64_t* offs;
+  const uint8_t* enc;
+  uint64_t enc_end;          // offset, in the image's payload, where the last slot ends
+  uint64_t n_slots;
+  uint64_t* h_table;
+  unsigned int* error;       // set when a slot does not decode (skipped)
+};
+
+struct BpdChecksumArgs {
+  const uint8_t* meta;       // image bytes [0, payload offset)
+  const uint8_t* enc;        // encoded payload
+  const uint64_t* n_dirty;
+  const uint64_t* total;     // encoded payload bytes (device)
+  uint32_t n_allocs;
+  unsigned long long* trailer;  // pre-zeroed; receives the image checksum
 };
 
 // Launch shape of one kernel: launched directly (launch_spec) or added to a
@@ -137,7 +191,12 @@ cudaError_t launch_gather(const GatherArgs& a, uint64_t max_slots, int mapping, 
                           cudaStream_t st);
 cudaError_t launch_restore(const RestoreArgs& a, cudaStream_t st);
 cudaError_t launch_chain_owner(const OwnerArgs& a, cudaStream_t st);
-cudaError_t launch_restore_merged(const MergedRestoreArgs& a, cudaStream_t st);
+cudaError_t launch_bpd_size(const BpdSizeArgs& a, uint64_t max_slots, cudaStream_t st);
+cudaError_t launch_bpd_scan(const BpdScanArgs& a, cudaStream_t st);
+cudaError_t launch_bpd_encode(const BpdEncodeArgs& a, uint64_t max_slots, cudaStream_t st);
+cudaError_t launch_bpd_checksum(const BpdChecksumArgs& a, uint64_t max_bytes, cudaStream_t st);
+cudaError_t launch_bpd_restore(const BpdRestoreArgs& a, cudaStream_t st);
+cudaError_t launch_restore_merged(const MergedRestoreArgs& a, bool compressed, cudaStream_t st);
 cudaError_t launch_hash_bytes(const uint8_t* p, uint64_t n, uint64_t first_index, uint64_t* out,
                               cudaStream_t st);
 

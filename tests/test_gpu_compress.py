@@ -1,0 +1,141 @@
+"""Compressed images (crum_config.compress): the CUDA path's version-2
+images equal the oracle's byte for byte, for float pages (which shrink),
+random words (stored as is) and ragged tails; every restore form brings the
+chain back; files round-trip; the checksum of a payload that is not kept
+still matches."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1808_00117_b300 as crum
+from paper_1808_00117_b300 import workloads as W
+
+from helpers import device_buffers, first_diff, host_copies, make_set, mutate, stream_handle, torch
+
+pytestmark = pytest.mark.gpu
+P = W.PAGE
+SIZES = [1, 4096 + 8, P - 8, P, 3 * P + 40, 21 * P + 4104]
+
+
+@pytest.fixture(autouse=True)
+def _cuda():
+    t = torch()
+    if not t.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    crum.load()
+    yield
+    t.cuda.synchronize()
+
+
+def _ckpt(s, flags=crum.INCR):
+    img = s.checkpoint(stream_handle(), flags)
+    img.wait()
+    return img, img.to_bytes()
+
+
+@pytest.mark.parametrize("kind", ["fp32", "fp64", "bf16", "u32"])
+def test_compressed_images_equal_the_oracle(kind):
+    bufs = device_buffers(SIZES, seed=81, kind=kind)
+    s = make_set(bufs, compress=1)
+    o = oracle.OracleSet(SIZES, compress=True)
+    raw = oracle.OracleSet(SIZES)
+    for step in range(3):
+        if step:
+            mutate(bufs, SIZES, 0.4, seed=810 + step)
+        img, got = _ckpt(s)
+        state = host_copies(bufs)
+        exp, *_ = o.checkpoint(state)
+        plain, *_ = raw.checkpoint(state)
+        assert oracle.image_version(got) == 2
+        assert first_diff(got, exp) is None, f"step {step}"
+        assert img.info()["image_bytes"] == len(exp)
+        if kind in ("fp32", "fp64", "bf16") and step == 0:
+            assert len(got) < 0.95 * len(plain)
+        img.release()
+    s.destroy()
+
+
+@pytest.mark.parametrize("mode", [crum.RESTORE_REPLAY, crum.RESTORE_MERGED, crum.RESTORE_DELTA])
+def test_compressed_chain_restores(mode):
+    bufs = device_buffers(SIZES, seed=83, kind="fp32")
+    s = make_set(bufs, compress=1, restore_mode=mode)
+    chain, states = [], []
+    for step in range(3):
+        if step:
+            mutate(bufs, SIZES, 0.3, seed=830 + step)
+        img = s.checkpoint(stream_handle())
+        img.wait()
+        chain.append(img)
+        states.append(host_copies(bufs))
+    for k in (2, 0, 1):
+        for i, b in enumerate(bufs):
+            W.fill_(b, 8300 + k + 10 * i, "u32")
+        s.restore(chain[k], stream_handle())
+        torch().cuda.synchronize()
+        assert all(np.array_equal(g, w) for g, w in zip(host_copies(bufs), states[k])), k
+        assert s.restore_pages() > 0
+    for c in chain:
+        c.release()
+    s.destroy()
+
+
+def test_compressed_files_round_trip(tmp_path):
+    sizes = [5 * P + 8, 2 * P]
+    bufs = device_buffers(sizes, seed=85, kind="fp64")
+    s = make_set(bufs, compress=1, sink=crum.SINK_FILE, sink_dir=str(tmp_path))
+    states = []
+    for step in range(2):
+        if step:
+            mutate(bufs, sizes, 0.5, seed=850 + step)
+        img = s.checkpoint(stream_handle())
+        img.wait()
+        states.append(host_copies(bufs))
+        img.release()
+    files = sorted(tmp_path.iterdir(), key=lambda x: int(x.stem.rsplit("_", 1)[1]))
+    for f in files:
+        assert oracle.check_image(f.read_bytes()) == oracle.OK
+    r = make_set(bufs)  # an uncompressed set restores compressed images too
+    chain = []
+    for f in files:
+        chain.append(r.load_image(str(f), chain[-1] if chain else None))
+    for i, b in enumerate(bufs):
+        W.fill_(b, 8500 + i, "u32")
+    r.restore(chain[-1], stream_handle())
+    torch().cuda.synchronize()
+    assert all(np.array_equal(g, w) for g, w in zip(host_copies(bufs), states[-1]))
+    for c in chain:
+        c.release()
+    r.destroy()
+    s.destroy()
+
+
+def test_compressed_no_payload_and_verify():
+    sizes = [300 * P + 24]
+    bufs = device_buffers(sizes, seed=87, kind="fp32")
+    s = make_set(bufs, compress=1, verify=1)
+    o = oracle.OracleSet(sizes, compress=True)
+    img = s.checkpoint(stream_handle(), crum.FULL | crum.NO_PAYLOAD)
+    img.wait()
+    exp, *_ = o.checkpoint(host_copies(bufs))
+    assert img.info()["checksum"] == int(np.frombuffer(exp[-8:], dtype=np.uint64)[0])
+    assert img.info()["image_bytes"] == len(exp)
+    mutate(bufs, sizes, 0.1, seed=871)
+    img2 = s.checkpoint(stream_handle(), crum.VERIFY)
+    assert img2.wait() == crum.OK
+    exp2, *_ = o.checkpoint(host_copies(bufs))
+    assert first_diff(img2.to_bytes(), exp2) is None
+    s.destroy()
+
+
+def test_compression_needs_staging_for_every_page():
+    sizes = [20 * P]
+    bufs = device_buffers(sizes, seed=89)
+    s = make_set(bufs, compress=1, staging_bytes=4 * P)
+    with pytest.raises(crum.CrumError) as e:
+        s.checkpoint(stream_handle())
+    assert e.value.status == crum.EINVAL
+    s.destroy()
+    with pytest.raises(crum.CrumError):
+        crum.CheckpointSet(compress=1, external_staging=1)
