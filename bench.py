@@ -56,6 +56,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-verify", action="store_true", help="skip the verify-mode measurement")
+    ap.add_argument("--compress", action="store_true",
+                    help="images in the compressed form (byte-plane dictionary code on the device)")
+    ap.add_argument("--kind", choices=["u32", "fp32", "fp64", "bf16"], default=None,
+                    help="uint32 workload: element kind of the synthetic data")
     ap.add_argument("--sink", choices=["memory", "file"], default="memory",
                     help="uint32 workload: where the writer persists images (file: a "
                          "temporary directory on the host's disk, fsync per image)")
@@ -71,6 +75,11 @@ def parse_args(argv=None):
                     help="application memory: cudaMalloc (PyTorch) or cudaMallocManaged "
                          "prefetched to the device; default managed for the large workload")
     return ap.parse_args(argv)
+
+
+def raw_image_bytes(info) -> int:
+    """Bytes of the uncompressed image with the same pages."""
+    return 64 + 16 * info["n_allocs"] + 16 * info["n_dirty"] + info["n_dirty"] * 65536 + 8
 
 
 def app_memory(args, wl) -> str:
@@ -378,6 +387,8 @@ def run_ours(args):
     if args.footprint_gib:
         wl.sizes = [args.footprint_gib * W.GiB]
         wl.name = f"uint32_{args.footprint_gib}g"
+    if args.kind:
+        wl.kind = args.kind
     S = wl.total_bytes
     n_pages = wl.n_pages
     k_dirty = int(round(wl.dirty_frac * n_pages))
@@ -404,7 +415,7 @@ def run_ours(args):
                            hash_mapping=fixed[0] if fixed else -1,
                            gather_mapping=fixed[1] if fixed else -1,
                            sink=crum.SINK_FILE if sink_dir else crum.SINK_MEMORY,
-                           sink_dir=sink_dir, fsync=int(bool(sink_dir)))
+                           sink_dir=sink_dir, fsync=int(bool(sink_dir)), compress=int(args.compress))
     for b in bufs:
         s.register(b.data_ptr(), b.numel())
     stream = torch.cuda.current_stream()
@@ -584,7 +595,8 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": wl.name, "footprint_bytes": S, "allocations": len(wl.sizes),
                    "n_pages": n_pages, "dirty_pages_per_step": k_dirty,
-                   "memory": MEMORY_DESC[memory],
+                   "memory": MEMORY_DESC[memory], "kind": wl.kind,
+                   "images": "compressed (byte-plane dictionary code)" if args.compress else "plain",
                    "staging_bytes": staging, "parallelism": f"replica per GPU x{world}",
                    "l2": "inputs (8 GiB) larger than L2 (126 MB); no flush",
                    "value_def": "footprint bytes / capture-kernel device time (hash+scan+gather)",
@@ -602,6 +614,8 @@ def run_ours(args):
                     "frac_of_hbm": round(value / world / peaks["hbm_gbs"], 4)},
         "drain": {"gbs": round(drain_gbs, 2), "link_measured_gbs": round(link_peak, 2),
                   "frac_measured": round(drain_gbs / link_peak, 4),
+                  "effective_gbs": round(statistics.mean(
+                      raw_image_bytes(i) / (i["t_drain_ms"] * 1e-3) / 1e9 for i in infos), 2),
                   "link_nominal_gbs": NOMINAL_LINK_GBS,
                   "frac_nominal": round(drain_gbs / NOMINAL_LINK_GBS, 4),
                   "bytes_per_step": int(statistics.mean(drained_bytes))},
@@ -820,7 +834,8 @@ def run_batched(args):
         staging = 2 * (int(1.5 * max(dirty.values())) + 1) * W.PAGE  # halves hold a step's pages
     max_img = 64 + 16 * len(wl.sizes) + 16 * n_pages + 8 + min(n_pages, staging // 2 // W.PAGE) * W.PAGE
     s = crum.CheckpointSet(device=local, staging_bytes=staging, sink=crum.SINK_NULL,
-                           host_pool_bytes=max_img if stencil else 3 * max_img)
+                           host_pool_bytes=max_img if stencil else 3 * max_img,
+                           compress=int(args.compress))
     for b in bufs:
         s.register(b.data_ptr(), b.numel())
     stream = torch.cuda.current_stream()
@@ -934,6 +949,7 @@ def run_batched(args):
         "config": {"workload": wl.name, "footprint_bytes": S, "allocations": len(wl.sizes),
                    "n_pages": n_pages, "dirty_pages_per_step": int(statistics.mean(i["n_dirty"] for i in infos)),
                    "sink": "null", "staging_bytes": staging, "memory": MEMORY_DESC[memory],
+                   "images": "compressed (byte-plane dictionary code)" if args.compress else "plain",
                    "hash_mapping": tune["hash_mapping"], "gather_mapping": tune["gather_mapping"],
                    "autotune_hash_ms": [round(x, 4) for x in tune["hash_ms"]],
                    "autotune_gather_ms": [round(x, 4) for x in tune["gather_ms"]]},
@@ -944,7 +960,9 @@ def run_batched(args):
         "capture": {"ms_mean": round(statistics.mean(cap_ms), 4),
                     "hash_ms_mean": round(statistics.mean(hash_ms), 4)},
         "drain": {"gbs": round(drain_gbs, 2), "link_measured_gbs": round(link_peak, 2),
-                  "frac_measured": round(drain_gbs / link_peak, 4)},
+                  "frac_measured": round(drain_gbs / link_peak, 4),
+                  "effective_gbs": round(statistics.mean(
+                      raw_image_bytes(i) / (i["t_drain_ms"] * 1e-3) / 1e9 for i in infos), 2)},
         "latency_ms": {"captured_p50": pct([i["t_captured_ms"] for i in infos], 50),
                        "captured_p99": pct([i["t_captured_ms"] for i in infos], 99),
                        "drained_p50": pct([i["t_drained_ms"] for i in infos], 50),
