@@ -1,8 +1,9 @@
 """Seeded random scenarios through the C ABI against the oracle: random
 allocation sizes (tiny, ragged, several pages), staging that holds every
 page or only a few (chunked capture), graph or plain launches, random hash
-and gather mappings, verify sets, and per step a random rewrite and a random
-checkpoint flag (incremental, full, verify, no payload); now and then the
+and gather mappings, verify sets, compressed images, four data kinds, and
+per step a random rewrite and a random checkpoint flag (incremental, full,
+verify, no payload); now and then the
 chain end is restored onto scribbled memory with the scenario's restore
 form.  Every image is compared with the oracle's byte for byte (checksum
 and size when the payload is not kept)."""
@@ -63,13 +64,14 @@ def test_random_scenario(seed):
     n_pages = sum(W.pages_of(n) for n in sizes)
     chunked = bool(rng.integers(0, 2))
     verify = (not chunked) and bool(rng.integers(0, 2))
+    compress = (not chunked) and bool(rng.integers(0, 2))
     cfg = dict(staging_bytes=(2 * int(rng.integers(1, 4)) * P) if chunked else 2 * (n_pages + 1) * P,
                use_graph=int(rng.integers(0, 2)), hash_mapping=int(rng.integers(0, crum.NUM_HASH_MAPPINGS)),
                gather_mapping=int(rng.integers(0, 6)), verify=int(verify),
-               restore_mode=int(rng.integers(0, 4)))
-    bufs = device_buffers(sizes, seed=seed + 50)
+               restore_mode=int(rng.integers(0, 4)), compress=int(compress))
+    bufs = device_buffers(sizes, seed=seed + 50, kind=["u32", "fp32", "fp64", "bf16"][seed % 4])
     s = make_set(bufs, **cfg)
-    o = oracle.OracleSet(sizes)
+    o = oracle.OracleSet(sizes, compress=compress)
     chain_ok = False  # every image since the last full one kept its payload
     chain_end, state_end = None, None
     images = []
