@@ -785,6 +785,8 @@ def run_batched(args):
     crum.load()
     dev = torch.device("cuda", local)
     wl = W.workload(args.workload)
+    if args.kind:
+        wl.kind = args.kind
     S, n_pages = wl.total_bytes, wl.n_pages
     steps, warmup = args.steps, max(args.warmup, 3)
     link_peak = link_d2h_peak(torch)
@@ -949,6 +951,7 @@ def run_batched(args):
         "config": {"workload": wl.name, "footprint_bytes": S, "allocations": len(wl.sizes),
                    "n_pages": n_pages, "dirty_pages_per_step": int(statistics.mean(i["n_dirty"] for i in infos)),
                    "sink": "null", "staging_bytes": staging, "memory": MEMORY_DESC[memory],
+                   "kind": wl.kind,
                    "images": "compressed (byte-plane dictionary code)" if args.compress else "plain",
                    "hash_mapping": tune["hash_mapping"], "gather_mapping": tune["gather_mapping"],
                    "autotune_hash_ms": [round(x, 4) for x in tune["hash_ms"]],

@@ -142,8 +142,11 @@ typedef struct crum_config {
                                   flags bit 1): each payload slot is encoded with
                                   the byte-plane dictionary code below on the
                                   device before it drains, so fewer bytes cross
-                                  the link; needs staging that holds every page of
-                                  the set and owned (not external) staging */
+                                  the link; needs owned (not external) staging.
+                                  With staging smaller than the set, the dirty
+                                  pages are encoded and drained one staging half
+                                  at a time, each chunk's code placed after the
+                                  previous chunk's */
 } crum_config;
 
 typedef enum crum_restore_mode {

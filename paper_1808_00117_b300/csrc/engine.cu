@@ -212,11 +212,10 @@ constexpr uint64_t kBounceBytes = 256ull << 20;  // 4,096 pages
 // the drain stream: into the image's own buffer, or, when the image keeps no
 // payload, through the set's bounce region so that a footprint larger than
 // host memory can still be drained and timed.
-crum_status drain_payload(crum_set* s, crum_image* img, uint64_t s0, const uint8_t* src,
+crum_status drain_payload(crum_set* s, crum_image* img, uint64_t host_off, const uint8_t* src,
                           uint64_t bytes) {
   if (!img->drop_payload) {
-    CK(cudaMemcpyAsync(img->host + payload_offset(img) + s0 * kPage, src, bytes,
-                       cudaMemcpyDeviceToHost, s->drain_stream));
+    CK(cudaMemcpyAsync(img->host + host_off, src, bytes, cudaMemcpyDeviceToHost, s->drain_stream));
     return CRUM_OK;
   }
   {
@@ -247,7 +246,8 @@ crum_status enqueue_drain(crum_set* s, crum_image* img, Half& H) {
   // the null sink drains too (the bytes cross the link); the writer drops them
   const uint64_t payload = img->compressed ? img->payload_bytes : n * kPage;
   if (payload > 0) {
-    const crum_status st = drain_payload(s, img, 0, img->compressed ? H.cpay : H.payload, payload);
+    const crum_status st =
+        drain_payload(s, img, payload_offset(img), img->compressed ? H.cpay : H.payload, payload);
     if (st != CRUM_OK) return st;
   }
   CK(cudaMemcpyAsync(trailer_dst(img), H.scalars + 1, 8, cudaMemcpyDeviceToHost, s->drain_stream));
@@ -528,9 +528,21 @@ crum_status checkpoint_chunked(crum_set* s, crum_image* img, cudaStream_t app,
   img->collisions = reinterpret_cast<volatile uint64_t*>(H0.mailbox)[1];
   if (reinterpret_cast<volatile uint64_t*>(H0.mailbox)[2] != 0)
     return fail(CRUM_ETIMEOUT, "hash kernel: a bounded device wait ran out");
+  const uint64_t n = img->n_dirty, A = img->n_allocs, hs = s->half_slots;
+  const bool comp = img->compressed;
+  const uint64_t poff = cmeta_bytes(A, n);
+  if (comp) {
+    // sized for the plain payload until the chunks are encoded, then trimmed
+    img->payload_off = poff;
+    img->payload_bytes = n * kPage;
+    // the compressed checksum is summed afresh (the scan left the plain
+    // form's header in it)
+    CK(cudaMemsetAsync(H0.scalars + 1, 0, sizeof(uint64_t), s->cap_stream));
+  }
   st = alloc_image_host(s, img);
   if (st != CRUM_OK) return st;
-  const uint64_t n = img->n_dirty, A = img->n_allocs, hs = s->half_slots;
+  uint64_t* const offs = reinterpret_cast<uint64_t*>(H0.meta + kHeaderBytes + 16 * A + 16 * n);
+  uint64_t enc_base = 0;  // encoded bytes of the chunks before this one
   int h = img->half;
   for (uint64_t s0 = 0; s0 < n || s0 == 0; s0 += hs) {
     const uint64_t s1 = std::min(n, s0 + hs);
@@ -544,23 +556,76 @@ crum_status checkpoint_chunked(crum_set* s, crum_image* img, cudaStream_t app,
     g.payload = H.payload;
     g.s_begin = s0;
     g.s_end = s1;
+    if (comp) g.trailer = H0.cn + 1;  // the plain form's checksum is not wanted
     CK(crum::launch_gather(g, s1 - s0, s->map_gather, false, s->cap_stream));
+    if (s1 == n) {
+      // every dirty page is in staging: the application continues while the
+      // last chunk is encoded and the image's tables are finished
+      CK(cudaEventRecord(img->ev_captured, s->cap_stream));
+      CK(cudaStreamWaitEvent(app, img->ev_captured, 0));
+    }
     if (n == 0) break;
+    const uint8_t* src = H.payload;
+    uint64_t bytes = (s1 - s0) * kPage, host_off = poff + s0 * kPage;
+    if (comp) {
+      // this chunk's slots: sizes, offsets after enc_base, code, checksum
+      const uint64_t m = s1 - s0;
+      CK(cudaMemcpyAsync(H.cn, &m, sizeof m, cudaMemcpyHostToDevice, s->cap_stream));
+      crum::BpdSizeArgs za{H.payload, H.cn, H.enc_len};
+      CK(crum::launch_bpd_size(za, m, s->cap_stream));
+      crum::BpdScanArgs qa{H.enc_len, H.cn, offs + s0, enc_base, H.ctotal, H.mailbox_dev, H0.meta,
+                           static_cast<uint32_t>(A)};
+      CK(crum::launch_bpd_scan(qa, s->cap_stream));
+      CK(cudaEventRecord(H.ev_sized, s->cap_stream));
+      if ((st = wait_event(H.ev_sized, kBackgroundLimitNs)) != CRUM_OK) return st;
+      bytes = reinterpret_cast<volatile uint64_t*>(H.mailbox)[3];
+      crum::BpdEncodeArgs ea{H.payload, H.cn, offs + s0, enc_base, H.cpay, H0.meta, static_cast<uint32_t>(A)};
+      CK(crum::launch_bpd_encode(ea, m, s->cap_stream));
+      CK(crum::launch_hash_bytes(H.cpay, bytes, (poff + enc_base) / 8, H0.scalars + 1, s->cap_stream));
+      src = H.cpay;
+      host_off = poff + enc_base;
+      enc_base += bytes;
+    } else {
+      host_off = meta_bytes(A, n) + s0 * kPage;
+    }
     cudaEvent_t ev;
     CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     CK(cudaEventRecord(ev, s->cap_stream));
     CK(cudaStreamWaitEvent(s->drain_stream, ev, 0));
     CK(cudaEventDestroy(ev));  // released once the recorded work completes
     if (s0 == 0) CK(cudaEventRecord(img->ev_d0, s->drain_stream));  // drain starts here
-    if ((st = drain_payload(s, img, s0, H.payload, (s1 - s0) * kPage)) != CRUM_OK) return st;
+    if ((st = drain_payload(s, img, host_off, src, bytes)) != CRUM_OK) return st;
     CK(cudaEventRecord(H.ev_drained, s->drain_stream));
     h ^= 1;
   }
-  CK(cudaEventRecord(img->ev_captured, s->cap_stream));
-  CK(cudaStreamWaitEvent(app, img->ev_captured, 0));
-  CK(cudaStreamWaitEvent(s->drain_stream, img->ev_captured, 0));
+  if (comp) {
+    // the compressed header words, the padding after the tables, and the
+    // tables' share of the checksum; then the image buffer shrinks to fit
+    const uint64_t final_len = poff + enc_base + 8;
+    const uint64_t tab_end = kHeaderBytes + 16 * A + 24 * n;
+    const uint64_t w1 = 2ull | ((static_cast<uint64_t>(img->full ? 1u : 0u) | 2ull) << 32);
+    if (poff > tab_end) CK(cudaMemsetAsync(H0.meta + tab_end, 0, poff - tab_end, s->cap_stream));
+    CK(cudaMemcpyAsync(H0.meta + 8, &w1, 8, cudaMemcpyHostToDevice, s->cap_stream));
+    CK(cudaMemcpyAsync(H0.meta + 48, &poff, 8, cudaMemcpyHostToDevice, s->cap_stream));
+    CK(cudaMemcpyAsync(H0.meta + 56, &final_len, 8, cudaMemcpyHostToDevice, s->cap_stream));
+    CK(crum::launch_hash_bytes(H0.meta, poff, 0, H0.scalars + 1, s->cap_stream));
+    img->payload_bytes = enc_base;
+    img->image_bytes = final_len;
+    if (!img->drop_payload) {
+      const size_t have = (img->host_len + 4095) & ~size_t(4095), need = (final_len + 4095) & ~size_t(4095);
+      if (have > need) img->pool->free(img->host + need, have - need);
+      img->host_len = final_len;
+    }
+  }
+  {
+    cudaEvent_t ev;  // the tables and the trailer are final
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CK(cudaEventRecord(ev, s->cap_stream));
+    CK(cudaStreamWaitEvent(s->drain_stream, ev, 0));
+    CK(cudaEventDestroy(ev));
+  }
   if (n == 0) CK(cudaEventRecord(img->ev_d0, s->drain_stream));  // no payload chunk was copied
-  CK(cudaMemcpyAsync(img->host, H0.meta, meta_bytes(A, n), cudaMemcpyDeviceToHost, s->drain_stream));
+  CK(cudaMemcpyAsync(img->host, H0.meta, payload_offset(img), cudaMemcpyDeviceToHost, s->drain_stream));
   CK(cudaMemcpyAsync(trailer_dst(img), H0.scalars + 1, 8, cudaMemcpyDeviceToHost, s->drain_stream));
   CK(cudaEventRecord(img->ev_drained, s->drain_stream));
   CK(cudaEventRecord(s->half[0].ev_drained, s->drain_stream));
@@ -844,6 +909,7 @@ crum_status crum_set_create(const crum_config* cfg_in, crum_set** out) {
       }
       CK(cudaMalloc(&H.enc_len, std::max<uint64_t>(s->half_slots, 1) * sizeof(uint32_t)));
       CK(cudaMalloc(&H.ctotal, sizeof(uint64_t)));
+      CK(cudaMalloc(&H.cn, 2 * sizeof(uint64_t)));
       CK(cudaEventCreateWithFlags(&H.ev_sized, cudaEventDisableTiming));
       CK(cudaEventCreateWithFlags(&H.ev_encoded, cudaEventDisableTiming));
     }
@@ -896,6 +962,7 @@ crum_status crum_set_destroy(crum_set* s) {
     cudaFree(H.cpay);
     cudaFree(H.enc_len);
     cudaFree(H.ctotal);
+    cudaFree(H.cn);
     if (H.ev_sized) cudaEventDestroy(H.ev_sized);
     if (H.ev_encoded) cudaEventDestroy(H.ev_encoded);
   }
@@ -1217,8 +1284,6 @@ crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, cr
   const bool fast = s->n_pages <= s->half_slots;
   if (!fast && gather_shadow)
     return bail(fail(CRUM_EINVAL, "verify mode needs staging that holds every page"));
-  if (!fast && s->cfg.compress)
-    return bail(fail(CRUM_EINVAL, "compression needs staging that holds every page"));
   img->compressed = s->cfg.compress != 0;
   if (fast) {
     ga.payload = H.payload;
@@ -1257,15 +1322,17 @@ crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, cr
     if (ce == cudaSuccess && fast)
       ce = crum::launch_gather(ga, s->n_pages, s->map_gather, gather_shadow, s->cap_stream);
     if (ce == cudaSuccess && fast) ce = cudaEventRecord(img->ev_captured, s->cap_stream);
-    if (ce == cudaSuccess && img->compressed) {
+    if (ce == cudaSuccess && fast && img->compressed) {
       // the application has its memory back; the staged slots are encoded
       // behind it: sizes, offsets and header, then the code and checksum
       crum::BpdSizeArgs za{H.payload, H.scalars, H.enc_len};
       ce = crum::launch_bpd_size(za, s->n_pages, s->cap_stream);
-      crum::BpdScanArgs qa{H.enc_len, H.scalars, img->n_allocs, H.meta, H.ctotal, H.mailbox_dev};
+      // the whole image: the kernels place the offset table after the
+      // hashes once n is known on the device
+      crum::BpdScanArgs qa{H.enc_len, H.scalars, nullptr, 0, H.ctotal, H.mailbox_dev, H.meta, img->n_allocs};
       if (ce == cudaSuccess) ce = crum::launch_bpd_scan(qa, s->cap_stream);
       if (ce == cudaSuccess) ce = cudaEventRecord(H.ev_sized, s->cap_stream);
-      crum::BpdEncodeArgs ea{H.payload, H.scalars, H.meta, img->n_allocs, H.cpay};
+      crum::BpdEncodeArgs ea{H.payload, H.scalars, nullptr, 0, H.cpay, H.meta, img->n_allocs};
       if (ce == cudaSuccess) ce = crum::launch_bpd_encode(ea, s->n_pages, s->cap_stream);
       if (ce == cudaSuccess) ce = cudaMemsetAsync(H.scalars + 1, 0, sizeof(uint64_t), s->cap_stream);
       crum::BpdChecksumArgs ka{H.meta, H.cpay, H.scalars, H.ctotal, img->n_allocs,

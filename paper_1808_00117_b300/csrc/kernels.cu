@@ -568,7 +568,7 @@ __global__ void __launch_bounds__(1024) k_bpd_scan(BpdScanArgs a) {
   __shared__ unsigned long long wsum[32];
   __shared__ unsigned long long total_sh;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint64_t n = *a.n_dirty;
+  const uint64_t n = *a.n;
   const uint64_t A = a.n_allocs;
   const uint64_t seg = (n + 31) / 32;
   const uint64_t s0 = min(static_cast<uint64_t>(warp) * seg, n), s1 = min(s0 + seg, n);
@@ -590,8 +590,9 @@ __global__ void __launch_bounds__(1024) k_bpd_scan(BpdScanArgs a) {
     if (lane == 31) total_sh = incl;
   }
   __syncthreads();
-  unsigned long long carry = wsum[warp];
-  uint64_t* off = reinterpret_cast<uint64_t*>(a.meta + kHeaderBytes + 16 * A + 16 * n);
+  unsigned long long carry = wsum[warp] + a.base;
+  uint64_t* off = a.offs != nullptr ? a.offs
+                                    : reinterpret_cast<uint64_t*>(a.meta + kHeaderBytes + 16 * A + 16 * n);
   for (uint64_t base = s0; base < s1; base += 32) {
     const uint64_t s = base + lane;
     const unsigned long long len = s < s1 ? a.enc_len[s] : 0ull;
@@ -606,14 +607,16 @@ __global__ void __launch_bounds__(1024) k_bpd_scan(BpdScanArgs a) {
   }
   if (tid == 0) {
     const uint64_t total = total_sh;
-    const uint64_t tab_end = kHeaderBytes + 16 * A + 24 * n;
-    const uint64_t poff = (tab_end + 15) & ~15ull;
-    for (uint64_t b = tab_end; b < poff; ++b) a.meta[b] = 0;
-    uint64_t* h = reinterpret_cast<uint64_t*>(a.meta);
-    const uint64_t flags = (h[1] >> 32) | 2ull;
-    h[1] = 2ull | (flags << 32);
-    h[6] = poff;
-    h[7] = poff + total + 8;
+    if (a.offs == nullptr) {
+      const uint64_t tab_end = kHeaderBytes + 16 * A + 24 * n;
+      const uint64_t poff = (tab_end + 15) & ~15ull;
+      for (uint64_t b = tab_end; b < poff; ++b) a.meta[b] = 0;
+      uint64_t* h = reinterpret_cast<uint64_t*>(a.meta);
+      const uint64_t flags = (h[1] >> 32) | 2ull;
+      h[1] = 2ull | (flags << 32);
+      h[6] = poff;
+      h[7] = poff + total + 8;
+    }
     *a.total_out = total;
     if (a.mailbox != nullptr) {
       a.mailbox[3] = total;
@@ -630,9 +633,10 @@ __global__ void __launch_bounds__(kBpdThreads) k_bpd_encode(BpdEncodeArgs a) {
   uint8_t* plane = dyn + kPage;        // kPlaneBytes bytes
   __shared__ BpdSmem m;
   const int tid = threadIdx.x;
-  const uint64_t n = *a.n_dirty;
-  const uint64_t A = a.n_allocs;
-  const uint64_t* off = reinterpret_cast<const uint64_t*>(a.meta + kHeaderBytes + 16 * A + 16 * n);
+  const uint64_t n = *a.n;
+  const uint64_t* off =
+      a.offs != nullptr ? a.offs
+                        : reinterpret_cast<const uint64_t*>(a.meta + kHeaderBytes + 16ull * a.n_allocs + 16 * n);
   for (uint64_t s = blockIdx.x; s < n; s += gridDim.x) {
     for (uint32_t i = tid; i < 8 * 256 / 4; i += blockDim.x) reinterpret_cast<uint32_t*>(m.present)[i] = 0;
     __syncthreads();
@@ -644,7 +648,7 @@ __global__ void __launch_bounds__(kBpdThreads) k_bpd_encode(BpdEncodeArgs a) {
     }
     __syncthreads();
     bpd_plan(m);
-    uint8_t* out = a.out + off[s];
+    uint8_t* out = a.out + (off[s] - a.base);
     if (m.len == kPage) {
       for (uint32_t v = tid; v < kPageVecs; v += blockDim.x)
         reinterpret_cast<uint4*>(out)[v] = reinterpret_cast<const uint4*>(page)[v];

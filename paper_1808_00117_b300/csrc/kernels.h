@@ -130,21 +130,32 @@ struct BpdSizeArgs {
   uint32_t* enc_len;         // out: encoded length of every slot
 };
 
+// Offsets of `n` encoded slots (base + exclusive prefix of their lengths)
+// into offs[0, n).  With offs null the slots are a whole image's (base 0):
+// the table is the image's own (64 + 16 A + 16 n into meta), and the header
+// words of the compressed form and the padding after the tables are
+// written too.
 struct BpdScanArgs {
   const uint32_t* enc_len;
-  const uint64_t* n_dirty;
+  const uint64_t* n;         // device: slots
+  uint64_t* offs;            // or null, see above
+  uint64_t base;
+  uint64_t* total_out;       // device: encoded bytes of these slots
+  volatile uint64_t* mailbox;  // [3] = the same (optional)
+  uint8_t* meta;
   uint32_t n_allocs;
-  uint8_t* meta;             // header words rewritten, offset table + padding written
-  uint64_t* total_out;       // device: encoded payload bytes
-  volatile uint64_t* mailbox;  // [3] = encoded payload bytes (optional)
 };
 
+// Encodes slot s of `payload` to out + offs[s] - base, s < n (offs null:
+// the image's own table in meta, as for BpdScanArgs).
 struct BpdEncodeArgs {
   const uint8_t* payload;    // raw slots
-  const uint64_t* n_dirty;
-  const uint8_t* meta;       // offset table at 64 + 16 A + 16 n
+  const uint64_t* n;         // device: slots
+  const uint64_t* offs;
+  uint64_t base;
+  uint8_t* out;              // encoded bytes
+  const uint8_t* meta;
   uint32_t n_allocs;
-  uint8_t* out;              // encoded payload
 };
 
 // Replay restore of a compressed image's slots [0, n_slots): slot s is

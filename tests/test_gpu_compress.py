@@ -129,13 +129,46 @@ def test_compressed_no_payload_and_verify():
     s.destroy()
 
 
-def test_compression_needs_staging_for_every_page():
-    sizes = [20 * P]
-    bufs = device_buffers(sizes, seed=89)
-    s = make_set(bufs, compress=1, staging_bytes=4 * P)
-    with pytest.raises(crum.CrumError) as e:
-        s.checkpoint(stream_handle())
-    assert e.value.status == crum.EINVAL
+@pytest.mark.parametrize("kind", ["fp32", "u32"])
+def test_compressed_chunked_capture_equals_the_oracle(kind):
+    # staging of 3 slots per half: the dirty pages are encoded and drained
+    # in chunks, each chunk's code placed after the ones before it
+    sizes = [20 * P + 40, 7 * P, 8]
+    bufs = device_buffers(sizes, seed=91, kind=kind)
+    s = make_set(bufs, compress=1, staging_bytes=6 * P)
+    o = oracle.OracleSet(sizes, compress=True)
+    chain, states = [], []
+    for step, frac in enumerate([None, 0.4, 0.0, 0.05]):
+        if frac:
+            mutate(bufs, sizes, frac, seed=910 + step)
+        img, got = _ckpt(s)
+        states.append(host_copies(bufs))
+        exp, *_ = o.checkpoint(states[-1])
+        assert oracle.image_version(got) == 2
+        assert first_diff(got, exp) is None, f"step {step}"
+        assert img.info()["image_bytes"] == len(exp)
+        chain.append(img)
+    for mode in (crum.RESTORE_REPLAY, crum.RESTORE_MERGED, crum.RESTORE_DELTA):
+        r = make_set(bufs, restore_mode=mode)
+        for k in (3, 0, 1):
+            for i, b in enumerate(bufs):
+                W.fill_(b, 9100 + k + 10 * i, "u32")
+            r.restore(chain[k], stream_handle())
+            torch().cuda.synchronize()
+            assert all(np.array_equal(g, w) for g, w in zip(host_copies(bufs), states[k])), (mode, k)
+        r.destroy()
+    # a payload that is not kept still crosses the link and is summed
+    img = s.checkpoint(stream_handle(), crum.FULL | crum.NO_PAYLOAD)
+    img.wait()
+    exp, *_ = o.checkpoint(host_copies(bufs), full=True)
+    assert img.info()["checksum"] == int(np.frombuffer(exp[-8:], dtype=np.uint64)[0])
+    assert img.info()["image_bytes"] == len(exp)
+    img.release()
+    for c in chain:
+        c.release()
     s.destroy()
+
+
+def test_compression_rejects_external_staging():
     with pytest.raises(crum.CrumError):
         crum.CheckpointSet(compress=1, external_staging=1)
