@@ -223,13 +223,15 @@ def measured_peaks() -> dict:
 
 
 def kernel_code_digest() -> str:
-    """First 16 hex digits of the sha256 of the device code (kernels.cu and
-    device.cuh) with comments and whitespace removed, so that editing a
-    comment keeps a recorded profile valid and editing code does not."""
+    """First 16 hex digits of the sha256 of the capture kernels' code
+    (kernels.cu with its headers kernels.h, launch.cuh and device.cuh) with
+    comments and whitespace removed, so that editing a comment, or the
+    compression and restore kernels, keeps a recorded profile of a capture
+    kernel valid, and editing its code does not."""
     import hashlib
     import re
     h = hashlib.sha256()
-    for name in ("kernels.cu", "device.cuh"):
+    for name in ("kernels.cu", "kernels.h", "launch.cuh", "device.cuh"):
         text = open(os.path.join(ROOT, "paper_1808_00117_b300", "csrc", name)).read()
         text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
         text = re.sub(r"//[^\n]*", " ", text)

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libcrum.so")
-SOURCES = ["kernels.cu", "engine.cu", "serve.cu", "noalloc.cu"]
+SOURCES = ["kernels.cu", "codec.cu", "restore.cu", "engine.cu", "serve.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

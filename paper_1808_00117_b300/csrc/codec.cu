@@ -1,0 +1,279 @@
+// Kernels of the byte-plane dictionary code on the capture side and their
+// launchers (the code itself is stated in codec.cuh and include/crum.h).
+//
+//   k_bpd_size      one CTA per staged slot: alphabet of each byte plane and
+//                   the slot's encoded length
+//   k_bpd_scan      one CTA: slot offsets (exclusive prefix of the lengths),
+//                   encoded payload size, compressed-form header words
+//   k_bpd_encode    one CTA per slot: the slot's code at its offset
+//   k_bpd_checksum  the compressed image's trailer hash
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+
+#include "codec.cuh"
+#include "device.cuh"
+#include "kernels.h"
+#include "launch.cuh"
+
+namespace crum {
+namespace {
+
+using dev::hash_vec;
+using dev::ld_stream;
+
+// present[plane][value] for every byte of one 16-byte vector of the slot
+// (several threads may store the same 1; no atomics needed).
+__device__ __forceinline__ void bpd_mark(const uint4& x, BpdSmem& m) {
+  const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int t = 0; t < 4; ++t) m.present[(q & 1) * 4 + t][(w[q] >> (8 * t)) & 255u] = 1;
+}
+
+// Alphabet size, width, ranks and section layout of every plane (CTA-wide,
+// after the presence marks; leaves the CTA synchronised).
+__device__ void bpd_plan(BpdSmem& m) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp < 8) {
+    uint32_t c = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) c += m.present[warp][lane * 8 + j];
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    uint32_t r = incl - c;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      m.rank[warp][lane * 8 + j] = static_cast<uint8_t>(r);
+      r += m.present[warp][lane * 8 + j];
+    }
+    if (lane == 31) {
+      m.k[warp] = incl;
+      m.b[warp] = ceil_log2(incl);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t pos = 16;
+    for (int j = 0; j < 8; ++j) {
+      m.sec[j] = pos;
+      pos += m.b[j] == 8 ? kPlaneBytes : ((m.k[j] + 15u) & ~15u) + 1024u * m.b[j];
+    }
+    m.sec[8] = pos;
+    m.len = pos >= kPage ? static_cast<uint32_t>(kPage) : pos;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBpdThreads) k_bpd_size(BpdSizeArgs a) {
+  __shared__ BpdSmem m;
+  const uint64_t n = *a.n_dirty;
+  for (uint64_t s = blockIdx.x; s < n; s += gridDim.x) {
+    for (uint32_t i = threadIdx.x; i < 8 * 256 / 4; i += blockDim.x)
+      reinterpret_cast<uint32_t*>(m.present)[i] = 0;
+    __syncthreads();
+    const uint8_t* slot = a.payload + s * kPage;
+    for (uint32_t v = threadIdx.x; v < kPageVecs; v += blockDim.x) bpd_mark(ld_stream(slot + 16ull * v), m);
+    __syncthreads();
+    bpd_plan(m);
+    if (threadIdx.x == 0) a.enc_len[s] = m.len;
+    __syncthreads();
+  }
+}
+
+// Slot offsets (exclusive prefix of the encoded lengths) into the image's
+// offset table, the encoded payload size, and the header words that differ
+// in the compressed form.  One CTA; warp w owns a contiguous segment.
+__global__ void __launch_bounds__(1024) k_bpd_scan(BpdScanArgs a) {
+  __shared__ unsigned long long wsum[32];
+  __shared__ unsigned long long total_sh;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint64_t n = *a.n;
+  const uint64_t A = a.n_allocs;
+  const uint64_t seg = (n + 31) / 32;
+  const uint64_t s0 = min(static_cast<uint64_t>(warp) * seg, n), s1 = min(s0 + seg, n);
+  unsigned long long cnt = 0;
+  for (uint64_t s = s0 + lane; s < s1; s += 32) cnt += a.enc_len[s];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if (lane == 0) wsum[warp] = cnt;
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned long long x = wsum[lane];
+    unsigned long long incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    wsum[lane] = incl - x;
+    if (lane == 31) total_sh = incl;
+  }
+  __syncthreads();
+  unsigned long long carry = wsum[warp] + a.base;
+  uint64_t* off = a.offs != nullptr ? a.offs
+                                    : reinterpret_cast<uint64_t*>(a.meta + kHeaderBytes + 16 * A + 16 * n);
+  for (uint64_t base = s0; base < s1; base += 32) {
+    const uint64_t s = base + lane;
+    const unsigned long long len = s < s1 ? a.enc_len[s] : 0ull;
+    unsigned long long incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (s < s1) off[s] = carry + incl - len;
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (tid == 0) {
+    const uint64_t total = total_sh;
+    if (a.offs == nullptr) {
+      const uint64_t tab_end = kHeaderBytes + 16 * A + 24 * n;
+      const uint64_t poff = (tab_end + 15) & ~15ull;
+      for (uint64_t b = tab_end; b < poff; ++b) a.meta[b] = 0;
+      uint64_t* h = reinterpret_cast<uint64_t*>(a.meta);
+      const uint64_t flags = (h[1] >> 32) | 2ull;
+      h[1] = 2ull | (flags << 32);
+      h[6] = poff;
+      h[7] = poff + total + 8;
+    }
+    *a.total_out = total;
+    if (a.mailbox != nullptr) {
+      a.mailbox[3] = total;
+      __threadfence_system();
+    }
+  }
+}
+
+// Encodes slot s into out + offset[s] (dynamic shared memory: the 64 KiB
+// slot and one 8 KiB plane).
+__global__ void __launch_bounds__(kBpdThreads) k_bpd_encode(BpdEncodeArgs a) {
+  extern __shared__ __align__(16) uint8_t dyn[];
+  uint8_t* page = dyn;                 // kPage bytes
+  uint8_t* plane = dyn + kPage;        // kPlaneBytes bytes
+  __shared__ BpdSmem m;
+  const int tid = threadIdx.x;
+  const uint64_t n = *a.n;
+  const uint64_t* off =
+      a.offs != nullptr ? a.offs
+                        : reinterpret_cast<const uint64_t*>(a.meta + kHeaderBytes + 16ull * a.n_allocs + 16 * n);
+  for (uint64_t s = blockIdx.x; s < n; s += gridDim.x) {
+    for (uint32_t i = tid; i < 8 * 256 / 4; i += blockDim.x) reinterpret_cast<uint32_t*>(m.present)[i] = 0;
+    __syncthreads();
+    const uint8_t* slot = a.payload + s * kPage;
+    for (uint32_t v = tid; v < kPageVecs; v += blockDim.x) {
+      const uint4 x = ld_stream(slot + 16ull * v);
+      reinterpret_cast<uint4*>(page)[v] = x;
+      bpd_mark(x, m);
+    }
+    __syncthreads();
+    bpd_plan(m);
+    uint8_t* out = a.out + (off[s] - a.base);
+    if (m.len == kPage) {
+      for (uint32_t v = tid; v < kPageVecs; v += blockDim.x)
+        reinterpret_cast<uint4*>(out)[v] = reinterpret_cast<const uint4*>(page)[v];
+      __syncthreads();
+      continue;
+    }
+    if (tid < 16)
+      out[tid] = tid < 8 ? static_cast<uint8_t>(m.b[tid])
+                         : static_cast<uint8_t>(m.b[tid - 8] == 8 ? 255u : m.k[tid - 8] - 1u);
+    for (int j = 0; j < 8; ++j) {
+      const uint32_t b = m.b[j];
+      // plane j into `plane`: its bytes (stored plane) or their ranks
+      for (uint32_t i = tid; i < kPlaneBytes; i += blockDim.x) {
+        const uint8_t x = page[8 * i + j];
+        plane[i] = b == 8 ? x : m.rank[j][x];
+      }
+      __syncthreads();
+      uint8_t* sec = out + m.sec[j];
+      if (b == 8) {
+        for (uint32_t v = tid; v < kPlaneBytes / 16; v += blockDim.x)
+          reinterpret_cast<uint4*>(sec)[v] = reinterpret_cast<const uint4*>(plane)[v];
+      } else {
+        const uint32_t k = m.k[j], dpad = (k + 15u) & ~15u;
+        if (m.present[j][tid]) sec[m.rank[j][tid]] = static_cast<uint8_t>(tid);
+        for (uint32_t i = k + tid; i < dpad; i += blockDim.x) sec[i] = 0;
+        if (b > 0) {
+          const uint4 r0 = reinterpret_cast<const uint4*>(plane)[2 * tid];
+          const uint4 r1 = reinterpret_cast<const uint4*>(plane)[2 * tid + 1];
+          const uint32_t rw[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+          uint32_t* words = reinterpret_cast<uint32_t*>(sec + dpad) + tid * b;
+          uint64_t acc = 0;
+          uint32_t nb = 0, e = 0;
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            acc |= static_cast<uint64_t>((rw[q >> 2] >> (8 * (q & 3))) & 255u) << nb;
+            nb += b;
+            if (nb >= 32) {
+              words[e++] = static_cast<uint32_t>(acc);
+              acc >>= 32;
+              nb -= 32;
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Image checksum of a compressed image: the header and tables (word index
+// from 0) plus the encoded payload (word index from the payload offset).
+__global__ void __launch_bounds__(256) k_bpd_checksum(BpdChecksumArgs a) {
+  const uint64_t n = *a.n_dirty;
+  const uint64_t A = a.n_allocs;
+  const uint64_t poff = (kHeaderBytes + 16 * A + 24 * n + 15) & ~15ull;
+  const uint64_t meta_vecs = poff / 16, enc_vecs = *a.total / 16;
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  uint64_t h = 0;
+  for (uint64_t v = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < meta_vecs + enc_vecs;
+       v += stride) {
+    if (v < meta_vecs)
+      h += hash_vec(ld_stream(a.meta + 16 * v), (2 * v) * kPhi);
+    else
+      h += hash_vec(ld_stream(a.enc + 16 * (v - meta_vecs)), (2 * v) * kPhi);
+  }
+  h = dev::warp_sum(h);
+  if ((threadIdx.x & 31) == 0 && h != 0) atomicAdd(a.trailer, static_cast<unsigned long long>(h));
+}
+
+}  // namespace
+
+cudaError_t launch_bpd_size(const BpdSizeArgs& a, uint64_t max_slots, cudaStream_t st) {
+  if (max_slots == 0) return cudaSuccess;
+  const unsigned grid = grid_for(k_bpd_size, max_slots, 1, kBpdThreads);
+  k_bpd_size<<<grid, kBpdThreads, 0, st>>>(a);
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bpd_scan(const BpdScanArgs& a, cudaStream_t st) {
+  k_bpd_scan<<<1, 1024, 0, st>>>(a);
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bpd_encode(const BpdEncodeArgs& a, uint64_t max_slots, cudaStream_t st) {
+  if (max_slots == 0) return cudaSuccess;
+  cudaError_t e = allow_big_smem(k_bpd_encode);
+  if (e != cudaSuccess) return e;
+  k_bpd_encode<<<bpd_grid(k_bpd_encode, max_slots), kBpdThreads, kBpdDynSmem, st>>>(a);
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bpd_checksum(const BpdChecksumArgs& a, uint64_t max_bytes, cudaStream_t st) {
+  const unsigned grid = grid_for(k_bpd_checksum, (max_bytes / 16 + 255) / 256 + 1, 1, 256);
+  k_bpd_checksum<<<grid, 256, 0, st>>>(a);
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+}  // namespace crum

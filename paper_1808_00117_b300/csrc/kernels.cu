@@ -1,4 +1,4 @@
-// Kernels of the capture/restore path and their host-side launchers.
+// Capture kernels and their host-side launchers.
 //
 //   k_hash_dirty  hash every page of the flattened work-list, compare with
 //                 the committed hash, commit the new one, set dirty bits
@@ -9,15 +9,10 @@
 //   k_gather      one group per dirty slot: page table entry, hash entry and
 //                 the page's bytes into staging ("drain the device", Sections
 //                 3.3-3.4), plus the image checksum of everything it writes
-//   k_restore     inverse scatter of image slots onto the allocations and
-//                 installation of the image hashes (Section 3.4 restart)
-//   k_chain_owner newest (image, slot) of every page over a restore chain
-//   k_restore_merged  every page once from that image, read from the
-//                 image's pinned host memory (optionally only pages whose
-//                 current hash differs: delta restore)
 //   k_hash_bytes  the hash over an arbitrary byte string (image checksum)
 //   k_hash_dirty_bulk  k_hash_dirty with pages staged into shared memory by
 //                 cp.async.bulk (warp-specialised; bounded mbarrier waits)
+// The compression kernels are in codec.cu, the restore kernels in restore.cu.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,6 +25,7 @@
 #include "crum.h"
 #include "device.cuh"
 #include "kernels.h"
+#include "launch.cuh"
 
 namespace crum {
 
@@ -440,521 +436,6 @@ __global__ void __launch_bounds__(256) k_gather(GatherArgs a) {
   }
 }
 
-// --------------------------------------------------------------- restore ---
-
-template <int G>
-__global__ void __launch_bounds__(256) k_restore(RestoreArgs a) {
-  constexpr int kGroupsPerCta = (G == 32) ? 256 / 32 : 1;
-  const int t = threadIdx.x % G;
-  const uint64_t group = static_cast<uint64_t>(blockIdx.x) * kGroupsPerCta + threadIdx.x / G;
-  const uint64_t n_groups = static_cast<uint64_t>(gridDim.x) * kGroupsPerCta;
-  for (uint64_t s = group; s < a.n_slots; s += n_groups) {
-    const uint32_t k = a.ptab[2 * s];
-    const uint64_t p = a.ptab[2 * s + 1];
-    if (k >= a.n_allocs || p >= a.allocs[k].n_pages) continue;  // rejected on the host already
-    uint8_t* dst = a.allocs[k].base + p * kPage;
-    const uint32_t valid = dev::valid_bytes(a.allocs[k].bytes, p);
-    const uint8_t* src = a.payload + s * kPage;
-    const uint32_t nvec = valid >> 4;
-    for (uint32_t v = t; v < nvec; v += G)
-      *reinterpret_cast<uint4*>(dst + 16ull * v) = ld_stream(src + 16ull * v);
-    const uint32_t rem = valid & 15u;
-    if (rem != 0 && t == 0)
-      for (uint32_t b = 0; b < rem; ++b) dst[16ull * nvec + b] = src[16ull * nvec + b];
-    if (t == 0) a.h_table[a.allocs[k].first_page + p] = a.hashes[s];
-  }
-}
-
-// ------------------------------------------- byte-plane dictionary code ---
-//
-// Optional compression of the drained payload.  A slot (64 KiB: the page's
-// valid bytes, then zeros) is split into 8 byte planes of 8,192 bytes
-// (plane j = bytes 8i + j).  A plane with k distinct values and
-// b = ceil(log2 k) < 8 is stored as its values in ascending order (padded
-// to 16 bytes) and 1,024 b bytes holding each byte's position among them, b
-// bits each, LSB first; a plane with b = 8 is stored as is.  A 16-byte head
-// (b of each plane, then k - 1, 255 for a stored plane) leads; a slot whose
-// code would not be shorter than 64 KiB is stored as is.  One CTA of 256
-// threads handles one slot; group q of 32 consecutive plane bytes belongs
-// to thread q, so its b bits x 32 are exactly b words of the packed stream.
-
-constexpr uint32_t kPlaneBytes = kPage / 8;
-constexpr int kBpdThreads = 256;
-
-struct BpdSmem {
-  uint8_t present[8][256];
-  uint8_t rank[8][256];
-  uint32_t k[8];
-  uint32_t b[8];
-  uint32_t sec[9];  // section offsets in the encoded slot; sec[8] = code length
-  uint32_t len;     // encoded length (kPage: stored as is)
-  int skip;
-};
-
-__device__ __forceinline__ uint32_t ceil_log2(uint32_t k) {
-  uint32_t b = 0;
-  while ((1u << b) < k) ++b;
-  return b;
-}
-
-// present[plane][value] for every byte of one 16-byte vector of the slot
-// (several threads may store the same 1; no atomics needed).
-__device__ __forceinline__ void bpd_mark(const uint4& x, BpdSmem& m) {
-  const uint32_t w[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-#pragma unroll
-    for (int t = 0; t < 4; ++t) m.present[(q & 1) * 4 + t][(w[q] >> (8 * t)) & 255u] = 1;
-}
-
-// Alphabet size, width, ranks and section layout of every plane (CTA-wide,
-// after the presence marks; leaves the CTA synchronised).
-__device__ void bpd_plan(BpdSmem& m) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (warp < 8) {
-    uint32_t c = 0;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) c += m.present[warp][lane * 8 + j];
-    uint32_t incl = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    uint32_t r = incl - c;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      m.rank[warp][lane * 8 + j] = static_cast<uint8_t>(r);
-      r += m.present[warp][lane * 8 + j];
-    }
-    if (lane == 31) {
-      m.k[warp] = incl;
-      m.b[warp] = ceil_log2(incl);
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t pos = 16;
-    for (int j = 0; j < 8; ++j) {
-      m.sec[j] = pos;
-      pos += m.b[j] == 8 ? kPlaneBytes : ((m.k[j] + 15u) & ~15u) + 1024u * m.b[j];
-    }
-    m.sec[8] = pos;
-    m.len = pos >= kPage ? static_cast<uint32_t>(kPage) : pos;
-  }
-  __syncthreads();
-}
-
-__global__ void __launch_bounds__(kBpdThreads) k_bpd_size(BpdSizeArgs a) {
-  __shared__ BpdSmem m;
-  const uint64_t n = *a.n_dirty;
-  for (uint64_t s = blockIdx.x; s < n; s += gridDim.x) {
-    for (uint32_t i = threadIdx.x; i < 8 * 256 / 4; i += blockDim.x)
-      reinterpret_cast<uint32_t*>(m.present)[i] = 0;
-    __syncthreads();
-    const uint8_t* slot = a.payload + s * kPage;
-    for (uint32_t v = threadIdx.x; v < kPageVecs; v += blockDim.x) bpd_mark(ld_stream(slot + 16ull * v), m);
-    __syncthreads();
-    bpd_plan(m);
-    if (threadIdx.x == 0) a.enc_len[s] = m.len;
-    __syncthreads();
-  }
-}
-
-// Slot offsets (exclusive prefix of the encoded lengths) into the image's
-// offset table, the encoded payload size, and the header words that differ
-// in the compressed form.  One CTA; warp w owns a contiguous segment.
-__global__ void __launch_bounds__(1024) k_bpd_scan(BpdScanArgs a) {
-  __shared__ unsigned long long wsum[32];
-  __shared__ unsigned long long total_sh;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint64_t n = *a.n;
-  const uint64_t A = a.n_allocs;
-  const uint64_t seg = (n + 31) / 32;
-  const uint64_t s0 = min(static_cast<uint64_t>(warp) * seg, n), s1 = min(s0 + seg, n);
-  unsigned long long cnt = 0;
-  for (uint64_t s = s0 + lane; s < s1; s += 32) cnt += a.enc_len[s];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-  if (lane == 0) wsum[warp] = cnt;
-  __syncthreads();
-  if (warp == 0) {
-    const unsigned long long x = wsum[lane];
-    unsigned long long incl = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    wsum[lane] = incl - x;
-    if (lane == 31) total_sh = incl;
-  }
-  __syncthreads();
-  unsigned long long carry = wsum[warp] + a.base;
-  uint64_t* off = a.offs != nullptr ? a.offs
-                                    : reinterpret_cast<uint64_t*>(a.meta + kHeaderBytes + 16 * A + 16 * n);
-  for (uint64_t base = s0; base < s1; base += 32) {
-    const uint64_t s = base + lane;
-    const unsigned long long len = s < s1 ? a.enc_len[s] : 0ull;
-    unsigned long long incl = len;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    if (s < s1) off[s] = carry + incl - len;
-    carry += __shfl_sync(0xffffffffu, incl, 31);
-  }
-  if (tid == 0) {
-    const uint64_t total = total_sh;
-    if (a.offs == nullptr) {
-      const uint64_t tab_end = kHeaderBytes + 16 * A + 24 * n;
-      const uint64_t poff = (tab_end + 15) & ~15ull;
-      for (uint64_t b = tab_end; b < poff; ++b) a.meta[b] = 0;
-      uint64_t* h = reinterpret_cast<uint64_t*>(a.meta);
-      const uint64_t flags = (h[1] >> 32) | 2ull;
-      h[1] = 2ull | (flags << 32);
-      h[6] = poff;
-      h[7] = poff + total + 8;
-    }
-    *a.total_out = total;
-    if (a.mailbox != nullptr) {
-      a.mailbox[3] = total;
-      __threadfence_system();
-    }
-  }
-}
-
-// Encodes slot s into out + offset[s] (dynamic shared memory: the 64 KiB
-// slot and one 8 KiB plane).
-__global__ void __launch_bounds__(kBpdThreads) k_bpd_encode(BpdEncodeArgs a) {
-  extern __shared__ __align__(16) uint8_t dyn[];
-  uint8_t* page = dyn;                 // kPage bytes
-  uint8_t* plane = dyn + kPage;        // kPlaneBytes bytes
-  __shared__ BpdSmem m;
-  const int tid = threadIdx.x;
-  const uint64_t n = *a.n;
-  const uint64_t* off =
-      a.offs != nullptr ? a.offs
-                        : reinterpret_cast<const uint64_t*>(a.meta + kHeaderBytes + 16ull * a.n_allocs + 16 * n);
-  for (uint64_t s = blockIdx.x; s < n; s += gridDim.x) {
-    for (uint32_t i = tid; i < 8 * 256 / 4; i += blockDim.x) reinterpret_cast<uint32_t*>(m.present)[i] = 0;
-    __syncthreads();
-    const uint8_t* slot = a.payload + s * kPage;
-    for (uint32_t v = tid; v < kPageVecs; v += blockDim.x) {
-      const uint4 x = ld_stream(slot + 16ull * v);
-      reinterpret_cast<uint4*>(page)[v] = x;
-      bpd_mark(x, m);
-    }
-    __syncthreads();
-    bpd_plan(m);
-    uint8_t* out = a.out + (off[s] - a.base);
-    if (m.len == kPage) {
-      for (uint32_t v = tid; v < kPageVecs; v += blockDim.x)
-        reinterpret_cast<uint4*>(out)[v] = reinterpret_cast<const uint4*>(page)[v];
-      __syncthreads();
-      continue;
-    }
-    if (tid < 16)
-      out[tid] = tid < 8 ? static_cast<uint8_t>(m.b[tid])
-                         : static_cast<uint8_t>(m.b[tid - 8] == 8 ? 255u : m.k[tid - 8] - 1u);
-    for (int j = 0; j < 8; ++j) {
-      const uint32_t b = m.b[j];
-      // plane j into `plane`: its bytes (stored plane) or their ranks
-      for (uint32_t i = tid; i < kPlaneBytes; i += blockDim.x) {
-        const uint8_t x = page[8 * i + j];
-        plane[i] = b == 8 ? x : m.rank[j][x];
-      }
-      __syncthreads();
-      uint8_t* sec = out + m.sec[j];
-      if (b == 8) {
-        for (uint32_t v = tid; v < kPlaneBytes / 16; v += blockDim.x)
-          reinterpret_cast<uint4*>(sec)[v] = reinterpret_cast<const uint4*>(plane)[v];
-      } else {
-        const uint32_t k = m.k[j], dpad = (k + 15u) & ~15u;
-        if (m.present[j][tid]) sec[m.rank[j][tid]] = static_cast<uint8_t>(tid);
-        for (uint32_t i = k + tid; i < dpad; i += blockDim.x) sec[i] = 0;
-        if (b > 0) {
-          const uint4 r0 = reinterpret_cast<const uint4*>(plane)[2 * tid];
-          const uint4 r1 = reinterpret_cast<const uint4*>(plane)[2 * tid + 1];
-          const uint32_t rw[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
-          uint32_t* words = reinterpret_cast<uint32_t*>(sec + dpad) + tid * b;
-          uint64_t acc = 0;
-          uint32_t nb = 0, e = 0;
-#pragma unroll
-          for (int q = 0; q < 32; ++q) {
-            acc |= static_cast<uint64_t>((rw[q >> 2] >> (8 * (q & 3))) & 255u) << nb;
-            nb += b;
-            if (nb >= 32) {
-              words[e++] = static_cast<uint32_t>(acc);
-              acc >>= 32;
-              nb -= 32;
-            }
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
-}
-
-// Image checksum of a compressed image: the header and tables (word index
-// from 0) plus the encoded payload (word index from the payload offset).
-__global__ void __launch_bounds__(256) k_bpd_checksum(BpdChecksumArgs a) {
-  const uint64_t n = *a.n_dirty;
-  const uint64_t A = a.n_allocs;
-  const uint64_t poff = (kHeaderBytes + 16 * A + 24 * n + 15) & ~15ull;
-  const uint64_t meta_vecs = poff / 16, enc_vecs = *a.total / 16;
-  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
-  uint64_t h = 0;
-  for (uint64_t v = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < meta_vecs + enc_vecs;
-       v += stride) {
-    if (v < meta_vecs)
-      h += hash_vec(ld_stream(a.meta + 16 * v), (2 * v) * kPhi);
-    else
-      h += hash_vec(ld_stream(a.enc + 16 * (v - meta_vecs)), (2 * v) * kPhi);
-  }
-  h = dev::warp_sum(h);
-  if ((threadIdx.x & 31) == 0 && h != 0) atomicAdd(a.trailer, static_cast<unsigned long long>(h));
-}
-
-// Decodes the `len` encoded bytes at `enc` (device or mapped host memory)
-// into `page` (shared, 64 KiB) using `plane` (shared, 8 KiB) and `dict`
-// (shared, 8 x 128).  Returns false, CTA-uniformly, for a code this build
-// cannot have written (the slot is then skipped).
-__device__ bool bpd_decode(const uint8_t* enc, uint32_t len, uint8_t* page, uint8_t* plane,
-                           uint8_t (*dict)[128], BpdSmem& m) {
-  const int tid = threadIdx.x;
-  if (len == kPage) {
-    for (uint32_t v = tid; v < kPageVecs; v += blockDim.x)
-      reinterpret_cast<uint4*>(page)[v] = reinterpret_cast<const uint4*>(enc)[v];
-    __syncthreads();
-    return true;
-  }
-  if (tid == 0) {
-    int ok = len >= 16 && len % 16 == 0 && len < kPage;
-    uint32_t pos = 16;
-    for (int j = 0; ok && j < 8; ++j) {
-      const uint32_t b = enc[j], km1 = enc[8 + j];
-      m.b[j] = b;
-      m.k[j] = km1 + 1;
-      m.sec[j] = pos;
-      if (b == 8) {
-        ok = km1 == 255;
-        pos += kPlaneBytes;
-      } else {
-        ok = b < 8 && km1 < 128 && ceil_log2(km1 + 1) == b;
-        pos += ((km1 + 1 + 15) & ~15u) + 1024u * b;
-      }
-    }
-    m.skip = !(ok && pos == len);
-  }
-  __syncthreads();
-  if (m.skip) return false;
-  for (int j = 0; j < 8; ++j) {
-    const uint32_t b = m.b[j];
-    const uint8_t* sec = enc + m.sec[j];
-    if (b == 8) {
-      for (uint32_t v = tid; v < kPlaneBytes / 16; v += blockDim.x)
-        reinterpret_cast<uint4*>(plane)[v] = reinterpret_cast<const uint4*>(sec)[v];
-    } else {
-      const uint32_t k = m.k[j], dpad = (k + 15u) & ~15u;
-      if (tid < 128) dict[j][tid] = tid < k ? sec[tid] : 0;
-      __syncthreads();
-      uint32_t outw[8];
-      if (b == 0) {
-        const uint32_t x = dict[j][0] * 0x01010101u;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) outw[q] = x;
-      } else {
-        const uint32_t* words = reinterpret_cast<const uint32_t*>(sec + dpad) + tid * b;
-        uint64_t acc = 0;
-        uint32_t nb = 0, e = 0;
-        const uint32_t mask = (1u << b) - 1u;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) outw[q] = 0;
-#pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          if (nb < b) {
-            acc |= static_cast<uint64_t>(words[e++]) << nb;
-            nb += 32;
-          }
-          const uint32_t r = static_cast<uint32_t>(acc) & mask;
-          acc >>= b;
-          nb -= b;
-          outw[q >> 2] |= static_cast<uint32_t>(dict[j][r & 127u]) << (8 * (q & 3));
-        }
-      }
-      reinterpret_cast<uint4*>(plane)[2 * tid] = make_uint4(outw[0], outw[1], outw[2], outw[3]);
-      reinterpret_cast<uint4*>(plane)[2 * tid + 1] = make_uint4(outw[4], outw[5], outw[6], outw[7]);
-    }
-    __syncthreads();
-    for (uint32_t i = tid; i < kPlaneBytes; i += blockDim.x) page[8 * i + j] = plane[i];
-    __syncthreads();
-  }
-  return true;
-}
-
-// Valid bytes of the decoded page to the allocation (CTA-wide).
-__device__ __forceinline__ void bpd_store(const uint8_t* page, uint8_t* dst, uint32_t valid) {
-  const uint32_t nvec = valid >> 4;
-  for (uint32_t v = threadIdx.x; v < nvec; v += blockDim.x)
-    reinterpret_cast<uint4*>(dst)[v] = reinterpret_cast<const uint4*>(page)[v];
-  const uint32_t rem = valid & 15u;
-  if (rem != 0 && threadIdx.x == 0)
-    for (uint32_t b = 0; b < rem; ++b) dst[16ull * nvec + b] = page[16ull * nvec + b];
-}
-
-__global__ void __launch_bounds__(kBpdThreads) k_bpd_restore(BpdRestoreArgs a) {
-  extern __shared__ __align__(16) uint8_t dyn[];
-  uint8_t* page = dyn;
-  uint8_t* plane = dyn + kPage;
-  __shared__ uint8_t dict[8][128];
-  __shared__ BpdSmem m;
-  for (uint64_t s = blockIdx.x; s < a.n_slots; s += gridDim.x) {
-    const uint32_t k = a.ptab[2 * s];
-    const uint64_t p = a.ptab[2 * s + 1];
-    if (k >= a.n_allocs || p >= a.allocs[k].n_pages) continue;  // rejected on the host already
-    const uint64_t lo = a.offs[s], hi = s + 1 < a.n_slots ? a.offs[s + 1] : a.enc_end;
-    if (!bpd_decode(a.enc + (lo - a.offs[0]), static_cast<uint32_t>(hi - lo), page, plane, dict, m)) {
-      if (threadIdx.x == 0 && a.error) atomicExch(a.error, 1u);
-      __syncthreads();
-      continue;
-    }
-    bpd_store(page, a.allocs[k].base + p * kPage, dev::valid_bytes(a.allocs[k].bytes, p));
-    if (threadIdx.x == 0) a.h_table[a.allocs[k].first_page + p] = a.hashes[s];
-    __syncthreads();
-  }
-}
-
-// ----------------------------------------------- merged (last-writer) restore ---
-//
-// A chain base..end restored page by page from the newest image that holds
-// each page, so every page crosses the link once however long the chain.
-// The images stay in pinned host memory; both kernels read them there.
-
-constexpr uint64_t kSlotMask = (1ull << 40) - 1;
-
-__global__ void __launch_bounds__(256) k_chain_owner(OwnerArgs a) {
-  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
-  for (uint64_t j = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-       j < a.total_slots; j += stride) {
-    uint32_t lo = 0, hi = a.n_images;  // image holding global slot j, in [lo, hi)
-    while (hi - lo > 1) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (a.images[mid].slot0 <= j)
-        lo = mid;
-      else
-        hi = mid;
-    }
-    const uint64_t s = j - a.images[lo].slot0;
-    const uint2 e = *reinterpret_cast<const uint2*>(a.images[lo].ptab + 8 * s);
-    if (e.x >= a.n_allocs || e.y >= a.allocs[e.x].n_pages) continue;  // rejected on the host already
-    const uint64_t g = a.allocs[e.x].first_page + e.y;
-    // later images carry larger tags, so the maximum is the last writer
-    atomicMax(reinterpret_cast<unsigned long long*>(a.owner + g),
-              static_cast<unsigned long long>((static_cast<uint64_t>(lo) + 1) << 40 | s));
-  }
-}
-
-// An image's payload starts 64 + 16A + 16n bytes into it: 16-byte aligned,
-// rarely 128-byte aligned.  Read across the link, a warp's 512 contiguous
-// bytes would then span five 128-byte lines instead of four; so each CTA
-// reads whole aligned lines of a 16 KiB stretch into shared memory and
-// writes the page from there, shifted by the misalignment (a whole number
-// of 16-byte vectors).
-constexpr uint32_t kMergeChunkVecs = 1024;  // 16 KiB per step
-
-// One page from an image payload slot in host memory to the allocation,
-// whole 128-byte lines at a time through `buf` (kMergeChunkVecs + 8 vectors).
-__device__ __forceinline__ void merged_copy_page(const uint8_t* src, uint8_t* dst, uint32_t valid,
-                                                 uint4* buf) {
-  const uint32_t nvec = valid >> 4;
-  const uintptr_t sa = reinterpret_cast<uintptr_t>(src);
-  const uint4* line = reinterpret_cast<const uint4*>(sa & ~uintptr_t(127));
-  const uint32_t m = static_cast<uint32_t>(sa & 127u) >> 4;
-  for (uint32_t c = 0; c < nvec; c += kMergeChunkVecs) {
-    const uint32_t cnt = min(kMergeChunkVecs, nvec - c);
-    // vectors line[c .. c+cnt+m) end at the last whole vector of the page
-    for (uint32_t i = threadIdx.x; i < cnt + m; i += blockDim.x) buf[i] = line[c + i];
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x)
-      reinterpret_cast<uint4*>(dst)[c + i] = buf[i + m];
-    __syncthreads();
-  }
-  const uint32_t rem = valid & 15u;
-  if (rem != 0 && threadIdx.x == 0)
-    for (uint32_t b = 0; b < rem; ++b) dst[16ull * nvec + b] = src[16ull * nvec + b];
-}
-
-// Installs the chain's hash of page g and decides, CTA-uniformly, whether
-// the page is copied (delta mode leaves a page whose current contents
-// already hash to the chain's value).
-__device__ __forceinline__ bool merged_take_page(const MergedRestoreArgs& a, const ChainImage& im,
-                                                 uint64_t g, uint64_t s, int* flag) {
-  if (threadIdx.x == 0) {
-    const uint64_t hc = reinterpret_cast<const uint64_t*>(im.hashes)[s];
-    a.h_table[g] = hc;
-    const bool skip = a.current != nullptr && a.current[g] == hc;
-    if (!skip && a.copied != nullptr) atomicAdd(a.copied, 1ull);
-    *flag = skip;
-  }
-  __syncthreads();
-  const bool skip = *flag;
-  __syncthreads();  // every thread has read the flag before it is rewritten
-  return !skip;
-}
-
-__global__ void __launch_bounds__(256) k_restore_merged(MergedRestoreArgs a) {
-  __shared__ uint4 buf[kMergeChunkVecs + 8];
-  __shared__ int skip_sh;
-  for (uint64_t g = blockIdx.x; g < a.n_pages; g += gridDim.x) {
-    const uint64_t o = a.owner[g];
-    if (o == 0) continue;  // no image of the chain holds this page
-    const ChainImage& im = a.images[(o >> 40) - 1];
-    const uint64_t s = o & kSlotMask;
-    if (!merged_take_page(a, im, g, s, &skip_sh)) continue;
-    const uint32_t k = dev::find_alloc(a.first_page, a.n_allocs, g);
-    const uint64_t p = g - a.allocs[k].first_page;
-    merged_copy_page(im.payload + s * kPage, a.allocs[k].base + p * kPage,
-                     dev::valid_bytes(a.allocs[k].bytes, p), buf);
-  }
-}
-
-// The merged restore of a chain holding compressed images: a compressed
-// slot is decoded from host memory in shared memory, then stored.
-__global__ void __launch_bounds__(kBpdThreads) k_restore_merged_bpd(MergedRestoreArgs a) {
-  extern __shared__ __align__(16) uint8_t dyn[];
-  uint8_t* page = dyn;
-  uint8_t* plane = dyn + kPage;
-  __shared__ uint8_t dict[8][128];
-  __shared__ BpdSmem m;
-  __shared__ int skip_sh;
-  for (uint64_t g = blockIdx.x; g < a.n_pages; g += gridDim.x) {
-    const uint64_t o = a.owner[g];
-    if (o == 0) continue;
-    const ChainImage& im = a.images[(o >> 40) - 1];
-    const uint64_t s = o & kSlotMask;
-    if (!merged_take_page(a, im, g, s, &skip_sh)) continue;
-    const uint32_t k = dev::find_alloc(a.first_page, a.n_allocs, g);
-    const uint64_t p = g - a.allocs[k].first_page;
-    uint8_t* dst = a.allocs[k].base + p * kPage;
-    const uint32_t valid = dev::valid_bytes(a.allocs[k].bytes, p);
-    if (im.offs == nullptr) {
-      merged_copy_page(im.payload + s * kPage, dst, valid, reinterpret_cast<uint4*>(page));
-      continue;
-    }
-    const uint64_t lo = im.offs[s], hi = s + 1 < im.n_slots ? im.offs[s + 1] : im.payload_bytes;
-    if (!bpd_decode(im.payload + lo, static_cast<uint32_t>(hi - lo), page, plane, dict, m)) {
-      if (threadIdx.x == 0 && a.error) atomicExch(a.error, 1u);
-      __syncthreads();
-      continue;
-    }
-    bpd_store(page, dst, valid);
-    __syncthreads();
-  }
-}
-
 // ------------------------------------------------------------ hash bytes ---
 
 __global__ void __launch_bounds__(256) k_hash_bytes(const uint8_t* p, uint64_t n,
@@ -1198,79 +679,6 @@ __global__ void __launch_bounds__(32 * (CW + 1)) k_hash_dirty_bulk(HashArgs a) {
   }
 }
 
-int g_num_sms = 0;
-
-int num_sms() {
-  if (g_num_sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = 1;
-  }
-  return g_num_sms;
-}
-
-// CTAs of `func` resident per SM at once (cached per device and shape).
-int resident_per_sm(const void* func, int threads, size_t smem) {
-  static std::mutex mu;
-  static std::map<std::tuple<const void*, int, size_t, int>, int> cache;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  const auto key = std::make_tuple(func, threads, smem, dev);
-  std::lock_guard<std::mutex> lk(mu);
-  auto it = cache.find(key);
-  if (it != cache.end()) return it->second;
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, threads, smem) != cudaSuccess) {
-    cudaGetLastError();
-    per_sm = 1;
-  }
-  per_sm = std::max(1, per_sm);
-  cache.emplace(key, per_sm);
-  return per_sm;
-}
-
-template <typename K>
-int resident_ctas(K kernel, int threads) {
-  return resident_per_sm(reinterpret_cast<const void*>(kernel), threads, 0) * num_sms();
-}
-
-// Grid for `units` groups of a kernel with `groups_per_cta` groups per CTA:
-// enough CTAs for every unit, at most what is resident at once.
-template <typename K>
-unsigned grid_for(K kernel, uint64_t units, int groups_per_cta, int threads = 256) {
-  const uint64_t need = (units + groups_per_cta - 1) / groups_per_cta;
-  const uint64_t cap = static_cast<uint64_t>(resident_ctas(kernel, threads));
-  return static_cast<unsigned>(std::max<uint64_t>(1, std::min(need, cap)));
-}
-
-constexpr size_t kBpdDynSmem = kPage + kPlaneBytes;  // the slot + one plane
-
-// Kernels that use more than 48 KiB of dynamic shared memory must say so
-// once per device.
-template <typename K>
-cudaError_t allow_big_smem(K kern) {
-  static std::mutex mu;
-  static std::map<std::pair<const void*, int>, bool> done;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  std::lock_guard<std::mutex> lk(mu);
-  auto key = std::make_pair(reinterpret_cast<const void*>(kern), dev);
-  if (done.count(key)) return cudaSuccess;
-  const cudaError_t e =
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kBpdDynSmem));
-  if (e == cudaSuccess) done[key] = true;
-  return e;
-}
-
-template <typename K>
-unsigned bpd_grid(K kern, uint64_t units) {
-  const uint64_t cap =
-      static_cast<uint64_t>(resident_per_sm(reinterpret_cast<const void*>(kern), kBpdThreads, kBpdDynSmem)) *
-      num_sms();
-  return static_cast<unsigned>(std::max<uint64_t>(1, std::min(units, cap)));
-}
-
 // G == 32: eight one-warp groups in a 256-thread CTA; G > 32: one group
 // per CTA of G threads.
 template <int G, int U, bool V, int MINB = 1>
@@ -1305,6 +713,37 @@ KernelSpec gather_spec_t(uint64_t max_slots) {
 }
 
 }  // namespace
+
+static int g_num_sms = 0;
+
+int num_sms() {
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 1;
+  }
+  return g_num_sms;
+}
+
+int resident_per_sm(const void* func, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<const void*, int, size_t, int>, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const auto key = std::make_tuple(func, threads, smem, dev);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  per_sm = std::max(1, per_sm);
+  cache.emplace(key, per_sm);
+  return per_sm;
+}
 
 // Hash mappings 0-5 are register mappings, 6-8 bulk-copy mappings; gather
 // and restore use the register mappings 0-5 only.
@@ -1411,83 +850,6 @@ cudaError_t launch_gather(const GatherArgs& a, uint64_t max_slots, int mapping, 
   if (e != cudaSuccess) return e;
   GatherArgs copy = a;
   return launch_spec(s, &copy, st);
-}
-
-cudaError_t launch_restore(const RestoreArgs& a, cudaStream_t st) {
-  if (a.n_slots == 0) return cudaSuccess;
-  // one CTA per image slot: restores carry few slots per launch, and a
-  // warp per slot left most of the device idle
-  auto kern = k_restore<256>;
-  const unsigned grid = grid_for(kern, a.n_slots, 1);
-  kern<<<grid, 256, 0, st>>>(a);
-  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_chain_owner(const OwnerArgs& a, cudaStream_t st) {
-  if (a.total_slots == 0 || a.n_images == 0) return cudaSuccess;
-  const uint64_t cap = static_cast<uint64_t>(resident_ctas(k_chain_owner, 256));
-  const unsigned grid =
-      static_cast<unsigned>(std::max<uint64_t>(1, std::min((a.total_slots + 255) / 256, cap)));
-  k_chain_owner<<<grid, 256, 0, st>>>(a);
-  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_restore_merged(const MergedRestoreArgs& a, bool compressed, cudaStream_t st) {
-  if (a.n_pages == 0) return cudaSuccess;
-  if (compressed) {
-    cudaError_t e = allow_big_smem(k_restore_merged_bpd);
-    if (e != cudaSuccess) return e;
-    k_restore_merged_bpd<<<bpd_grid(k_restore_merged_bpd, a.n_pages), kBpdThreads, kBpdDynSmem, st>>>(a);
-    g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-    return cudaGetLastError();
-  }
-  // one CTA per page; any shape that keeps a few MB of reads in flight
-  // saturates the link
-  const unsigned grid = grid_for(k_restore_merged, a.n_pages, 1);
-  k_restore_merged<<<grid, 256, 0, st>>>(a);
-  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_bpd_size(const BpdSizeArgs& a, uint64_t max_slots, cudaStream_t st) {
-  if (max_slots == 0) return cudaSuccess;
-  const unsigned grid = grid_for(k_bpd_size, max_slots, 1, kBpdThreads);
-  k_bpd_size<<<grid, kBpdThreads, 0, st>>>(a);
-  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_bpd_scan(const BpdScanArgs& a, cudaStream_t st) {
-  k_bpd_scan<<<1, 1024, 0, st>>>(a);
-  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_bpd_encode(const BpdEncodeArgs& a, uint64_t max_slots, cudaStream_t st) {
-  if (max_slots == 0) return cudaSuccess;
-  cudaError_t e = allow_big_smem(k_bpd_encode);
-  if (e != cudaSuccess) return e;
-  k_bpd_encode<<<bpd_grid(k_bpd_encode, max_slots), kBpdThreads, kBpdDynSmem, st>>>(a);
-  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_bpd_checksum(const BpdChecksumArgs& a, uint64_t max_bytes, cudaStream_t st) {
-  const unsigned grid = grid_for(k_bpd_checksum, (max_bytes / 16 + 255) / 256 + 1, 1, 256);
-  k_bpd_checksum<<<grid, 256, 0, st>>>(a);
-  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_bpd_restore(const BpdRestoreArgs& a, cudaStream_t st) {
-  if (a.n_slots == 0) return cudaSuccess;
-  cudaError_t e = allow_big_smem(k_bpd_restore);
-  if (e != cudaSuccess) return e;
-  k_bpd_restore<<<bpd_grid(k_bpd_restore, a.n_slots), kBpdThreads, kBpdDynSmem, st>>>(a);
-  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_hash_bytes(const uint8_t* p, uint64_t n, uint64_t first_index, uint64_t* out,
