@@ -670,9 +670,10 @@ def run_e2e(torch, crum, W, s, bufs, wl, steps, sh, stream, step0, dist, dev, wo
     image back (PERSISTED: its bytes crossed device->host).  Two forms, each
     step holding its own uploads and its own image drain:
     - pipelined (the value): step k+1's upload is issued before waiting for
-      image k, so the upload and the previous drain share the full-duplex
-      link, as an application that keeps running while its checkpoint
-      drains would;
+      image k, on a copy stream into one of two landing buffers, so it
+      overlaps step k's capture and shares the full-duplex link with the
+      previous drain, as an application that keeps running while its
+      checkpoint drains would;
     - serial: each step waits for its image before the next upload.
     Images are released once persisted, so the pinned pool is reused."""
     n_pages = wl.n_pages
@@ -682,18 +683,37 @@ def run_e2e(torch, crum, W, s, bufs, wl, steps, sh, stream, step0, dist, dev, wo
     new = torch.randint(0, 256, (k, W.PAGE), dtype=torch.uint8, generator=gen).pin_memory()
     n_full = bufs[0].numel() // W.PAGE
     pages_view = bufs[0][:n_full * W.PAGE].view(n_full, W.PAGE)
-    landing = torch.empty((k, W.PAGE), dtype=torch.uint8, device=dev)
+    # two landing buffers on a copy stream: step k+1's host->device copy may
+    # run while step k's capture and drain do; only the scatter into the
+    # application's memory is ordered after the capture (on the app stream)
+    landing = [torch.empty((k, W.PAGE), dtype=torch.uint8, device=dev) for _ in range(2)]
+    scattered = [None, None]  # app-stream event after the scatter that read landing[j]
+    copy_stream = torch.cuda.Stream(device=dev)
     plan = []
     for step in range(2 * steps + 4):
         p = W.choose_step(wl, step0 + step, n_pages)
         plan.append(torch.as_tensor(p[p < n_full], device=dev))
+    turn = [0]
 
-    def upload(idx):
+    def upload(idx, ev=None):
         # the application's new page contents: one pinned host->device copy
         # of the step's pages, then a device scatter into place
-        m = int(idx.numel())
-        landing[:m].copy_(new[:m], non_blocking=True)
-        pages_view.index_copy_(0, idx, landing[:m])
+        m, j = int(idx.numel()), turn[0]
+        turn[0] ^= 1
+        with torch.cuda.stream(copy_stream):
+            if scattered[j] is not None:
+                copy_stream.wait_event(scattered[j])
+            if ev is not None:
+                ev[0].record(copy_stream)
+            landing[j][:m].copy_(new[:m], non_blocking=True)
+            if ev is not None:
+                ev[1].record(copy_stream)
+            landed = torch.cuda.Event()
+            landed.record(copy_stream)
+        stream.wait_event(landed)
+        pages_view.index_copy_(0, idx, landing[j][:m])
+        scattered[j] = torch.cuda.Event()
+        scattered[j].record(stream)
         return m * W.PAGE
 
     def finish(im, infos):
@@ -719,11 +739,9 @@ def run_e2e(torch, crum, W, s, bufs, wl, steps, sh, stream, step0, dist, dev, wo
         t0 = time.perf_counter()
         prev = None
         for step in range(steps):
-            u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            u0.record(stream)
-            h2d.append(upload(plan[first_step + 2 + step]))
-            u1.record(stream)
-            ev.append((u0, u1))
+            u = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            h2d.append(upload(plan[first_step + 2 + step], u))
+            ev.append(u)
             im = s.checkpoint(sh)
             if pipelined:
                 if prev is not None:
@@ -746,8 +764,9 @@ def run_e2e(torch, crum, W, s, bufs, wl, steps, sh, stream, step0, dist, dev, wo
             "h2d_bytes_per_step": int(statistics.mean(h2d)),
             "d2h_bytes_per_step": int(statistics.mean(i["image_bytes"] for i in infos)),
             "ms_per_step": round(dt * 1e3 / steps, 3),
-            "what": "pinned H2D of the step's new pages + crum_checkpoint + image read back "
-                    "(PERSISTED); step k+1's upload overlaps image k's drain",
+            "what": "pinned H2D of the step's new pages (copy stream, two landing buffers) + device "
+                    "scatter + crum_checkpoint + image read back (PERSISTED); step k+1's upload "
+                    "overlaps image k's capture and drain",
             "submit_to_persisted_ms": round(statistics.mean(i["t_persisted_ms"] for i in infos), 3),
             "upload_ms": round(up_ms, 3),
             "serial": {"value": per(dt_s), "ms_per_step": round(dt_s * 1e3 / steps, 3),
