@@ -147,6 +147,24 @@ typedef struct crum_config {
                                   pages are encoded and drained one staging half
                                   at a time, each chunk's code placed after the
                                   previous chunk's */
+    int managed_in_place;      /* 1: managed allocations whose pages the application
+                                  placed in host memory (preferred location the
+                                  host, or last prefetched there) are read where
+                                  they are, over the host link, instead of being
+                                  migrated to the device by the capture's page
+                                  faults (the oversubscribed case of Section 4.4's
+                                  synthetic benchmark, where the device cannot
+                                  hold them).  At each checkpoint and restore the
+                                  set looks up every managed allocation's
+                                  placement (cudaMemRangeGetAttribute) and keeps
+                                  its device mapped to the host-placed ones
+                                  (cudaMemAdviseSetAccessedBy), withdrawing that
+                                  advice when the range moves back, is
+                                  unregistered or the set is destroyed; advice the
+                                  application set itself is left alone.  While the
+                                  advice stands, the application's own kernels
+                                  also read those pages in place.  0: pages are
+                                  read wherever the driver's policy puts them */
 } crum_config;
 
 typedef enum crum_restore_mode {
@@ -269,6 +287,8 @@ typedef struct crum_image_info {
     double t_compact_ms;     /* device time of scan + gather into staging, from the
                                 moment the staging half was free */
     double t_drain_ms;       /* device time of the device->host copies */
+    uint64_t host_pages;     /* pages of host-placed managed allocations the
+                                capture read in place (cfg.managed_in_place) */
 } crum_image_info;
 
 /* Fill *info.  Fields past `stage` are zero until the image gets there. */

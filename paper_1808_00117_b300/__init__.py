@@ -46,7 +46,8 @@ class Config(ctypes.Structure):
                 ("hash_mapping", ctypes.c_int), ("gather_mapping", ctypes.c_int),
                 ("external_staging", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("max_chain", ctypes.c_int), ("restore_mode", ctypes.c_int),
-                ("max_pending", ctypes.c_int), ("compress", ctypes.c_int)]
+                ("max_pending", ctypes.c_int), ("compress", ctypes.c_int),
+                ("managed_in_place", ctypes.c_int)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -90,7 +91,8 @@ class ImageInfo(ctypes.Structure):
                 ("full", ctypes.c_uint32), ("stage", ctypes.c_int), ("status", ctypes.c_int),
                 ("t_captured_ms", ctypes.c_double), ("t_drained_ms", ctypes.c_double),
                 ("t_persisted_ms", ctypes.c_double), ("t_hash_ms", ctypes.c_double),
-                ("t_compact_ms", ctypes.c_double), ("t_drain_ms", ctypes.c_double)]
+                ("t_compact_ms", ctypes.c_double), ("t_drain_ms", ctypes.c_double),
+                ("host_pages", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -759,6 +759,66 @@ crum_status graph_launch(crum_set* s, int h, crum_image* img, const crum::HashAr
   return CRUM_OK;
 }
 
+// Placement of managed allocations (cfg.managed_in_place).  A range is
+// host-placed when its preferred location is the host, or it has none and
+// was last prefetched to the host; those are the pages a fault would
+// migrate to the device.  The device keeps a mapping to them
+// (cudaMemAdviseSetAccessedBy: no migration, reads cross the link), added
+// by the set only where the application has not set it for this device.
+void withdraw_advice(crum_set* s, Alloc& a) {
+  if (!a.advised) return;
+  cudaMemLocation loc{};
+  loc.type = cudaMemLocationTypeDevice;
+  loc.id = s->device;
+  // the application may have freed the range after the set's last use
+  if (cudaMemAdvise(a.ptr, a.bytes, cudaMemAdviseUnsetAccessedBy, loc) != cudaSuccess) cudaGetLastError();
+  a.advised = false;
+}
+
+bool accessed_by_device(const Alloc& a, int device) {
+  int devs[64];
+  for (int& d : devs) d = cudaInvalidDeviceId;
+  if (cudaMemRangeGetAttribute(devs, sizeof devs, cudaMemRangeAttributeAccessedBy, a.ptr, a.bytes) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  for (int d : devs)
+    if (d == device) return true;
+  return false;
+}
+
+// Looks up each managed allocation's placement and sets or withdraws the
+// set's advice; returns the pages of host-placed allocations.
+crum_status refresh_placement(crum_set* s, uint64_t* host_pages) {
+  *host_pages = 0;
+  if (!s->cfg.managed_in_place) return CRUM_OK;
+  for (Alloc& a : s->allocs) {
+    if (!a.managed) continue;
+    int pref = cudaInvalidDeviceId, last = cudaInvalidDeviceId;
+    if (cudaMemRangeGetAttribute(&pref, sizeof pref, cudaMemRangeAttributePreferredLocation, a.ptr, a.bytes) !=
+            cudaSuccess ||
+        cudaMemRangeGetAttribute(&last, sizeof last, cudaMemRangeAttributeLastPrefetchLocation, a.ptr,
+                                 a.bytes) != cudaSuccess)
+      return fail(CRUM_ECUDA, "placement of allocation %u: %s", a.id, cudaGetErrorString(cudaGetLastError()));
+    const bool host = pref == cudaCpuDeviceId || (pref == cudaInvalidDeviceId && last == cudaCpuDeviceId);
+    if (host) {
+      *host_pages += a.n_pages;
+      if (!a.advised && !accessed_by_device(a, s->device)) {
+        cudaMemLocation loc{};
+        loc.type = cudaMemLocationTypeDevice;
+        loc.id = s->device;
+        if (cudaMemAdvise(a.ptr, a.bytes, cudaMemAdviseSetAccessedBy, loc) != cudaSuccess)
+          return fail(CRUM_ECUDA, "advice for allocation %u: %s", a.id, cudaGetErrorString(cudaGetLastError()));
+        a.advised = true;
+      }
+    } else {
+      withdraw_advice(s, a);
+    }
+  }
+  return CRUM_OK;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------ PinnedPool ---
@@ -945,6 +1005,7 @@ crum_status crum_set_destroy(crum_set* s) {
   cudaStreamSynchronize(s->cap_stream);
   cudaStreamSynchronize(s->drain_stream);
   if (s->bounce != nullptr) s->pool->free(s->bounce, kBounceBytes);
+  for (Alloc& a : s->allocs) withdraw_advice(s, a);
   image_unref(s->last);
   for (crum::CaptureGraph& G : s->graph) {
     if (G.exec) cudaGraphExecDestroy(G.exec);
@@ -994,6 +1055,7 @@ crum_status crum_register(crum_set* s, void* ptr, size_t bytes, uint32_t* alloc_
   // both ends must be device memory of the set's device or managed memory
   // (read by the kernels wherever its pages are), so no kernel is ever
   // handed an address it cannot read
+  bool managed = true;
   for (const uint8_t* q : {static_cast<const uint8_t*>(ptr), static_cast<const uint8_t*>(ptr) + bytes - 1}) {
     cudaPointerAttributes pa{};
     if (cudaPointerGetAttributes(&pa, q) != cudaSuccess) {
@@ -1004,6 +1066,7 @@ crum_status crum_register(crum_set* s, void* ptr, size_t bytes, uint32_t* alloc_
       return fail(CRUM_EINVAL, "range is neither device memory of device %d nor managed memory",
                   s->device);
     }
+    managed = managed && pa.type == cudaMemoryTypeManaged;
   }
   std::lock_guard<std::mutex> lk(s->mu);
   const uintptr_t lo = reinterpret_cast<uintptr_t>(ptr), hi = lo + bytes;
@@ -1012,6 +1075,7 @@ crum_status crum_register(crum_set* s, void* ptr, size_t bytes, uint32_t* alloc_
     if (lo < ahi && alo < hi) return fail(CRUM_EINVAL, "range overlaps registration %u", a.id);
   }
   Alloc a{s->next_id++, static_cast<uint8_t*>(ptr), bytes, pages_of(bytes), s->n_pages};
+  a.managed = managed;
   s->allocs.push_back(a);
   s->n_pages += a.n_pages;
   s->table_dirty = s->reg_changed = true;
@@ -1026,6 +1090,10 @@ crum_status crum_unregister(crum_set* s, uint32_t id) {
   std::lock_guard<std::mutex> lk(s->mu);
   auto it = std::find_if(s->allocs.begin(), s->allocs.end(), [&](const Alloc& a) { return a.id == id; });
   if (it == s->allocs.end()) return fail(CRUM_EINVAL, "unknown allocation id %u", id);
+  {
+    DeviceGuard dg(s->device);
+    withdraw_advice(s, *it);
+  }
   s->allocs.erase(it);
   uint64_t first = 0;
   for (Alloc& a : s->allocs) {
@@ -1236,6 +1304,7 @@ crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, cr
       cudaEventRecord(img->ev_submit, s->cap_stream) != cudaSuccess)
     return bail(fail(CRUM_ECUDA, "cannot order capture after the application stream: %s",
                      cudaGetErrorString(cudaGetLastError())));
+  if ((st = refresh_placement(s, &img->host_pages)) != CRUM_OK) return bail(st);
   if ((st = upload_table(s)) != CRUM_OK) return bail(st);
   const uint64_t words = (s->n_pages + 31) / 32;
 
@@ -1438,6 +1507,7 @@ crum_status crum_image_info_get(const crum_image* cimg, crum_image_info* info) {
     info->t_compact_ms = img->t_compact_ms;
     info->t_drain_ms = img->t_drain_ms;
   }
+  info->host_pages = img->host_pages;
   if (img->stage >= CRUM_WAIT_PERSISTED) info->t_persisted_ms = img->t_persisted_ms;
   return CRUM_OK;
 }
@@ -1679,6 +1749,12 @@ crum_status crum_restore(crum_set* s, const crum_image* chain_end, crum_stream_t
                     (unsigned long long)img->table[a].second, (unsigned long long)s->allocs[a].bytes);
   }
   const uint64_t A = s->allocs.size();
+  {
+    // restored pages of host-placed managed allocations are written in place
+    uint64_t host_pages = 0;
+    const crum_status pst = refresh_placement(s, &host_pages);
+    if (pst != CRUM_OK) return pst;
+  }
   // auto: merged when the incrementals would carry more than 8 % of the
   // base's pages a second time (kernel reads of host memory run ~7 % below
   // DMA); delta is merged restricted to pages whose contents differ

@@ -63,6 +63,8 @@ struct Alloc {
   uint64_t bytes;
   uint64_t n_pages;
   uint64_t first_page;
+  bool managed = false;   // managed (unified) memory
+  bool advised = false;   // the set added cudaMemAdviseSetAccessedBy for its device
 };
 
 struct Half {
@@ -152,6 +154,7 @@ struct crum_image {
   bool compressed = false;    // version 2 image
   uint64_t payload_off = 0;   // compressed: where the encoded payload starts
   uint64_t payload_bytes = 0; // compressed: encoded payload bytes
+  uint64_t host_pages = 0;    // pages read in place from host-placed managed memory
   std::string sink_path;
   bool do_fsync = false;
 };

@@ -278,6 +278,29 @@ def managed_prefetch(ptr: int, nbytes: int, where: str, device: int = 0) -> None
         raise RuntimeError("cudaMemPrefetchAsync failed")
 
 
+def managed_advise(ptr: int, nbytes: int, advice: str, device: int = 0) -> None:
+    """cudaMemAdvise on a managed range: "preferred_host" (preferred location
+    the host) or "accessed_by" (the device keeps a mapping), as an
+    application sets it."""
+    rt = _rt()
+    rt.cudaMemAdvise.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, _CudaMemLocation]
+    code, loc = {"preferred_host": (3, _CudaMemLocation(2, 0)),
+                 "accessed_by": (5, _CudaMemLocation(1, device))}[advice]
+    if rt.cudaMemAdvise(ptr, nbytes, code, loc) != 0:
+        raise RuntimeError("cudaMemAdvise failed")
+
+
+def managed_accessed_by(ptr: int, nbytes: int) -> list:
+    """Devices holding cudaMemAdviseSetAccessedBy for the whole range."""
+    rt = _rt()
+    rt.cudaMemRangeGetAttribute.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
+                                            ctypes.c_void_p, ctypes.c_size_t]
+    devs = (ctypes.c_int * 64)(*([-2] * 64))
+    if rt.cudaMemRangeGetAttribute(devs, ctypes.sizeof(devs), 3, ptr, nbytes) != 0:
+        raise RuntimeError("cudaMemRangeGetAttribute failed")
+    return [d for d in devs if d >= 0]
+
+
 def managed_empty(nbytes: int, device: int = 0, where: str = "device"):
     """uint8 CUDA tensor over a new managed allocation whose pages were
     prefetched to `where` ("device" or "host")."""

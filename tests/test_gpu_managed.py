@@ -1,8 +1,9 @@
 """Managed (unified) memory, the paper's subject: allocations made with
 cudaMallocManaged are registered like device memory and must give the same
 bit-exact images and restores, whether their pages sit on the device or on
-the host when the checkpoint runs.  Registration rejects memory the kernels
-cannot read."""
+the host when the checkpoint runs; with managed_in_place, host-placed pages
+are read where they are and stay there.  Registration rejects memory the
+kernels cannot read."""
 from __future__ import annotations
 
 import ctypes
@@ -117,4 +118,91 @@ def test_registration_rejects_memory_kernels_cannot_read():
             s.register(ptr, n)
         assert e.value.status == crum.EINVAL
     s.register(dev.data_ptr(), 4 * P)
+    s.destroy()
+
+
+def _read_gbs(b):
+    """Rate of one device page-hash pass over b (best of three), GB/s."""
+    t = torch()
+    out = t.empty(W.pages_of(b.numel()), dtype=t.int64, device="cuda")
+    best = 1e30
+    for _ in range(3):
+        e0, e1 = t.cuda.Event(enable_timing=True), t.cuda.Event(enable_timing=True)
+        e0.record()
+        crum.hash_pages(b.data_ptr(), b.numel(), out.data_ptr(), stream_handle())
+        e1.record()
+        t.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return b.numel() / best / 1e6
+
+
+def test_host_placed_managed_pages_are_read_in_place():
+    """Section 4.4's oversubscribed case in small: one allocation on the
+    device, one the application prefetched to the host, one whose preferred
+    location is the host.  With managed_in_place the images and restores are
+    bit-exact and the host-placed pages are still in host memory afterwards
+    (a device pass over them runs at the link's rate, not HBM's); the set's
+    advice is withdrawn when it is destroyed, the application's own is kept."""
+    sizes = [512 * P + 40, 128 * P * 16, 8 * P * 16 + 8]
+    bufs = _managed(sizes, seed=75)
+    dev_buf, host_buf, pref_buf = bufs
+    W.managed_advise(pref_buf.data_ptr(), pref_buf.numel(), "preferred_host")
+    mine = W.managed_empty(4 * P)
+    W.managed_advise(mine.data_ptr(), mine.numel(), "accessed_by")
+
+    def place():
+        # host copies go through the copy engine; put the pages back where the
+        # application keeps them before each checkpoint
+        for b in (host_buf, pref_buf, mine):
+            W.managed_prefetch(b.data_ptr(), b.numel(), "host")
+
+    host_pages = W.pages_of(sizes[1]) + W.pages_of(sizes[2])
+    o = oracle.OracleSet(sizes)
+    s = make_set(bufs, managed_in_place=1)
+    probe = make_set([mine], managed_in_place=1)
+    chain, states = [], []
+    for step in range(3):
+        if step:
+            _mutate(bufs, 0.3, seed=750 + step)
+        states.append(host_copies(bufs))
+        place()
+        img, got = _ckpt(s)
+        assert img.info()["host_pages"] == host_pages
+        # 128 MiB: over the link ~50 GB/s; from HBM (had it migrated) > 1 TB/s
+        assert _read_gbs(host_buf) < 200, "host-placed pages migrated"
+        assert _read_gbs(dev_buf) > 400
+        exp, *_ = o.checkpoint(states[-1])
+        assert first_diff(got, exp) is None, f"step {step}"
+        chain.append(img)
+    assert 0 in W.managed_accessed_by(host_buf.data_ptr(), host_buf.numel())
+    assert 0 not in W.managed_accessed_by(dev_buf.data_ptr(), dev_buf.numel())
+    for mode in (crum.RESTORE_REPLAY, crum.RESTORE_MERGED, crum.RESTORE_DELTA):
+        r = make_set(bufs, restore_mode=mode, managed_in_place=1)
+        for i, b in enumerate(bufs):
+            W.fill_(b, 7500 + i, "u32")
+        place()
+        r.restore(chain[-1], stream_handle())
+        torch().cuda.synchronize()
+        assert _read_gbs(host_buf) < 200, f"restore migrated host-placed pages ({mode})"
+        assert all(np.array_equal(g, w) for g, w in zip(host_copies(bufs), states[-1])), mode
+        r.destroy()
+    for c in chain:
+        c.release()
+    probe.checkpoint(stream_handle()).wait()
+    s.destroy()
+    probe.destroy()
+    assert 0 not in W.managed_accessed_by(host_buf.data_ptr(), host_buf.numel())
+    assert 0 not in W.managed_accessed_by(pref_buf.data_ptr(), pref_buf.numel())
+    assert 0 in W.managed_accessed_by(mine.data_ptr(), mine.numel())
+
+
+def test_managed_placement_left_alone_by_default():
+    b = _managed([16 * P], seed=77)[0]
+    W.managed_prefetch(b.data_ptr(), b.numel(), "host")
+    s = make_set([b])
+    img, got = _ckpt(s)
+    assert img.info()["host_pages"] == 0
+    assert 0 not in W.managed_accessed_by(b.data_ptr(), b.numel())
+    exp, *_ = oracle.OracleSet([16 * P]).checkpoint(host_copies([b]))
+    assert first_diff(got, exp) is None
     s.destroy()
