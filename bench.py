@@ -375,6 +375,213 @@ def link_d2h_peak(torch, nbytes=2 << 30):
     return gbs
 
 
+def link_h2d_peak(torch, nbytes=2 << 30):
+    """Pinned host->device copy bandwidth, measured with CUDA events."""
+    dev = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    for _ in range(2):
+        dev.copy_(host, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        dev.copy_(host, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    gbs = 3 * nbytes / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    del dev, host
+    return gbs
+
+
+def run_oversub(args):
+    """Section 4.4's synthetic benchmark: two vectors of 2^32 fp32 (32 GiB) in
+    managed memory on a GPU that holds half of them.  A device-memory ballast
+    leaves the application 16 GiB of HBM (plus the library's working set, 2
+    GiB of scratch), so the footprint really oversubscribes the device:
+    vector a sits on the device, vector b in host memory.  Each step
+    rewrites 2 % of the pages of both (a seeded scatter) and checkpoints
+    (null sink).  Two forms of the same steps:
+    - in place (managed_in_place=1, the value): b's pages are hashed and
+      gathered where they are, over the link, and stay there;
+    - the driver's default, run first: a set without managed_in_place takes
+      one full and two incremental checkpoints, and the capture's reads
+      fault b's pages in wherever the driver's policy moves them (the
+      paper's data-migration cost)."""
+    import torch
+    import paper_1808_00117_b300 as crum
+    from paper_1808_00117_b300 import workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    crum.load()
+    dev = torch.device("cuda", local)
+    wl = W.workload("oversub")
+    S, n_pages = wl.total_bytes, wl.n_pages
+    steps, warmup = args.steps, max(args.warmup, 3)
+    link_d2h, link_h2d = link_d2h_peak(torch), link_h2d_peak(torch)
+    # the managed ranges start in host memory: the driver keeps device memory
+    # it once gave to managed pages, so the ballast must come before any of
+    # them reaches the device
+    a_buf, b_buf = (W.managed_empty(n, local, where="host") for n in wl.sizes)
+    pages_a = W.pages_of(wl.sizes[0])
+    k = int(round(wl.dirty_frac * n_pages))
+    staging = 2 * (int(1.5 * k) + 1) * W.PAGE
+    scatter = {}
+    for t in range(1, warmup + steps + 8):
+        chosen = W.choose_step(wl, t, n_pages)
+        gen = np.random.default_rng(wl.seed * 31 + t)
+        masks = torch.as_tensor(gen.integers(1, 2**62, size=chosen.size, dtype=np.int64) | 1, device=dev)
+        in_a = chosen < pages_a
+        scatter[t] = [(buf.view(torch.int64), torch.as_tensor(pages * (W.PAGE // 8), device=dev), masks[sel])
+                      for buf, pages, sel in ((a_buf, chosen[in_a], torch.as_tensor(in_a, device=dev)),
+                                              (b_buf, chosen[~in_a] - pages_a,
+                                               torch.as_tensor(~in_a, device=dev)))]
+
+    def app_update(t):
+        for w64, idx, m in scatter[t]:
+            w64[idx] = w64[idx] ^ m
+
+    sets = {}
+    for form, flag in (("in_place", 1), ("default", 0)):
+        st = crum.CheckpointSet(device=local, staging_bytes=staging, sink=crum.SINK_NULL,
+                                managed_in_place=flag)
+        for b in (a_buf, b_buf):
+            st.register(b.data_ptr(), b.numel())
+        sets[form] = st
+    probe_out = torch.empty(W.pages_of(1 << 30), dtype=torch.int64, device=dev)
+    torch.cuda.synchronize()
+    free, _ = torch.cuda.mem_get_info()
+    hbm_left = wl.meta["device_holds_bytes"] + (2 << 30)
+    ballast = torch.empty(max(0, free - hbm_left), dtype=torch.uint8, device=dev)
+    ballast_bytes = ballast.numel()
+    for i, b in enumerate((a_buf, b_buf)):
+        W.fill_(b, wl.seed * 7919 + i + 1000 * rank, wl.kind)
+    W.managed_prefetch(b_buf.data_ptr(), b_buf.numel(), "host", local)
+    W.managed_prefetch(a_buf.data_ptr(), a_buf.numel(), "device", local)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+
+    def b_read_gbs():
+        # a device pass over b's first GiB: HBM rate if its pages moved in,
+        # the link's if they are still in host memory
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        crum.hash_pages(b_buf.data_ptr(), 1 << 30, probe_out.data_ptr(), sh)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return round((1 << 30) / (e0.elapsed_time(e1) * 1e-3) / 1e9, 1)
+
+    # the driver's default placement policy first, before any advice was
+    # ever given for these ranges: full + 2 incremental checkpoints
+    s0 = sets["default"]
+    d_infos = []
+    for j, flags in enumerate((crum.FULL, crum.INCR, crum.INCR)):
+        if j:
+            app_update(warmup + steps + 2 + j)
+        im = s0.checkpoint(sh, flags)
+        im.wait()
+        d_infos.append(im.info())
+        im.release()
+    b_after_default = b_read_gbs()
+    s0.destroy()
+    # back to the application's placement for the in-place form
+    W.managed_prefetch(b_buf.data_ptr(), b_buf.numel(), "host", local)
+    W.managed_prefetch(a_buf.data_ptr(), a_buf.numel(), "device", local)
+    torch.cuda.synchronize()
+    # in place
+    s = sets["in_place"]
+    full = s.checkpoint(sh, crum.FULL)
+    full.wait()
+    full_info = full.info()
+    full.release()
+    for t in range(1, warmup + 1):
+        app_update(t)
+        s.checkpoint(sh).wait()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(dist)
+    torch.cuda.synchronize()
+    launches0 = crum.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.mark("t0")
+    e0.record(stream)
+    timed = []
+    for t in range(warmup + 1, warmup + steps + 1):
+        app_update(t)
+        timed.append(s.checkpoint(sh))
+    for img in timed:
+        img.wait(crum.WAIT_DRAINED)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks.mark("t1")
+    barrier(dist)
+    launches = crum.kernel_launches() - launches0
+    clk = clocks.stop()
+    for img in timed:
+        img.wait()
+    infos = [img.info() for img in timed]
+    for img in timed:
+        img.release()
+    b_after_in_place = b_read_gbs()
+    s.destroy()
+    total_ms = max_over_ranks(dist, e0.elapsed_time(e1), dev)
+    cap_ms = [i["t_hash_ms"] + i["t_compact_ms"] for i in infos]
+    hash_ms = [i["t_hash_ms"] for i in infos]
+    mean_cap = max_over_ranks(dist, statistics.mean(cap_ms), dev)
+    mean_hash = max_over_ranks(dist, statistics.mean(hash_ms), dev)
+    host_bytes = wl.sizes[1]
+    achieved = host_bytes / (mean_hash * 1e-3) / 1e9
+    drain_gbs = statistics.mean(i["image_bytes"] / (i["t_drain_ms"] * 1e-3) / 1e9 for i in infos)
+    assert all(i["host_pages"] == W.pages_of(wl.sizes[1]) for i in infos)
+
+    del ballast
+    line = {
+        "metric": METRIC, "value": round(world * S / (mean_cap * 1e-3) / 1e9, 2), "unit": UNIT,
+        "n_gpus": world, "steps": steps, "warmup": warmup,
+        "ms_per_step": round(total_ms / steps, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": wl.name, "footprint_bytes": S, "kind": wl.kind,
+                   "vectors": "2 x 2^32 fp32 in managed memory",
+                   "placement": "a on the device, b in host memory; a device-memory ballast, "
+                                "allocated before any managed page reached the device, leaves "
+                                "the managed ranges 18 GiB of HBM (a's 16 GiB + 2 GiB)",
+                   "ballast_bytes": int(ballast_bytes),
+                   "dirty_pages_per_step": int(statistics.mean(i["n_dirty"] for i in infos)),
+                   "sink": "null", "staging_bytes": staging, "managed_in_place": 1},
+        "roofline": {"kernel": "k_hash_dirty", "bound": "host link",
+                     "what": "b's 16 GiB read in place over the link (a's 16 GiB from HBM beside it)",
+                     "achieved": round(achieved, 1), "peak": round(link_h2d, 2), "unit": "GB/s",
+                     "frac": round(achieved / link_h2d, 4), "traffic": None,
+                     "peak_source": "pinned host->device copy measured in this run"},
+        "capture": {"ms_mean": round(statistics.mean(cap_ms), 3),
+                    "hash_ms_mean": round(statistics.mean(hash_ms), 3)},
+        "drain": {"gbs": round(drain_gbs, 2), "link_measured_gbs": round(link_d2h, 2),
+                  "frac_measured": round(drain_gbs / link_d2h, 4)},
+        "latency_ms": {"captured_p50": pct([i["t_captured_ms"] for i in infos], 50),
+                       "captured_p99": pct([i["t_captured_ms"] for i in infos], 99),
+                       "drained_p50": pct([i["t_drained_ms"] for i in infos], 50),
+                       "drained_p99": pct([i["t_drained_ms"] for i in infos], 99)},
+        "full_checkpoint": {"captured_ms": round(full_info["t_captured_ms"], 1),
+                            "drained_ms": round(full_info["t_drained_ms"], 1),
+                            "hash_ms": round(full_info["t_hash_ms"], 1)},
+        "driver_default": {"what": "a set without managed_in_place, run first (no advice ever given "
+                                   "for these ranges): full + 2 incremental",
+                           "captured_ms": [round(i["t_captured_ms"], 1) for i in d_infos],
+                           "hash_ms": [round(i["t_hash_ms"], 1) for i in d_infos],
+                           "drained_ms": [round(i["t_drained_ms"], 1) for i in d_infos]},
+        "b_read_gbs_after": {"in_place": b_after_in_place, "driver_default": b_after_default,
+                             "link_h2d_gbs": round(link_h2d, 2)},
+        "clocks": clk, "gpu_launches": int(launches),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_ours(args):
     import torch
     import paper_1808_00117_b300 as crum
@@ -1159,6 +1366,8 @@ def main(argv=None):
         return run_serving(args)
     if args.workload in ("stencil", "large"):
         return run_batched(args)
+    if args.workload == "oversub":
+        return run_oversub(args)
     return run_ours(args)
 
 

@@ -90,6 +90,11 @@ def workload(name: str) -> Workload:
     if name == "large":
         sizes = loguniform_sizes(0x5EED + 4, 4096, 64 * KiB, 2 * GiB, 140 * GiB)
         return Workload(name, sizes, "fp32", 0.02, 50, "uniform", 0x5EED + 4)
+    if name == "oversub":
+        # Section 4.4's synthetic benchmark: two vectors of 2^32 fp32 (32 GiB)
+        # in managed memory, twice what its GPU holds
+        return Workload(name, [4 * GiB * 4, 4 * GiB * 4], "fp32", 0.02, 10, "uniform", 0x5EED + 5,
+                        {"device_holds_bytes": 16 * GiB})
     if name == "serving":
         # 32 clients, footprints log-uniform 1 MiB .. 4 GiB (not rescaled);
         # the mean of the per-request U[1 %, 50 %] rewrite as the dirty share
