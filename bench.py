@@ -58,6 +58,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-verify", action="store_true", help="skip the verify-mode measurement")
     ap.add_argument("--compress", action="store_true",
                     help="images in the compressed form (byte-plane dictionary code on the device)")
+    ap.add_argument("--managed-in-place", action="store_true",
+                    help="stencil/large: sets look up managed placement at every checkpoint "
+                         "(managed_in_place=1)")
     ap.add_argument("--kind", choices=["u32", "fp32", "fp64", "bf16"], default=None,
                     help="uint32 workload: element kind of the synthetic data")
     ap.add_argument("--sink", choices=["memory", "file"], default="memory",
@@ -1065,7 +1068,7 @@ def run_batched(args):
     max_img = 64 + 16 * len(wl.sizes) + 16 * n_pages + 8 + min(n_pages, staging // 2 // W.PAGE) * W.PAGE
     s = crum.CheckpointSet(device=local, staging_bytes=staging, sink=crum.SINK_NULL,
                            host_pool_bytes=max_img if stencil else 3 * max_img,
-                           compress=int(args.compress))
+                           compress=int(args.compress), managed_in_place=int(args.managed_in_place))
     for b in bufs:
         s.register(b.data_ptr(), b.numel())
     stream = torch.cuda.current_stream()
@@ -1179,7 +1182,7 @@ def run_batched(args):
         "config": {"workload": wl.name, "footprint_bytes": S, "allocations": len(wl.sizes),
                    "n_pages": n_pages, "dirty_pages_per_step": int(statistics.mean(i["n_dirty"] for i in infos)),
                    "sink": "null", "staging_bytes": staging, "memory": MEMORY_DESC[memory],
-                   "kind": wl.kind,
+                   "kind": wl.kind, "managed_in_place": int(args.managed_in_place),
                    "images": "compressed (byte-plane dictionary code)" if args.compress else "plain",
                    "hash_mapping": tune["hash_mapping"], "gather_mapping": tune["gather_mapping"],
                    "autotune_hash_ms": [round(x, 4) for x in tune["hash_ms"]],

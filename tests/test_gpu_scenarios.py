@@ -1,7 +1,9 @@
 """Seeded random scenarios through the C ABI against the oracle: random
 allocation sizes (tiny, ragged, several pages), staging that holds every
 page or only a few (chunked capture), graph or plain launches, random hash
-and gather mappings, verify sets, compressed images, four data kinds, and
+and gather mappings, verify sets, compressed images (chunked too), four
+data kinds, managed memory whose pages the scenario places on the device or
+the host (read in place or migrated), and
 per step a random rewrite and a random checkpoint flag (incremental, full,
 verify, no payload); now and then the
 chain end is restored onto scribbled memory with the scenario's restore
@@ -64,12 +66,27 @@ def test_random_scenario(seed):
     n_pages = sum(W.pages_of(n) for n in sizes)
     chunked = bool(rng.integers(0, 2))
     verify = (not chunked) and bool(rng.integers(0, 2))
-    compress = (not chunked) and bool(rng.integers(0, 2))
+    compress = bool(rng.integers(0, 2))
+    managed = int(rng.integers(0, 3)) == 0
+    in_place = managed and bool(rng.integers(0, 2))
     cfg = dict(staging_bytes=(2 * int(rng.integers(1, 4)) * P) if chunked else 2 * (n_pages + 1) * P,
                use_graph=int(rng.integers(0, 2)), hash_mapping=int(rng.integers(0, crum.NUM_HASH_MAPPINGS)),
                gather_mapping=int(rng.integers(0, 6)), verify=int(verify),
-               restore_mode=int(rng.integers(0, 4)), compress=int(compress))
-    bufs = device_buffers(sizes, seed=seed + 50, kind=["u32", "fp32", "fp64", "bf16"][seed % 4])
+               restore_mode=int(rng.integers(0, 4)), compress=int(compress),
+               managed_in_place=int(in_place))
+    kind = ["u32", "fp32", "fp64", "bf16"][seed % 4]
+    if managed:
+        bufs = []
+        for i, n in enumerate(sizes):
+            b = W.managed_empty(n)
+            W.fill_(b, (seed + 50) * 7919 + i, kind)
+            bufs.append(b)
+        torch().cuda.synchronize()
+        for b in bufs:
+            if rng.integers(0, 2):
+                W.managed_prefetch(b.data_ptr(), b.numel(), "host")
+    else:
+        bufs = device_buffers(sizes, seed=seed + 50, kind=kind)
     s = make_set(bufs, **cfg)
     o = oracle.OracleSet(sizes, compress=compress)
     chain_ok = False  # every image since the last full one kept its payload
