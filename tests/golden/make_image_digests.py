@@ -17,16 +17,18 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
 P = 65536
 
-# case name -> (allocation sizes, seed, element kind)
+# case name -> (allocation sizes, seed, element kind, compressed form)
 CASES = {
-    "fp32_ragged": ([3 * P + 100, P - 8, 17, 2 * P], 101, "fp32"),
-    "u64_tails": ([4096, 4096 + 8, P + 24, 5 * P], 202, "u64"),
+    "fp32_ragged": ([3 * P + 100, P - 8, 17, 2 * P], 101, "fp32", False),
+    "u64_tails": ([4096, 4096 + 8, P + 24, 5 * P], 202, "u64", False),
+    "fp32_ragged_v2": ([3 * P + 100, P - 8, 17, 2 * P], 101, "fp32", True),
+    "u64_tails_v2": ([4096, 4096 + 8, P + 24, 5 * P], 202, "u64", True),
 }
 
 
 def inputs(case):
     """Seeded host buffers (numpy only) and, per step, the pages to rewrite."""
-    sizes, seed, kind = CASES[case]
+    sizes, seed, kind, _ = CASES[case]
     rng = np.random.default_rng(seed)
     bufs = []
     for n in sizes:
@@ -58,7 +60,7 @@ def digests(case):
     sys.path.insert(0, ROOT)
     import oracle
     sizes, bufs, steps = inputs(case)
-    o = oracle.OracleSet(sizes)
+    o = oracle.OracleSet(sizes, compress=CASES[case][3])
     out = []
     img, *_ = o.checkpoint(bufs)
     out.append(img)

@@ -42,7 +42,7 @@ def test_cuda_path_produces_stored_images(case):
     sizes, host, steps = G.inputs(case)
     dev = [torch.from_numpy(h.copy()).cuda() for h in host]
     torch.cuda.synchronize()
-    s = crum.CheckpointSet()
+    s = crum.CheckpointSet(compress=int(G.CASES[case][3]))
     for d in dev:
         s.register(d.data_ptr(), d.numel())
     sh = torch.cuda.current_stream().cuda_stream
