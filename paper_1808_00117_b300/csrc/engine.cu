@@ -557,7 +557,7 @@ crum_status checkpoint_chunked(crum_set* s, crum_image* img, cudaStream_t app,
     g.s_begin = s0;
     g.s_end = s1;
     if (comp) g.trailer = H0.cn + 1;  // the plain form's checksum is not wanted
-    CK(crum::launch_gather(g, s1 - s0, s->map_gather, false, s->cap_stream));
+    CK(crum::launch_gather(g, s1 - s0, s->map_gather, g.shadow != nullptr, s->cap_stream));
     if (s1 == n) {
       // every dirty page is in staging: the application continues while the
       // last chunk is encoded and the image's tables are finished
@@ -1351,8 +1351,6 @@ crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, cr
   ga.shadow = s->cfg.verify ? s->d_shadow : nullptr;
   const bool gather_shadow = ga.shadow != nullptr;
   const bool fast = s->n_pages <= s->half_slots;
-  if (!fast && gather_shadow)
-    return bail(fail(CRUM_EINVAL, "verify mode needs staging that holds every page"));
   img->compressed = s->cfg.compress != 0;
   if (fast) {
     ga.payload = H.payload;

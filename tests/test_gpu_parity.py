@@ -189,10 +189,12 @@ def test_registration_change_forces_full():
     s.destroy()
 
 
-def test_verify_mode_reports_injected_collision():
-    sizes = [4 * P]
+@pytest.mark.parametrize("staging", [0, 4 * P])
+def test_verify_mode_reports_injected_collision(staging):
+    # staging 4 * P: two slots per half, so the shadow is written chunk by chunk
+    sizes = [4 * P + 24]
     bufs = device_buffers(sizes, seed=11)
-    s = make_set(bufs, verify=1)
+    s = make_set(bufs, verify=1, staging_bytes=staging)
     o = oracle.OracleSet(sizes)
     _, _ = _checkpoint_bytes(s, crum.VERIFY)
     prev = host_copies(bufs)

@@ -65,7 +65,7 @@ def test_random_scenario(seed):
     sizes = _sizes(rng)
     n_pages = sum(W.pages_of(n) for n in sizes)
     chunked = bool(rng.integers(0, 2))
-    verify = (not chunked) and bool(rng.integers(0, 2))
+    verify = bool(rng.integers(0, 2))
     compress = bool(rng.integers(0, 2))
     managed = int(rng.integers(0, 3)) == 0
     in_place = managed and bool(rng.integers(0, 2))
