@@ -116,8 +116,9 @@ typedef struct crum_config {
     int external_staging;      /* 1: allocate no staging; a crum_server lends staging
                                   to the set for each request it admits */
     int use_graph;             /* 1: launch each capture (memsets, hash, scan, gather
-                                  and their events) as one instantiated CUDA graph
-                                  per staging half, rebuilt when registrations or
+                                  and their events; with compress, the encoding
+                                  stage too) as one instantiated CUDA graph per
+                                  staging half, rebuilt when registrations or
                                   mappings change; verify-mode and chunked captures
                                   use plain launches */
     int max_chain;             /* > 0: after this many incremental images the next

@@ -246,34 +246,49 @@ __global__ void __launch_bounds__(256) k_bpd_checksum(BpdChecksumArgs a) {
 
 }  // namespace
 
+KernelSpec bpd_size_spec(uint64_t max_slots) {
+  return KernelSpec{reinterpret_cast<const void*>(k_bpd_size),
+                    grid_for(k_bpd_size, std::max<uint64_t>(max_slots, 1), 1, kBpdThreads), kBpdThreads, 0};
+}
+
+KernelSpec bpd_scan_spec() { return KernelSpec{reinterpret_cast<const void*>(k_bpd_scan), 1, 1024, 0}; }
+
+cudaError_t bpd_encode_spec(uint64_t max_slots, KernelSpec* out) {
+  const cudaError_t e = allow_big_smem(k_bpd_encode);
+  if (e != cudaSuccess) return e;
+  *out = KernelSpec{reinterpret_cast<const void*>(k_bpd_encode),
+                    bpd_grid(k_bpd_encode, std::max<uint64_t>(max_slots, 1)), kBpdThreads, kBpdDynSmem};
+  return cudaSuccess;
+}
+
+KernelSpec bpd_checksum_spec(uint64_t max_bytes) {
+  return KernelSpec{reinterpret_cast<const void*>(k_bpd_checksum),
+                    grid_for(k_bpd_checksum, (max_bytes / 16 + 255) / 256 + 1, 1, 256), 256, 0};
+}
+
 cudaError_t launch_bpd_size(const BpdSizeArgs& a, uint64_t max_slots, cudaStream_t st) {
   if (max_slots == 0) return cudaSuccess;
-  const unsigned grid = grid_for(k_bpd_size, max_slots, 1, kBpdThreads);
-  k_bpd_size<<<grid, kBpdThreads, 0, st>>>(a);
-  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-  return cudaGetLastError();
+  BpdSizeArgs copy = a;
+  return launch_spec(bpd_size_spec(max_slots), &copy, st);
 }
 
 cudaError_t launch_bpd_scan(const BpdScanArgs& a, cudaStream_t st) {
-  k_bpd_scan<<<1, 1024, 0, st>>>(a);
-  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-  return cudaGetLastError();
+  BpdScanArgs copy = a;
+  return launch_spec(bpd_scan_spec(), &copy, st);
 }
 
 cudaError_t launch_bpd_encode(const BpdEncodeArgs& a, uint64_t max_slots, cudaStream_t st) {
   if (max_slots == 0) return cudaSuccess;
-  cudaError_t e = allow_big_smem(k_bpd_encode);
+  KernelSpec sp;
+  const cudaError_t e = bpd_encode_spec(max_slots, &sp);
   if (e != cudaSuccess) return e;
-  k_bpd_encode<<<bpd_grid(k_bpd_encode, max_slots), kBpdThreads, kBpdDynSmem, st>>>(a);
-  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-  return cudaGetLastError();
+  BpdEncodeArgs copy = a;
+  return launch_spec(sp, &copy, st);
 }
 
 cudaError_t launch_bpd_checksum(const BpdChecksumArgs& a, uint64_t max_bytes, cudaStream_t st) {
-  const unsigned grid = grid_for(k_bpd_checksum, (max_bytes / 16 + 255) / 256 + 1, 1, 256);
-  k_bpd_checksum<<<grid, 256, 0, st>>>(a);
-  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-  return cudaGetLastError();
+  BpdChecksumArgs copy = a;
+  return launch_spec(bpd_checksum_spec(max_bytes), &copy, st);
 }
 
 }  // namespace crum

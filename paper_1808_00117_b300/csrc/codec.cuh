@@ -161,4 +161,11 @@ unsigned bpd_grid(K kern, uint64_t units) {
   return static_cast<unsigned>(std::max<uint64_t>(1, std::min(units, cap)));
 }
 
+// Launch shapes of the compression kernels (the launchers in kernels.h use
+// them; the capture graph adds them as nodes).
+KernelSpec bpd_size_spec(uint64_t max_slots);
+KernelSpec bpd_scan_spec();
+cudaError_t bpd_encode_spec(uint64_t max_slots, KernelSpec* out);
+KernelSpec bpd_checksum_spec(uint64_t max_bytes);
+
 }  // namespace crum

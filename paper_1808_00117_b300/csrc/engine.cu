@@ -12,6 +12,7 @@
 #include <functional>
 
 #include "engine.h"
+#include "codec.cuh"
 #include "kernels.h"
 
 using crum::Alloc;
@@ -707,6 +708,46 @@ crum_status graph_build(crum_set* s, int h, crum_image* img, const crum::HashArg
   if (e == cudaSuccess) e = cudaGraphAddKernelNode(&G.gather, g, &prev, 1, &kp);
   after(G.gather);
   if (e == cudaSuccess) e = cudaGraphAddEventRecordNode(&G.captured, g, &prev, 1, G.placeholder[3]);
+  after(G.captured);
+  if (s->cfg.compress) {
+    // the encoding stage behind the capture: its arguments are this half's
+    // buffers, fixed for the graph's life, so the nodes are never updated
+    const uint32_t A = static_cast<uint32_t>(s->allocs.size());
+    crum::BpdSizeArgs za{H.payload, H.scalars, H.enc_len};
+    crum::BpdScanArgs qa{H.enc_len, H.scalars, nullptr, 0, H.ctotal, H.mailbox_dev, H.meta, A};
+    crum::BpdEncodeArgs ea{H.payload, H.scalars, nullptr, 0, H.cpay, H.meta, A};
+    crum::BpdChecksumArgs ka{H.meta, H.cpay, H.scalars, H.ctotal, A,
+                             reinterpret_cast<unsigned long long*>(H.scalars + 1)};
+    void* a_z[] = {&za};
+    void* a_q[] = {&qa};
+    void* a_e[] = {&ea};
+    void* a_k[] = {&ka};
+    crum::KernelSpec es{};
+    if (e == cudaSuccess) e = crum::bpd_encode_spec(s->n_pages, &es);
+    kp = kparams(crum::bpd_size_spec(s->n_pages), a_z);
+    if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n, g, &prev, 1, &kp);
+    after(n);
+    kp = kparams(crum::bpd_scan_spec(), a_q);
+    if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n, g, &prev, 1, &kp);
+    after(n);
+    if (e == cudaSuccess) e = cudaGraphAddEventRecordNode(&n, g, &prev, 1, H.ev_sized);
+    after(n);
+    kp = kparams(es, a_e);
+    if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n, g, &prev, 1, &kp);
+    after(n);
+    cudaMemsetParams zp{};
+    zp.dst = H.scalars + 1;
+    zp.value = 0;
+    zp.elementSize = 4;
+    zp.width = 2;
+    zp.height = 1;
+    if (e == cudaSuccess) e = cudaGraphAddMemsetNode(&n, g, &prev, 1, &zp);
+    after(n);
+    kp = kparams(crum::bpd_checksum_spec(cmeta_bytes(A, s->n_pages) + s->n_pages * kPage), a_k);
+    if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n, g, &prev, 1, &kp);
+    after(n);
+    if (e == cudaSuccess) e = cudaGraphAddEventRecordNode(&n, g, &prev, 1, H.ev_encoded);
+  }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&G.exec, g, 0);
   if (e != cudaSuccess) {
     cudaGraphDestroy(g);
@@ -755,7 +796,7 @@ crum_status graph_launch(crum_set* s, int h, crum_image* img, const crum::HashAr
     if (e == cudaSuccess) e = r;
   }
   if (e != cudaSuccess) return fail(CRUM_ECUDA, "capture graph launch: %s", cudaGetErrorString(e));
-  crum::g_kernel_launches.fetch_add(3, std::memory_order_relaxed);
+  crum::g_kernel_launches.fetch_add(s->cfg.compress ? 7 : 3, std::memory_order_relaxed);
   return CRUM_OK;
 }
 
@@ -1370,7 +1411,7 @@ crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, cr
     return bail(e);
   };
   cudaError_t ce = cudaSuccess;
-  if (fast && s->cfg.use_graph && !verify && !s->cfg.external_staging && !s->cfg.compress) {
+  if (fast && s->cfg.use_graph && !verify && !s->cfg.external_staging) {
     // one graph launch for the whole capture sequence
     st = graph_launch(s, h, img, ha, sa, ga);
     if (st != CRUM_OK) return unwind(st);

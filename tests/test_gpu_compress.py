@@ -57,6 +57,34 @@ def test_compressed_images_equal_the_oracle(kind):
     s.destroy()
 
 
+def test_compressed_capture_as_one_graph():
+    """use_graph: the encoding stage runs as nodes of the capture graph;
+    images stay byte-identical, including after a registration change
+    rebuilds the graph."""
+    bufs = device_buffers(SIZES, seed=93, kind="fp32")
+    s = make_set(bufs, compress=1, use_graph=1)
+    o = oracle.OracleSet(SIZES, compress=True)
+    for step in range(3):
+        if step:
+            mutate(bufs, SIZES, 0.3, seed=930 + step)
+        img, got = _ckpt(s)
+        exp, *_ = o.checkpoint(host_copies(bufs))
+        assert first_diff(got, exp) is None, f"step {step}"
+        img.release()
+    extra = device_buffers([5 * P + 16], seed=94, kind="fp32")
+    s.register(extra[0].data_ptr(), extra[0].numel())
+    sizes = SIZES + [5 * P + 16]
+    o = oracle.OracleSet(sizes, compress=True)
+    for step in range(2):
+        if step:
+            mutate(bufs + extra, sizes, 0.3, seed=940 + step)
+        img, got = _ckpt(s)
+        exp, *_ = o.checkpoint(host_copies(bufs + extra))
+        assert first_diff(got[32:-8], exp[32:-8]) is None, f"after the change, step {step}"
+        img.release()
+    s.destroy()
+
+
 @pytest.mark.parametrize("mode", [crum.RESTORE_REPLAY, crum.RESTORE_MERGED, crum.RESTORE_DELTA])
 def test_compressed_chain_restores(mode):
     bufs = device_buffers(SIZES, seed=83, kind="fp32")

@@ -206,3 +206,24 @@ def test_managed_placement_left_alone_by_default():
     exp, *_ = oracle.OracleSet([16 * P]).checkpoint(host_copies([b]))
     assert first_diff(got, exp) is None
     s.destroy()
+
+
+def test_advice_follows_the_application_placement():
+    """A range prefetched back to the device loses the set's advice at the
+    next checkpoint, and gets it again once it is back in host memory."""
+    sizes = [12 * P + 8]
+    b = _managed(sizes, seed=79)[0]
+    s = make_set([b], managed_in_place=1)
+    o = oracle.OracleSet(sizes)
+    for k, (where, advised) in enumerate((("host", True), ("device", False), ("host", True))):
+        _mutate([b], 0.5, seed=790 + k)
+        state = host_copies([b])
+        W.managed_prefetch(b.data_ptr(), b.numel(), where)
+        img, got = _ckpt(s)
+        assert (0 in W.managed_accessed_by(b.data_ptr(), b.numel())) == advised, where
+        assert img.info()["host_pages"] == (W.pages_of(sizes[0]) if advised else 0)
+        exp, *_ = o.checkpoint(state)
+        assert first_diff(got, exp) is None, where
+        img.release()
+    s.destroy()
+    assert 0 not in W.managed_accessed_by(b.data_ptr(), b.numel())
