@@ -151,12 +151,15 @@ __global__ void __launch_bounds__(1024) k_bpd_scan(BpdScanArgs a) {
   }
 }
 
-// Encodes slot s into out + offset[s] (dynamic shared memory: the 64 KiB
-// slot and one 8 KiB plane).
-__global__ void __launch_bounds__(kBpdThreads) k_bpd_encode(BpdEncodeArgs a) {
-  extern __shared__ __align__(16) uint8_t dyn[];
-  uint8_t* page = dyn;                 // kPage bytes
-  uint8_t* plane = dyn + kPage;        // kPlaneBytes bytes
+// Encodes slot s into out + offset[s].  Thread t owns bytes [256 t, 256 t +
+// 256) of the slot, held in registers as 32 little-endian 64-bit words: byte
+// j of word q is byte 32 t + q of plane j, so each thread packs its own 32
+// bytes of every plane (exactly b words of the plane's rank stream) and,
+// once the alphabets are known, needs no shared memory but the rank tables
+// and no further barrier.  The 16-byte loads are 256 bytes apart across a
+// warp; they go through L1, so the second half of each 32-byte sector is a
+// hit for the next load.
+__global__ void __launch_bounds__(kBpdThreads, 2) k_bpd_encode(BpdEncodeArgs a) {
   __shared__ BpdSmem m;
   const int tid = threadIdx.x;
   const uint64_t n = *a.n;
@@ -166,61 +169,68 @@ __global__ void __launch_bounds__(kBpdThreads) k_bpd_encode(BpdEncodeArgs a) {
   for (uint64_t s = blockIdx.x; s < n; s += gridDim.x) {
     for (uint32_t i = tid; i < 8 * 256 / 4; i += blockDim.x) reinterpret_cast<uint32_t*>(m.present)[i] = 0;
     __syncthreads();
-    const uint8_t* slot = a.payload + s * kPage;
-    for (uint32_t v = tid; v < kPageVecs; v += blockDim.x) {
-      const uint4 x = ld_stream(slot + 16ull * v);
-      reinterpret_cast<uint4*>(page)[v] = x;
-      bpd_mark(x, m);
+    const uint4* src = reinterpret_cast<const uint4*>(a.payload + s * kPage + 256ull * tid);
+    uint64_t w[32];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const uint4 x = __ldg(src + q);
+      w[2 * q] = (static_cast<uint64_t>(x.y) << 32) | x.x;
+      w[2 * q + 1] = (static_cast<uint64_t>(x.w) << 32) | x.z;
     }
+#pragma unroll
+    for (int q = 0; q < 32; ++q)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) m.present[j][(w[q] >> (8 * j)) & 255u] = 1;
     __syncthreads();
     bpd_plan(m);
     uint8_t* out = a.out + (off[s] - a.base);
     if (m.len == kPage) {
-      for (uint32_t v = tid; v < kPageVecs; v += blockDim.x)
-        reinterpret_cast<uint4*>(out)[v] = reinterpret_cast<const uint4*>(page)[v];
-      __syncthreads();
-      continue;
-    }
-    if (tid < 16)
-      out[tid] = tid < 8 ? static_cast<uint8_t>(m.b[tid])
-                         : static_cast<uint8_t>(m.b[tid - 8] == 8 ? 255u : m.k[tid - 8] - 1u);
-    for (int j = 0; j < 8; ++j) {
-      const uint32_t b = m.b[j];
-      // plane j into `plane`: its bytes (stored plane) or their ranks
-      for (uint32_t i = tid; i < kPlaneBytes; i += blockDim.x) {
-        const uint8_t x = page[8 * i + j];
-        plane[i] = b == 8 ? x : m.rank[j][x];
-      }
-      __syncthreads();
-      uint8_t* sec = out + m.sec[j];
-      if (b == 8) {
-        for (uint32_t v = tid; v < kPlaneBytes / 16; v += blockDim.x)
-          reinterpret_cast<uint4*>(sec)[v] = reinterpret_cast<const uint4*>(plane)[v];
-      } else {
+      uint4* dst = reinterpret_cast<uint4*>(out + 256ull * tid);
+#pragma unroll
+      for (int q = 0; q < 16; ++q)
+        dst[q] = make_uint4(static_cast<uint32_t>(w[2 * q]), static_cast<uint32_t>(w[2 * q] >> 32),
+                            static_cast<uint32_t>(w[2 * q + 1]), static_cast<uint32_t>(w[2 * q + 1] >> 32));
+    } else {
+      if (tid < 16)
+        out[tid] = tid < 8 ? static_cast<uint8_t>(m.b[tid])
+                           : static_cast<uint8_t>(m.b[tid - 8] == 8 ? 255u : m.k[tid - 8] - 1u);
+#pragma unroll 1
+      for (int j = 0; j < 8; ++j) {
+        const uint32_t b = m.b[j];
+        uint8_t* sec = out + m.sec[j];
+        if (b == 8) {
+          // the plane as is: this thread's 32 bytes of it
+          uint32_t pw[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) pw[q] = 0;
+#pragma unroll
+          for (int q = 0; q < 32; ++q)
+            pw[q >> 2] |= static_cast<uint32_t>((w[q] >> (8 * j)) & 255u) << (8 * (q & 3));
+          uint4* dst = reinterpret_cast<uint4*>(sec + 32 * tid);
+          dst[0] = make_uint4(pw[0], pw[1], pw[2], pw[3]);
+          dst[1] = make_uint4(pw[4], pw[5], pw[6], pw[7]);
+          continue;
+        }
         const uint32_t k = m.k[j], dpad = (k + 15u) & ~15u;
         if (m.present[j][tid]) sec[m.rank[j][tid]] = static_cast<uint8_t>(tid);
         for (uint32_t i = k + tid; i < dpad; i += blockDim.x) sec[i] = 0;
-        if (b > 0) {
-          const uint4 r0 = reinterpret_cast<const uint4*>(plane)[2 * tid];
-          const uint4 r1 = reinterpret_cast<const uint4*>(plane)[2 * tid + 1];
-          const uint32_t rw[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
-          uint32_t* words = reinterpret_cast<uint32_t*>(sec + dpad) + tid * b;
-          uint64_t acc = 0;
-          uint32_t nb = 0, e = 0;
+        if (b == 0) continue;
+        uint32_t* words = reinterpret_cast<uint32_t*>(sec + dpad) + tid * b;
+        uint64_t acc = 0;
+        uint32_t nb = 0, e = 0;
 #pragma unroll
-          for (int q = 0; q < 32; ++q) {
-            acc |= static_cast<uint64_t>((rw[q >> 2] >> (8 * (q & 3))) & 255u) << nb;
-            nb += b;
-            if (nb >= 32) {
-              words[e++] = static_cast<uint32_t>(acc);
-              acc >>= 32;
-              nb -= 32;
-            }
+        for (int q = 0; q < 32; ++q) {
+          acc |= static_cast<uint64_t>(m.rank[j][(w[q] >> (8 * j)) & 255u]) << nb;
+          nb += b;
+          if (nb >= 32) {
+            words[e++] = static_cast<uint32_t>(acc);
+            acc >>= 32;
+            nb -= 32;
           }
         }
       }
-      __syncthreads();
     }
+    __syncthreads();  // the tables are read until here
   }
 }
 
@@ -254,10 +264,8 @@ KernelSpec bpd_size_spec(uint64_t max_slots) {
 KernelSpec bpd_scan_spec() { return KernelSpec{reinterpret_cast<const void*>(k_bpd_scan), 1, 1024, 0}; }
 
 cudaError_t bpd_encode_spec(uint64_t max_slots, KernelSpec* out) {
-  const cudaError_t e = allow_big_smem(k_bpd_encode);
-  if (e != cudaSuccess) return e;
   *out = KernelSpec{reinterpret_cast<const void*>(k_bpd_encode),
-                    bpd_grid(k_bpd_encode, std::max<uint64_t>(max_slots, 1)), kBpdThreads, kBpdDynSmem};
+                    grid_for(k_bpd_encode, std::max<uint64_t>(max_slots, 1), 1, kBpdThreads), kBpdThreads, 0};
   return cudaSuccess;
 }
 
