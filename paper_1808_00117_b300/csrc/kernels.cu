@@ -95,7 +95,11 @@ __device__ __forceinline__ uint64_t hash_full_page(const uint8_t* src, int t) {
   const uint4* v4 = reinterpret_cast<const uint4*>(src) + t;
   uint64_t c = static_cast<uint64_t>(2 * t) * kPhi;
   uint64_t h = 0;
-  const uint64_t pol = dev::l2_evict_first_policy();
+  // evict-normal, stated explicitly: with an evict-first policy (or no
+  // hint) an 8 GiB pass after the application's 5 % page update took 1.39-
+  // 1.40 ms against 1.34 ms, and 1.43-1.46 against 1.39 ms with a
+  // device-to-host copy running beside it
+  const uint64_t pol = dev::l2_evict_normal_policy();
 #pragma unroll 1
   for (int k = 0; k < kPer; k += U) {
     uint4 v[U];
@@ -123,13 +127,14 @@ __device__ __forceinline__ uint64_t hash_full_page_cmp(const uint8_t* src, const
   uint64_t c = static_cast<uint64_t>(2 * t) * kPhi;
   uint64_t h = 0;
   uint32_t x = 0;
+  const uint64_t pol = dev::l2_evict_normal_policy();
 #pragma unroll 1
   for (int k = 0; k < kPer; k += U) {
     uint4 v[U], w[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      v[u] = ld_stream(v4 + (k + u) * G);
-      w[u] = ld_stream(w4 + (k + u) * G);
+      v[u] = dev::ld_stream_hint(v4 + (k + u) * G, pol);
+      w[u] = dev::ld_stream_hint(w4 + (k + u) * G, pol);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
