@@ -207,26 +207,28 @@ crum_status upload_table(crum_set* s) {
   return CRUM_OK;
 }
 
-constexpr uint64_t kBounceBytes = 256ull << 20;  // 4,096 pages
-
-// Queues the device->host copy of `bytes` of payload (slots from s0 on) on
-// the drain stream: into the image's own buffer, or, when the image keeps no
-// payload, through the set's bounce region so that a footprint larger than
+// Queues the device->host copy of `bytes` of payload on the drain stream, as
+// copies of at most cfg.chunk_bytes each: into the image's own buffer at
+// host_off, or, when the image keeps no payload, each into the set's bounce
+// region (cfg.chunk_bytes of pinned memory), so that a footprint larger than
 // host memory can still be drained and timed.
 crum_status drain_payload(crum_set* s, crum_image* img, uint64_t host_off, const uint8_t* src,
                           uint64_t bytes) {
+  const uint64_t chunk = s->cfg.chunk_bytes;
   if (!img->drop_payload) {
-    CK(cudaMemcpyAsync(img->host + host_off, src, bytes, cudaMemcpyDeviceToHost, s->drain_stream));
+    for (uint64_t off = 0; off < bytes; off += chunk)
+      CK(cudaMemcpyAsync(img->host + host_off + off, src + off, std::min(chunk, bytes - off),
+                         cudaMemcpyDeviceToHost, s->drain_stream));
     return CRUM_OK;
   }
   {
     std::lock_guard<std::mutex> lk(s->bounce_mu);
-    if (s->bounce == nullptr) s->bounce = s->pool->alloc(kBounceBytes);
+    if (s->bounce == nullptr) s->bounce = s->pool->alloc(chunk);
     if (s->bounce == nullptr) return fail(CRUM_ENOMEM, "pinned host pool exhausted (bounce region)");
   }
-  for (uint64_t off = 0; off < bytes; off += kBounceBytes)
-    CK(cudaMemcpyAsync(s->bounce, src + off, std::min(kBounceBytes, bytes - off),
-                       cudaMemcpyDeviceToHost, s->drain_stream));
+  for (uint64_t off = 0; off < bytes; off += chunk)
+    CK(cudaMemcpyAsync(s->bounce, src + off, std::min(chunk, bytes - off), cudaMemcpyDeviceToHost,
+                       s->drain_stream));
   return CRUM_OK;
 }
 
@@ -958,6 +960,7 @@ crum_status crum_set_create(const crum_config* cfg_in, crum_set** out) {
   if (cfg_in) cfg = *cfg_in;
   if (cfg.staging_bytes == 0) cfg.staging_bytes = kDefaultStaging;
   if (cfg.chunk_bytes == 0) cfg.chunk_bytes = kDefaultChunk;
+  cfg.chunk_bytes = (cfg.chunk_bytes + 15) & ~15ull;  // copies stay 16-byte aligned
   if (cfg.staging_bytes < 2ull * kPage)
     return fail(CRUM_EINVAL, "staging_bytes must hold at least one page per half");
   if (cfg.sink < CRUM_SINK_MEMORY || cfg.sink > CRUM_SINK_NULL) return fail(CRUM_EINVAL, "bad sink");
@@ -1045,7 +1048,7 @@ crum_status crum_set_destroy(crum_set* s) {
   if (s->writer.joinable()) s->writer.join();
   cudaStreamSynchronize(s->cap_stream);
   cudaStreamSynchronize(s->drain_stream);
-  if (s->bounce != nullptr) s->pool->free(s->bounce, kBounceBytes);
+  if (s->bounce != nullptr) s->pool->free(s->bounce, s->cfg.chunk_bytes);
   for (Alloc& a : s->allocs) withdraw_advice(s, a);
   image_unref(s->last);
   for (crum::CaptureGraph& G : s->graph) {

@@ -158,11 +158,13 @@ def test_empty_and_all_dirty():
     s.destroy()
 
 
-def test_chunked_capture_small_staging():
-    """Staging halves of 3 pages: captures run chunk by chunk."""
+@pytest.mark.parametrize("chunk", [0, 3 * 4096 + 8])
+def test_chunked_capture_small_staging(chunk):
+    """Staging halves of 3 pages: captures run chunk by chunk; with a drain
+    copy size that is not a page multiple, every drain is many copies."""
     sizes = [17 * P + 5, 4 * P]
     bufs = device_buffers(sizes, seed=7)
-    s = make_set(bufs, staging_bytes=6 * P)
+    s = make_set(bufs, staging_bytes=6 * P, chunk_bytes=chunk)
     o = oracle.OracleSet(sizes)
     for step in range(3):
         if step:
@@ -647,7 +649,7 @@ def test_delta_restore_moves_only_changed_pages():
 @pytest.mark.gpu
 @pytest.mark.parametrize("staging", [None, 8 * P])
 def test_no_payload_keeps_checksum_and_chain(staging):
-    """CRUM_NO_PAYLOAD on a footprint larger than the 256 MiB bounce region,
+    """CRUM_NO_PAYLOAD on a footprint larger than the 64 MiB bounce region,
     through the one-pass and the chunked capture: the image's checksum and
     size equal the oracle's (its payload crossed the link, through several
     bounce copies, and was dropped), and the next incremental, which keeps
