@@ -344,7 +344,8 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": wl.name, "sample_bytes": args.cpu_sample_mib << 20,
                    "parallelism": "single host thread"},
-        "cpu_baseline": {**{k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "cpu_baseline": {**{k: cb[k] for k in ("unit", "cores", "kind", "sample")},
+                         "value": round(cb["value"], 4),
                          "parallel_hash": oracle_parallel_hash(args.cpu_sample_mib, 2, wl)},
         "e2e": {"value": round(cb["value"], 4), "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
