@@ -295,7 +295,8 @@ def test_invalid_registrations():
     t = torch()
     b = t.empty(4 * P, dtype=t.uint8, device="cuda")
     s = crum.CheckpointSet()
-    for ptr, n in [(b.data_ptr() + 8, P), (b.data_ptr(), 0), (0, P)]:
+    # misaligned, empty, null, and 2^32 pages (past the page table's u32 index)
+    for ptr, n in [(b.data_ptr() + 8, P), (b.data_ptr(), 0), (0, P), (b.data_ptr(), (1 << 32) * P)]:
         with pytest.raises(crum.CrumError) as e:
             s.register(ptr, n)
         assert e.value.status == crum.EINVAL
