@@ -70,9 +70,9 @@
  * (valid bytes, then zeros), encoded by oracle_bpd_encode; an encoded length
  * of 65,536 means the slot is stored as is.
  *
- * Byte-plane dictionary code of one slot (this build's compression of the
- * drained bytes; the paper compresses whole images with gzip or LZ4 on the
- * host, Section 4.4): plane j (j = 0..7) is the 8,192 bytes at offsets
+ * Byte-plane dictionary code of one slot (the compression of the drained
+ * bytes stated in include/crum.h; the paper compresses whole images with
+ * gzip or LZ4 on the host, Section 4.4): plane j (j = 0..7) is the 8,192 bytes at offsets
  * 8i + j.  For each plane let D be its distinct byte values in ascending
  * order, k = |D| and b = ceil(log2 k) (b = 0 when k = 1).  A plane with
  * b = 8 is stored as its 8,192 bytes; otherwise as D (k bytes, zero-padded

@@ -49,7 +49,7 @@ __device__ __forceinline__ uint32_t ceil_log2(uint32_t k) {
 
 // Decodes the `len` encoded bytes at `enc` (device or mapped host memory)
 // into `page` (shared, 64 KiB) using `plane` (shared, 8 KiB) and `dict`
-// (shared, 8 x 128).  Returns false, CTA-uniformly, for a code this build
+// (shared, 8 x 128).  Returns false, CTA-uniformly, for a code the encoder
 // cannot have written (the slot is then skipped).
 __device__ inline bool bpd_decode(const uint8_t* enc, uint32_t len, uint8_t* page, uint8_t* plane,
                            uint8_t (*dict)[128], BpdSmem& m) {
