@@ -798,7 +798,7 @@ def run_ours(args):
         vs.destroy()
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:  # a single-GPU run's baseline
         cb = oracle_sample_run(args.cpu_sample_mib, 3, 1, wl)
         cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
         cpu["parallel_hash"] = oracle_parallel_hash(4 * args.cpu_sample_mib, 3, wl)
