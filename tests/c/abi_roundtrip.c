@@ -1,8 +1,9 @@
 /* The C ABI used from C alone (no Python): register two device buffers,
  * take a full and an incremental checkpoint, check the incremental image's
- * page table against the pages this program changed, scribble, restore the
- * chain, and compare every byte.  Prints "ok" and exits 0 on success.
- * Built and run by tests/test_c_abi.py. */
+ * version and page table against the pages this program changed, scribble,
+ * restore the chain, and compare every byte; once with plain and once with
+ * compressed images.  Prints "ok" and exits 0 on success.  Built and run by
+ * tests/test_c_abi.py. */
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -30,7 +31,7 @@
 
 static const size_t kSizes[2] = {5 * CRUM_PAGE_SIZE + 40, 3 * CRUM_PAGE_SIZE};
 
-int main(void) {
+static int round_trip(int compress) {
   uint8_t *dev[2], *host[2], *back[2];
   for (int i = 0; i < 2; ++i) {
     CUDA(cudaMalloc((void **)&dev[i], kSizes[i]));
@@ -41,6 +42,7 @@ int main(void) {
   }
   crum_config cfg;
   crum_config_default(&cfg);
+  cfg.compress = compress;
   crum_set *set = NULL;
   CHECK(crum_set_create(&cfg, &set));
   uint32_t ids[2];
@@ -67,6 +69,12 @@ int main(void) {
   }
   uint8_t *img = (uint8_t *)malloc(info.image_bytes);
   CHECK(crum_image_copy(incr, img, info.image_bytes));
+  uint32_t version;
+  memcpy(&version, img + 8, 4);
+  if (version != (compress ? 2u : 1u)) {
+    fprintf(stderr, "image version %u with compress=%d\n", version, compress);
+    return 1;
+  }
   const uint32_t *ptab = (const uint32_t *)(img + 64 + 16 * 2);
   if (ptab[0] != 0 || ptab[1] != 1 || ptab[2] != 0 || ptab[3] != 5) {
     fprintf(stderr, "unexpected page table %u:%u %u:%u\n", ptab[0], ptab[1], ptab[2], ptab[3]);
@@ -92,6 +100,13 @@ int main(void) {
     free(back[i]);
   }
   free(img);
+  CUDA(cudaStreamDestroy(stream));
+  return 0;
+}
+
+int main(void) {
+  for (int compress = 0; compress < 2; ++compress)
+    if (round_trip(compress) != 0) return 1;
   printf("ok\n");
   return 0;
 }
