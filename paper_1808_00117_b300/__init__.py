@@ -329,6 +329,12 @@ class CheckpointSet:
             load().crum_set_destroy(self.handle)
             self.handle = 0
 
+    def __enter__(self) -> "CheckpointSet":
+        return self
+
+    def __exit__(self, *exc) -> None:
+        self.destroy()
+
     def __del__(self):
         try:
             self.destroy()
