@@ -217,10 +217,11 @@ def test_verify_mode_reports_injected_collision(staging):
     s.destroy()
 
 
-def test_save_load_corrupt_mismatch(tmp_path):
+@pytest.mark.parametrize("compress", [0, 1])
+def test_save_load_corrupt_mismatch(tmp_path, compress):
     sizes = [6 * P + 17]
-    bufs = device_buffers(sizes, seed=13)
-    s = make_set(bufs)
+    bufs = device_buffers(sizes, seed=13, kind="fp32")
+    s = make_set(bufs, compress=compress)
     img0, b0 = _checkpoint_bytes(s)
     mutate(bufs, sizes, 0.4, seed=5)
     img1, b1 = _checkpoint_bytes(s)
