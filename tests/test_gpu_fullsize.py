@@ -138,8 +138,10 @@ def test_large_4096_allocations_sampled():
     """The 140 GiB / 4,096-allocation footprint: the base image is drained
     without keeping its payload (it exceeds host memory); two incremental
     steps of a seeded 2 % scatter are checked: page table in full, the image
-    checksum by the oracle's checker, sampled payload slots, and committed
-    hashes on a seeded sample of pages against the oracle."""
+    checksum by the oracle's checker, sampled payload slots, committed hashes
+    on a seeded sample of pages after each step, and after the last step
+    every committed hash (2.3 million pages) against the oracle's, 8 GiB of
+    the footprint at a time on all host cores."""
     t = torch()
     free, _ = t.cuda.mem_get_info()
     wl = W.workload("large")
@@ -188,5 +190,18 @@ def test_large_4096_allocations_sampled():
             n_valid = min(P, int(wl.sizes[a]) - int(page_local[g]) * P)
             assert int(hashes[g]) == oracle.page_hash(big[lo:lo + n_valid].cpu().numpy())
         img.release()
+    hashes = s.hashes()
+    g0, group, acc = 0, [], 0
+    for a in range(len(wl.sizes)):
+        group.append(a)
+        acc += int(wl.sizes[a])
+        if acc >= (8 << 30) or a == len(wl.sizes) - 1:
+            host = [big[int(offs[k]):int(offs[k + 1])].cpu().numpy() for k in group]
+            exp = oracle_hashes(host)
+            assert np.array_equal(hashes[g0:g0 + exp.size], exp), f"allocations {group[0]}-{group[-1]}"
+            g0 += exp.size
+            group, acc = [], 0
+            del host
+    assert g0 == wl.n_pages
     s.destroy()
     del big
