@@ -205,3 +205,59 @@ def test_large_4096_allocations_sampled():
     assert g0 == wl.n_pages
     s.destroy()
     del big
+
+
+@pytest.mark.parametrize("mode", [crum.RESTORE_MERGED, crum.RESTORE_REPLAY])
+def test_large_shape_restore_from_the_chain(mode):
+    """The large configuration's shape (4,096 managed allocations, sizes
+    log-uniform 64 KiB-2 GiB) at 40 GiB, the most the host can hold as a kept
+    full image: a full image and two incrementals of a 2 % scatter, the
+    memory scribbled, the chain end restored; the whole footprint must equal
+    its state at the chain end (compared on the device byte for byte) and
+    sampled pages equal the host copies taken before the scribble."""
+    t = torch()
+    sizes = W.loguniform_sizes(0x5EED + 4, 4096, 64 << 10, 2 << 30, 40 << 30)
+    S = sum(sizes)
+    free, _ = t.cuda.mem_get_info()
+    if free < 2 * S + (16 << 30):
+        pytest.skip("needs about 100 GB of free device memory")
+    big = W.managed_empty(S)
+    W.fill_(big, 0x5EED + 4, "fp32")
+    offs = np.cumsum([0] + list(sizes))
+    bufs = [big[int(offs[i]):int(offs[i + 1])] for i in range(len(sizes))]
+    n_pages = sum(W.pages_of(n) for n in sizes)
+    first = np.cumsum([0] + [W.pages_of(n) for n in sizes])
+    page_alloc = np.repeat(np.arange(len(sizes)), np.diff(first))
+    page_local = np.arange(n_pages) - first[page_alloc]
+    k = int(round(0.02 * n_pages))
+    s = crum.CheckpointSet(staging_bytes=2 * (int(1.5 * k) + 1) * P, restore_mode=mode)
+    for b in bufs:
+        s.register(b.data_ptr(), b.numel())
+    chain = [s.checkpoint(stream_handle(), crum.FULL)]
+    chain[0].wait()
+    big64 = big.view(t.int64)
+    rng = np.random.default_rng(41)
+    for step in (1, 2):
+        chosen = np.sort(rng.choice(n_pages, size=k, replace=False))
+        words = t.as_tensor((offs[page_alloc[chosen]] + page_local[chosen] * P) // 8, device="cuda")
+        big64[words] = big64[words] ^ t.as_tensor(rng.integers(1, 2**62, size=k) | 1, device="cuda")
+        img = s.checkpoint(stream_handle())
+        img.wait()
+        chain.append(img)
+    t.cuda.synchronize()
+    expect = big.clone()
+    sample = rng.choice(n_pages, size=256, replace=False)
+    def page_bytes(g):
+        a = int(page_alloc[g])
+        lo = int(offs[a]) + int(page_local[g]) * P
+        return big[lo:lo + min(P, int(sizes[a]) - int(page_local[g]) * P)].cpu().numpy()
+    before = [page_bytes(g) for g in sample]
+    W.fill_(big, 77, "u32")
+    s.restore(chain[-1], stream_handle())
+    t.cuda.synchronize()
+    assert t.equal(big, expect)
+    assert all(np.array_equal(page_bytes(g), b) for g, b in zip(sample, before))
+    for c in chain:
+        c.release()
+    s.destroy()
+    del big, expect
