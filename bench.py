@@ -814,7 +814,7 @@ def run_ours(args):
                    "memory": MEMORY_DESC[memory], "kind": wl.kind,
                    "images": "compressed (byte-plane dictionary code)" if args.compress else "plain",
                    "staging_bytes": staging, "parallelism": f"replica per GPU x{world}",
-                   "l2": "inputs (8 GiB) larger than L2 (126 MB); no flush",
+                   "l2": f"inputs ({S / 2**30:g} GiB) larger than L2 (126 MB); no flush",
                    "value_def": "footprint bytes / capture-kernel device time (hash+scan+gather)",
                    "capture_launch": "cuda graph" if args.graph else "one launch per op",
                    "hash_mapping": tune["hash_mapping"], "gather_mapping": tune["gather_mapping"],
