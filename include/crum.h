@@ -100,7 +100,8 @@ typedef struct crum_config {
                                   alternate between consecutive checkpoints; 0: 1 GiB */
     uint64_t chunk_bytes;      /* largest single device->host copy of a drain: a
                                   payload drains as copies of at most this many
-                                  bytes (rounded up to 16), and a payload that is
+                                  bytes (rounded up to 16, at least 4 KiB), and a
+                                  payload that is
                                   not kept (null sink, CRUM_NO_PAYLOAD) lands in
                                   a pinned bounce region of this size; 0: 64 MiB */
     uint64_t host_pool_bytes;  /* initial pinned host pool for images; 0: grow on demand */

@@ -960,7 +960,9 @@ crum_status crum_set_create(const crum_config* cfg_in, crum_set** out) {
   if (cfg_in) cfg = *cfg_in;
   if (cfg.staging_bytes == 0) cfg.staging_bytes = kDefaultStaging;
   if (cfg.chunk_bytes == 0) cfg.chunk_bytes = kDefaultChunk;
-  cfg.chunk_bytes = (cfg.chunk_bytes + 15) & ~15ull;  // copies stay 16-byte aligned
+  // copies stay 16-byte aligned, and none is so small that issuing it costs
+  // more than moving it
+  cfg.chunk_bytes = std::max<uint64_t>((cfg.chunk_bytes + 15) & ~15ull, 4096);
   if (cfg.staging_bytes < 2ull * kPage)
     return fail(CRUM_EINVAL, "staging_bytes must hold at least one page per half");
   if (cfg.sink < CRUM_SINK_MEMORY || cfg.sink > CRUM_SINK_NULL) return fail(CRUM_EINVAL, "bad sink");
