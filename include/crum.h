@@ -101,9 +101,9 @@ typedef struct crum_config {
     uint64_t chunk_bytes;      /* largest single device->host copy of a drain: a
                                   payload drains as copies of at most this many
                                   bytes (rounded up to 16, at least 4 KiB), and a
-                                  payload that is
-                                  not kept (null sink, CRUM_NO_PAYLOAD) lands in
-                                  a pinned bounce region of this size; 0: 64 MiB */
+                                  payload that is not kept (null sink,
+                                  CRUM_NO_PAYLOAD) lands in a pinned bounce region
+                                  of this size; 0: 64 MiB */
     uint64_t host_pool_bytes;  /* initial pinned host pool for images; 0: grow on demand */
     int sink;                  /* crum_sink */
     const char *sink_dir;      /* directory for CRUM_SINK_FILE (copied at create) */
