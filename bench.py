@@ -52,7 +52,8 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="uint32_8g")
+    ap.add_argument("--workload", default="uint32_8g",
+                    help="uint32_8g (default), small16m, stencil, large, serving or oversub")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-verify", action="store_true", help="skip the verify-mode measurement")
@@ -62,7 +63,7 @@ def parse_args(argv=None):
                     help="stencil/large: sets look up managed placement at every checkpoint "
                          "(managed_in_place=1)")
     ap.add_argument("--kind", choices=["u32", "fp32", "fp64", "bf16"], default=None,
-                    help="uint32 workload: element kind of the synthetic data")
+                    help="element kind of the synthetic data (uint32, stencil and large workloads)")
     ap.add_argument("--sink", choices=["memory", "file"], default="memory",
                     help="uint32 workload: where the writer persists images (file: a "
                          "temporary directory on the host's disk, fsync per image)")
