@@ -885,10 +885,10 @@ def run_e2e(torch, crum, W, s, bufs, wl, steps, sh, stream, step0, dist, dev, wo
     image back (PERSISTED: its bytes crossed device->host).  Two forms, each
     step holding its own uploads and its own image drain:
     - pipelined (the value): step k+1's upload is issued before waiting for
-      image k, on a copy stream into one of two landing buffers, so it
-      overlaps step k's capture and shares the full-duplex link with the
-      previous drain, as an application that keeps running while its
-      checkpoint drains would;
+      image k-1 (two images in flight), on a copy stream into one of two
+      landing buffers, so it overlaps step k's capture and shares the
+      full-duplex link with the previous drains, as an application that
+      keeps running while its checkpoints drain would;
     - serial: each step waits for its image before the next upload.
     Images are released once persisted, so the pinned pool is reused."""
     n_pages = wl.n_pages
@@ -952,20 +952,19 @@ def run_e2e(torch, crum, W, s, bufs, wl, steps, sh, stream, step0, dist, dev, wo
         barrier(dist)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        prev = None
+        pending = []
         for step in range(steps):
             u = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
             h2d.append(upload(plan[first_step + 2 + step], u))
             ev.append(u)
-            im = s.checkpoint(sh)
-            if pipelined:
-                if prev is not None:
-                    finish(prev, infos)
-                prev = im
-            else:
-                finish(im, infos)
-        if prev is not None:
-            finish(prev, infos)
+            pending.append(s.checkpoint(sh))
+            # pipelined: two images stay in flight, so the next upload is
+            # queued while the one before it still runs and the copy engine
+            # moving host-to-device never idles; serial: none
+            while len(pending) > (2 if pipelined else 0):
+                finish(pending.pop(0), infos)
+        while pending:
+            finish(pending.pop(0), infos)
         torch.cuda.synchronize()
         dt = max_over_ranks(dist, time.perf_counter() - t0, dev)
         return dt, h2d, infos, statistics.mean(a.elapsed_time(b) for a, b in ev)
@@ -980,8 +979,8 @@ def run_e2e(torch, crum, W, s, bufs, wl, steps, sh, stream, step0, dist, dev, wo
             "d2h_bytes_per_step": int(statistics.mean(i["image_bytes"] for i in infos)),
             "ms_per_step": round(dt * 1e3 / steps, 3),
             "what": "pinned H2D of the step's new pages (copy stream, two landing buffers) + device "
-                    "scatter + crum_checkpoint + image read back (PERSISTED); step k+1's upload "
-                    "overlaps image k's capture and drain",
+                    "scatter + crum_checkpoint + image read back (PERSISTED); two images in flight, "
+                    "step k+1's upload overlaps image k's capture and the drains",
             "submit_to_persisted_ms": round(statistics.mean(i["t_persisted_ms"] for i in infos), 3),
             "upload_ms": round(up_ms, 3),
             "serial": {"value": per(dt_s), "ms_per_step": round(dt_s * 1e3 / steps, 3),
