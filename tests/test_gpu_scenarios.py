@@ -3,7 +3,7 @@ allocation sizes (tiny, ragged, several pages), staging that holds every
 page or only a few (chunked capture), graph or plain launches, random hash
 and gather mappings, verify sets, compressed images (chunked too), four
 data kinds, managed memory whose pages the scenario places on the device or
-the host (read in place or migrated), and
+the host (read in place or migrated), drain copy sizes down to 4 KiB, and
 per step a random rewrite and a random checkpoint flag (incremental, full,
 verify, no payload); now and then the
 chain end is restored onto scribbled memory with the scenario's restore
@@ -73,7 +73,8 @@ def test_random_scenario(seed):
                use_graph=int(rng.integers(0, 2)), hash_mapping=int(rng.integers(0, crum.NUM_HASH_MAPPINGS)),
                gather_mapping=int(rng.integers(0, 6)), verify=int(verify),
                restore_mode=int(rng.integers(0, 4)), compress=int(compress),
-               managed_in_place=int(in_place))
+               managed_in_place=int(in_place),
+               chunk_bytes=int(rng.choice([0, 4096, 12304, 1 << 20])))
     kind = ["u32", "fp32", "fp64", "bf16"][seed % 4]
     if managed:
         bufs = []
