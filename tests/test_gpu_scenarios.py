@@ -59,7 +59,7 @@ def _rewrite(bufs, sizes, frac, rng):
     torch().cuda.synchronize()
 
 
-@pytest.mark.parametrize("seed", range(32))
+@pytest.mark.parametrize("seed", range(64))
 def test_random_scenario(seed):
     rng = np.random.default_rng(1000 + seed)
     sizes = _sizes(rng)
