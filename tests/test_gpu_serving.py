@@ -24,14 +24,22 @@ def _cuda():
 
 
 class Client:
-    def __init__(self, server, idx, size, restore_mode=crum.RESTORE_AUTO):
+    def __init__(self, server, idx, size, restore_mode=crum.RESTORE_AUTO, memory="device"):
         t = torch()
         self.idx, self.size = idx, size
         self.stream = t.cuda.Stream()
-        self.buf = t.empty(size, dtype=t.uint8, device="cuda")
+        # device memory, managed memory on the device, or managed memory the
+        # client keeps in host memory (read in place by its set)
+        if memory == "device":
+            self.buf = t.empty(size, dtype=t.uint8, device="cuda")
+        else:
+            self.buf = W.managed_empty(size)
         W.fill_(self.buf, 600 + idx, "fp32")
         t.cuda.synchronize()
-        self.set = crum.CheckpointSet(external_staging=1, restore_mode=restore_mode)
+        if memory == "host_managed":
+            W.managed_prefetch(self.buf.data_ptr(), size, "host")
+        self.set = crum.CheckpointSet(external_staging=1, restore_mode=restore_mode,
+                                      managed_in_place=int(memory == "host_managed"))
         self.set.register(self.buf.data_ptr(), size)
         self.cid = server.add_client(self.set, self.stream.cuda_stream)
         self.restore_mode = restore_mode
@@ -145,4 +153,19 @@ def test_client_larger_than_budget_is_rejected():
     with pytest.raises(crum.CrumError) as e:
         srv.add_client(s, t.cuda.current_stream().cuda_stream)
     assert e.value.status == crum.EINVAL
+    srv.destroy()
+
+
+def test_managed_clients_in_the_mix():
+    """Clients whose memory is managed, on the device or kept in host memory
+    (read in place), served together with a device-memory client: every
+    image equals the oracle's and every restore brings the memory back."""
+    srv = crum.Server(staging_budget=1 << 30, max_inflight=4, max_checkpoints=-1, max_restores=-1)
+    kinds = ["device", "managed", "host_managed", "host_managed"]
+    mix = [Client(srv, 20 + i, s, crum.RESTORE_AUTO, kinds[i]) for i, s in enumerate(SIZES)]
+    got, exp = run_sequence(srv, mix, rounds=4, restore_at=2)
+    stats = srv.drain()
+    assert stats["failed"] == 0
+    for c in mix:
+        assert got[c.idx] == exp[c.idx], f"client {c.idx} ({kinds[c.idx - 20]}) differs from the oracle"
     srv.destroy()
