@@ -177,10 +177,18 @@ __global__ void __launch_bounds__(kBpdThreads, 2) k_bpd_encode(BpdEncodeArgs a) 
       w[2 * q] = (static_cast<uint64_t>(x.y) << 32) | x.x;
       w[2 * q + 1] = (static_cast<uint64_t>(x.w) << 32) | x.z;
     }
+    // a byte equal to the one before it in its plane needs no second mark
+    // (float planes holding sign and exponent repeat often)
 #pragma unroll
-    for (int q = 0; q < 32; ++q)
+    for (int j = 0; j < 8; ++j) {
+      uint32_t prev = 256u;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) m.present[j][(w[q] >> (8 * j)) & 255u] = 1;
+      for (int q = 0; q < 32; ++q) {
+        const uint32_t x = static_cast<uint32_t>(w[q] >> (8 * j)) & 255u;
+        if (x != prev) m.present[j][x] = 1;
+        prev = x;
+      }
+    }
     __syncthreads();
     bpd_plan(m);
     uint8_t* out = a.out + (off[s] - a.base);
@@ -217,10 +225,14 @@ __global__ void __launch_bounds__(kBpdThreads, 2) k_bpd_encode(BpdEncodeArgs a) 
         if (b == 0) continue;
         uint32_t* words = reinterpret_cast<uint32_t*>(sec + dpad) + tid * b;
         uint64_t acc = 0;
-        uint32_t nb = 0, e = 0;
+        uint32_t nb = 0, e = 0, px = 256u, pr = 0;
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
-          acc |= static_cast<uint64_t>(m.rank[j][(w[q] >> (8 * j)) & 255u]) << nb;
+          // a repeated byte reuses the rank looked up for the one before it
+          const uint32_t x = static_cast<uint32_t>(w[q] >> (8 * j)) & 255u;
+          pr = x == px ? pr : m.rank[j][x];
+          px = x;
+          acc |= static_cast<uint64_t>(pr) << nb;
           nb += b;
           if (nb >= 32) {
             words[e++] = static_cast<uint32_t>(acc);
