@@ -828,7 +828,11 @@ def run_ours(args):
                      "ms_per_launch": round(statistics.mean(hash_ms), 4)},
         "capture": {"ms_mean": round(statistics.mean(cap_ms), 4),
                     "hash_ms_mean": round(statistics.mean(hash_ms), 4),
-                    "frac_of_hbm": round(value / world / peaks["hbm_gbs"], 4)},
+                    "frac_of_hbm": round(value / world / peaks["hbm_gbs"], 4),
+                    **({"encode_ms_mean": round(statistics.mean(i["t_encode_ms"] for i in infos), 4),
+                        "encode_what": "compressed images: device time from captured to code and "
+                                       "trailer written (size, offsets, encode, checksum)"}
+                       if args.compress else {})},
         "drain": {"gbs": round(drain_gbs, 2), "link_measured_gbs": round(link_peak, 2),
                   "frac_measured": round(drain_gbs / link_peak, 4),
                   "effective_gbs": round(statistics.mean(
@@ -1196,7 +1200,9 @@ def run_batched(args):
                      "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
                      "peak_source": peaks["source"]},
         "capture": {"ms_mean": round(statistics.mean(cap_ms), 4),
-                    "hash_ms_mean": round(statistics.mean(hash_ms), 4)},
+                    "hash_ms_mean": round(statistics.mean(hash_ms), 4),
+                    **({"encode_ms_mean": round(statistics.mean(i["t_encode_ms"] for i in infos), 4)}
+                       if args.compress else {})},
         "drain": {"gbs": round(drain_gbs, 2), "link_measured_gbs": round(link_peak, 2),
                   "frac_measured": round(drain_gbs / link_peak, 4),
                   "effective_gbs": round(statistics.mean(

@@ -295,6 +295,9 @@ typedef struct crum_image_info {
     double t_drain_ms;       /* device time of the device->host copies */
     uint64_t host_pages;     /* pages of host-placed managed allocations the
                                 capture read in place (cfg.managed_in_place) */
+    double t_encode_ms;      /* compressed images: device time of the encoding
+                                stage, from captured until the code and the
+                                trailer are written (0 otherwise) */
 } crum_image_info;
 
 /* Fill *info.  Fields past `stage` are zero until the image gets there. */

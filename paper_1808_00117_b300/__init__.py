@@ -92,7 +92,7 @@ class ImageInfo(ctypes.Structure):
                 ("t_captured_ms", ctypes.c_double), ("t_drained_ms", ctypes.c_double),
                 ("t_persisted_ms", ctypes.c_double), ("t_hash_ms", ctypes.c_double),
                 ("t_compact_ms", ctypes.c_double), ("t_drain_ms", ctypes.c_double),
-                ("host_pages", ctypes.c_uint64)]
+                ("host_pages", ctypes.c_uint64), ("t_encode_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -106,7 +106,7 @@ void image_unref(crum_image* img) {
     if (img->ev_submit) cudaEventDestroy(img->ev_submit);
     if (img->ev_captured) cudaEventDestroy(img->ev_captured);
     if (img->ev_drained) cudaEventDestroy(img->ev_drained);
-    for (cudaEvent_t ev : {img->ev_k0, img->ev_k1, img->ev_k2, img->ev_d0})
+    for (cudaEvent_t ev : {img->ev_k0, img->ev_k1, img->ev_k2, img->ev_d0, img->ev_e1})
       if (ev) cudaEventDestroy(ev);
     delete img;
     img = parent;
@@ -413,6 +413,8 @@ void drainer_main(crum_set* s) {
     if (cudaEventElapsedTime(&ms, img->ev_submit, img->ev_drained) == cudaSuccess)
       img->t_drained_ms = ms;
     if (cudaEventElapsedTime(&ms, img->ev_k0, img->ev_k1) == cudaSuccess) img->t_hash_ms = ms;
+    if (img->compressed && cudaEventElapsedTime(&ms, img->ev_captured, img->ev_e1) == cudaSuccess)
+      img->t_encode_ms = ms;
     if (cudaEventElapsedTime(&ms, img->ev_k2, img->ev_captured) == cudaSuccess)
       img->t_compact_ms = ms;
     if (cudaEventElapsedTime(&ms, img->ev_d0, img->ev_drained) == cudaSuccess)
@@ -453,13 +455,11 @@ void writer_main(crum_set* s) {
 
 crum_status new_image_events(crum_image* img) {
   for (cudaEvent_t* ev : {&img->ev_submit, &img->ev_captured, &img->ev_drained, &img->ev_k0,
-                          &img->ev_k1, &img->ev_k2, &img->ev_d0})
+                          &img->ev_k1, &img->ev_k2, &img->ev_d0, &img->ev_e1})
     CK(cudaEventCreate(ev));
   return CRUM_OK;
 }
 
-// Captures in staging-sized chunks when the set has more pages than one
-// staging half holds.  The dirty count is read on the host first.
 // Restore of a whole chain in two launches (see k_chain_owner and
 // k_restore_merged): every page once, from the newest image holding it.
 crum_status restore_merged(crum_set* s, const std::vector<crum::ChainImage>& ci,
@@ -522,6 +522,10 @@ crum_status restore_merged(crum_set* s, const std::vector<crum::ChainImage>& ci,
   return CRUM_OK;
 }
 
+// Captures in staging-sized chunks when the set has more pages than one
+// staging half holds.  The dirty count is read on the host first; each
+// chunk is gathered (and, for compressed images, encoded) into one half
+// while the other half drains.
 crum_status checkpoint_chunked(crum_set* s, crum_image* img, cudaStream_t app,
                                std::unique_lock<std::mutex>& lk, const crum::GatherArgs& base) {
   Half& H0 = s->half[img->half];
@@ -612,6 +616,7 @@ crum_status checkpoint_chunked(crum_set* s, crum_image* img, cudaStream_t app,
     CK(cudaMemcpyAsync(H0.meta + 48, &poff, 8, cudaMemcpyHostToDevice, s->cap_stream));
     CK(cudaMemcpyAsync(H0.meta + 56, &final_len, 8, cudaMemcpyHostToDevice, s->cap_stream));
     CK(crum::launch_hash_bytes(H0.meta, poff, 0, H0.scalars + 1, s->cap_stream));
+    CK(cudaEventRecord(img->ev_e1, s->cap_stream));
     img->payload_bytes = enc_base;
     img->image_bytes = final_len;
     if (!img->drop_payload) {
@@ -652,6 +657,7 @@ crum_status graph_build(crum_set* s, int h, crum_image* img, const crum::HashArg
     cudaGraphDestroy(G.graph);
     G.graph = nullptr;
   }
+  G.encoded = nullptr;
   for (cudaEvent_t& ev : G.placeholder)
     if (ev == nullptr) CK(cudaEventCreate(&ev));
   (void)img;
@@ -749,6 +755,8 @@ crum_status graph_build(crum_set* s, int h, crum_image* img, const crum::HashArg
     if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n, g, &prev, 1, &kp);
     after(n);
     if (e == cudaSuccess) e = cudaGraphAddEventRecordNode(&n, g, &prev, 1, H.ev_encoded);
+    after(n);
+    if (e == cudaSuccess) e = cudaGraphAddEventRecordNode(&G.encoded, g, &prev, 1, G.placeholder[4]);
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&G.exec, g, 0);
   if (e != cudaSuccess) {
@@ -789,11 +797,14 @@ crum_status graph_launch(crum_set* s, int h, crum_image* img, const crum::HashAr
   if (e == cudaSuccess) e = cudaGraphExecEventRecordNodeSetEvent(G.exec, G.k2, img->ev_k2);
   if (e == cudaSuccess)
     e = cudaGraphExecEventRecordNodeSetEvent(G.exec, G.captured, img->ev_captured);
+  if (e == cudaSuccess && G.encoded != nullptr)
+    e = cudaGraphExecEventRecordNodeSetEvent(G.exec, G.encoded, img->ev_e1);
   if (e == cudaSuccess) e = cudaGraphLaunch(G.exec, s->cap_stream);
   // back to the placeholders: the launch just queued keeps the image's
   // events, and the executable graph never refers to an event that may die
-  const cudaGraphNode_t nodes[4] = {G.k0, G.k1, G.k2, G.captured};
-  for (int i = 0; i < 4; ++i) {
+  const cudaGraphNode_t nodes[5] = {G.k0, G.k1, G.k2, G.captured, G.encoded};
+  for (int i = 0; i < 5; ++i) {
+    if (nodes[i] == nullptr) continue;
     const cudaError_t r = cudaGraphExecEventRecordNodeSetEvent(G.exec, nodes[i], G.placeholder[i]);
     if (e == cudaSuccess) e = r;
   }
@@ -1454,6 +1465,7 @@ crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, cr
         ce = crum::launch_bpd_checksum(ka, cmeta_bytes(img->n_allocs, s->n_pages) + s->n_pages * kPage,
                                        s->cap_stream);
       if (ce == cudaSuccess) ce = cudaEventRecord(H.ev_encoded, s->cap_stream);
+      if (ce == cudaSuccess) ce = cudaEventRecord(img->ev_e1, s->cap_stream);
     }
     if (ce != cudaSuccess)
       return unwind(fail(CRUM_ECUDA, "capture launch: %s", cudaGetErrorString(ce)));
@@ -1552,6 +1564,7 @@ crum_status crum_image_info_get(const crum_image* cimg, crum_image_info* info) {
     info->t_drain_ms = img->t_drain_ms;
   }
   info->host_pages = img->host_pages;
+  if (img->stage >= CRUM_WAIT_DRAINED) info->t_encode_ms = img->t_encode_ms;
   if (img->stage >= CRUM_WAIT_PERSISTED) info->t_persisted_ms = img->t_persisted_ms;
   return CRUM_OK;
 }

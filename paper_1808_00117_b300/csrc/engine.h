@@ -96,11 +96,12 @@ struct CaptureGraph {
   cudaGraph_t graph = nullptr;  // kept: node handles below belong to it
   cudaGraphExec_t exec = nullptr;
   cudaGraphNode_t k0 = nullptr, k1 = nullptr, k2 = nullptr, captured = nullptr;
+  cudaGraphNode_t encoded = nullptr;  // compressed sets: end of the encoding stage
   cudaGraphNode_t hash = nullptr, scan = nullptr, gather = nullptr;
   KernelSpec hs{}, ss{}, gs{};
   // events the record nodes hold between launches (an image's events are
   // set only for its own launch: images, and their events, die earlier)
-  cudaEvent_t placeholder[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t placeholder[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   uint64_t epoch = 0;
 };
 
@@ -145,9 +146,10 @@ struct crum_image {
   // phase timing: hash kernel [ev_k0, ev_k1], compaction [ev_k2, ev_captured]
   // (ev_k2 is taken once the staging half is free), drain [ev_d0, ev_drained]
   cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr, ev_k2 = nullptr, ev_d0 = nullptr;
+  cudaEvent_t ev_e1 = nullptr;  // compressed: encoding stage done [ev_captured, ev_e1]
   std::chrono::steady_clock::time_point t_submit;
   double t_captured_ms = 0, t_drained_ms = 0, t_persisted_ms = 0;
-  double t_hash_ms = 0, t_compact_ms = 0, t_drain_ms = 0;
+  double t_hash_ms = 0, t_compact_ms = 0, t_drain_ms = 0, t_encode_ms = 0;
   int half = 0;
   bool drop_payload = false;  // null sink
   int64_t ticket = -1;        // drain order under a DrainSequencer

@@ -51,6 +51,7 @@ def test_compressed_images_equal_the_oracle(kind):
         assert oracle.image_version(got) == 2
         assert first_diff(got, exp) is None, f"step {step}"
         assert img.info()["image_bytes"] == len(exp)
+        assert img.info()["t_encode_ms"] > 0  # the encoding stage was timed
         if kind in ("fp32", "fp64", "bf16") and step == 0:
             assert len(got) < 0.95 * len(plain)
         img.release()
@@ -70,6 +71,7 @@ def test_compressed_capture_as_one_graph():
         img, got = _ckpt(s)
         exp, *_ = o.checkpoint(host_copies(bufs))
         assert first_diff(got, exp) is None, f"step {step}"
+        assert img.info()["t_encode_ms"] > 0
         img.release()
     extra = device_buffers([5 * P + 16], seed=94, kind="fp32")
     s.register(extra[0].data_ptr(), extra[0].numel())
@@ -174,7 +176,7 @@ def test_compressed_chunked_capture_equals_the_oracle(kind):
         exp, *_ = o.checkpoint(states[-1])
         assert oracle.image_version(got) == 2
         assert first_diff(got, exp) is None, f"step {step}"
-        assert img.info()["image_bytes"] == len(exp)
+        assert img.info()["image_bytes"] == len(exp) and img.info()["t_encode_ms"] > 0
         chain.append(img)
     for mode in (crum.RESTORE_REPLAY, crum.RESTORE_MERGED, crum.RESTORE_DELTA):
         r = make_set(bufs, restore_mode=mode)
