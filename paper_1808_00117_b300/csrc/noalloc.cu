@@ -119,13 +119,15 @@ extern "C" crum_status crum_dirty_pages_static(const void* ptr, uint64_t bytes, 
     crum::set_last_error("crum_dirty_pages_static: pointer not 16-byte aligned");
     return CRUM_EINVAL;
   }
-  const uint64_t n_pages = (bytes + crum::kPage - 1) / crum::kPage;
-  if (n_pages > crum::kStaticMaxPages) {
+  // compared in bytes before any rounding: near 2^64 the page count of
+  // `bytes` would wrap to a small number
+  if (bytes > crum::kStaticMaxPages * crum::kPage) {
     crum::set_last_error(
         "crum_dirty_pages_static: more pages than the static scratch holds "
         "(CRUM_STATIC_MAX_PAGES = 4194304, 256 GiB)");
     return CRUM_EINVAL;
   }
+  const uint64_t n_pages = (bytes + crum::kPage - 1) / crum::kPage;
   int device = -1;
   uint32_t* bits = nullptr;
   if (cudaGetDevice(&device) != cudaSuccess || crum::static_bits(device, &bits) != cudaSuccess) {
@@ -151,11 +153,16 @@ extern "C" crum_status crum_dirty_pages_static(const void* ptr, uint64_t bytes, 
     crum::set_last_error("crum_dirty_pages_static: hash launch failed");
     return CRUM_ECUDA;
   }
-  crum::k_emit_dirty_pages<<<1, crum::kEmitThreads, 0, st>>>(bits, n_words, pages_out, count_out);
-  crum::g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-  if (cudaGetLastError() != cudaSuccess) {
+  // launched through cudaLaunchKernel so that its own return value is the
+  // launch's status (cudaGetLastError would also report, and clear, an
+  // earlier unrelated error of the caller's)
+  const uint32_t* bits_arg = bits;
+  void* args[] = {&bits_arg, const_cast<uint64_t*>(&n_words), &pages_out, &count_out};
+  if (cudaLaunchKernel(reinterpret_cast<const void*>(crum::k_emit_dirty_pages), dim3(1),
+                       dim3(crum::kEmitThreads), args, 0, st) != cudaSuccess) {
     crum::set_last_error("crum_dirty_pages_static: list launch failed");
     return CRUM_ECUDA;
   }
+  crum::g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
   return CRUM_OK;
 }

@@ -75,11 +75,45 @@ def test_static_matches_checkpoint_on_consecutive_calls():
     s.destroy()
 
 
+@pytest.mark.parametrize("n_full, tail, k", [(1100, 100, 300), (32768, 4104, 2000)],
+                         ids=["1101_pages", "32769_pages"])
+def test_static_matches_checkpoint_many_warps(n_full, tail, k):
+    """Sizes whose bitmap spreads over several warps of the listing kernel
+    (1,101 pages: 35 bitmap words) and over more words than it has threads
+    (32,769 pages, just over 2 GiB: 1,025 words, two per thread), with the
+    changed pages scattered over the whole allocation and the tail page
+    among them; two calls back to back, checked against the regular path."""
+    t = torch()
+    size = n_full * P + tail
+    buf = device_buffers([size], seed=23)[0]
+    n = W.pages_of(size)
+    s = make_set([buf], staging_bytes=2 * (k + 8) * P, sink=crum.SINK_NULL)
+    hashes = t.zeros(n, dtype=t.int64, device="cuda")
+    s.checkpoint(stream_handle(), crum.FULL | crum.NO_PAYLOAD).wait()
+    _, c = _static_call(buf, hashes, full=True)
+    assert c == n
+    assert np.array_equal(hashes.cpu().numpy().view(np.uint64), s.hashes())
+    for rnd in range(2):
+        chosen = np.union1d(W.choose_uniform(40 + rnd, n, k), [n - 1])
+        W.mutate_pages_(buf, chosen, 50 + rnd)
+        img = s.checkpoint(stream_handle())
+        img.wait()
+        got_pages, c = _static_call(buf, hashes, full=False)
+        info = img.info()
+        assert c == info["n_dirty"] == chosen.size
+        assert np.array_equal(got_pages, chosen)
+        assert np.array_equal(hashes.cpu().numpy().view(np.uint64), s.hashes())
+        img.release()
+    s.destroy()
+
+
 def test_static_rejects_more_pages_than_its_scratch():
     t = torch()
     buf = t.empty(P, dtype=t.uint8, device="cuda")
-    too_many = (4194304 + 1) * P  # checked before any device work
-    st = crum.load().crum_dirty_pages_static(buf.data_ptr(), too_many, buf.data_ptr(), 0,
-                                             buf.data_ptr(), buf.data_ptr(), stream_handle())
-    assert st == crum.EINVAL
-    assert b"CRUM_STATIC_MAX_PAGES" in crum.load().crum_last_error()
+    # checked before any device work; the last size is one whose page count
+    # wraps past 2^64 when rounded up
+    for too_many in ((4194304 + 1) * P, 4194304 * P + 1, 2**64 - 1, 2**64 - P + 1):
+        st = crum.load().crum_dirty_pages_static(buf.data_ptr(), too_many, buf.data_ptr(), 0,
+                                                 buf.data_ptr(), buf.data_ptr(), stream_handle())
+        assert st == crum.EINVAL, too_many
+        assert b"CRUM_STATIC_MAX_PAGES" in crum.load().crum_last_error()
