@@ -265,11 +265,39 @@ class OracleSet:
         self.compress = compress
         self.sizes = [int(s) for s in sizes]
         self.ids = list(ids) if ids is not None else list(range(len(self.sizes)))
+        self.next_id = max(self.ids) + 1 if self.ids else 0
         n = total_pages(self.sizes)
         self.h_prev = np.zeros(n, dtype=np.uint64)
         self.force = np.ones(n, dtype=np.uint8)
         self.seq = 0
         self.last_seq = None
+        self.new_base = True
+
+    def _registration_changed(self):
+        # Algorithm 1: a region that starts being tracked has every page
+        # dirty.  Page indices of an image refer to the allocation table of
+        # its chain, so any change of the table starts a new chain: the next
+        # image is full (no parent), while sequence numbers keep counting.
+        n = total_pages(self.sizes)
+        self.h_prev = np.zeros(n, dtype=np.uint64)
+        self.force = np.ones(n, dtype=np.uint8)
+        self.new_base = True
+
+    def register(self, size: int) -> int:
+        """Add an allocation at the end of the registration order; returns
+        its id (ids count up from the set's first and are never reused)."""
+        self.sizes.append(int(size))
+        self.ids.append(self.next_id)
+        self.next_id += 1
+        self._registration_changed()
+        return self.ids[-1]
+
+    def unregister(self, alloc_id: int) -> None:
+        """Drop an allocation; the others keep their order and ids."""
+        k = self.ids.index(alloc_id)
+        del self.sizes[k]
+        del self.ids[k]
+        self._registration_changed()
 
     def checkpoint(self, allocs, full: bool = False, verify_prev=None):
         h = hash_all(allocs)
@@ -278,10 +306,11 @@ class OracleSet:
         if verify_prev is not None:
             d, collisions = verify(allocs, verify_prev, d)
         parent = self.last_seq if self.last_seq is not None else 0xFFFFFFFFFFFFFFFF
-        is_full = full or self.last_seq is None
+        is_full = full or self.new_base
         img = build_image(allocs, self.ids, h, d, is_full, self.seq, parent, self.compress)
         self.h_prev = h
         self.force[:] = 0
+        self.new_base = False
         self.last_seq = self.seq
         self.seq += 1
         return img, d, h, collisions
@@ -292,6 +321,7 @@ class OracleSet:
             if st != OK:
                 return st
         self.force[:] = 0
+        self.new_base = False
         last = chain[-1]
         self.last_seq = int(np.frombuffer(last[16:24], dtype=np.uint64)[0])
         self.seq = self.last_seq + 1

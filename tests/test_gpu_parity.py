@@ -176,18 +176,41 @@ def test_chunked_capture_small_staging(chunk):
 
 
 def test_registration_change_forces_full():
-    sizes = [3 * P, P + 1]
+    """Register and unregister between checkpoints: the image after each
+    change is full (a new chain base, sequence numbers counting on), the
+    one after it incremental again; whole images against the oracle's."""
+    sizes = [3 * P, P + 1, 2 * P + 24]
     bufs = device_buffers(sizes, seed=9)
     s = crum.CheckpointSet()
-    s.register(bufs[0].data_ptr(), sizes[0])
+    o = oracle.OracleSet(sizes[:1])
+    ids = [s.register(bufs[0].data_ptr(), sizes[0])]
     _, b0 = _checkpoint_bytes(s)
-    s.register(bufs[1].data_ptr(), sizes[1])
+    e0, *_ = o.checkpoint(host_copies(bufs[:1]))
+    assert first_diff(b0, e0) is None
+    for i in (1, 2):
+        ids.append(s.register(bufs[i].data_ptr(), sizes[i]))
+        assert o.register(sizes[i]) == ids[-1]
     _, b1 = _checkpoint_bytes(s)
+    e1, *_ = o.checkpoint(host_copies(bufs))
     h = parse_header(b1)
-    assert h["flags"] == 1 and h["n"] == 5 and h["A"] == 2
-    exp, *_ = oracle.OracleSet(sizes).checkpoint(host_copies(bufs))
-    # same bytes as a fresh set's first image except seq
-    assert first_diff(b1[32:-8], exp[32:-8]) is None
+    assert h["flags"] == 1 and h["n"] == 3 + 2 + 3 and h["A"] == 3 and h["seq"] == 1
+    assert first_diff(b1, e1) is None
+    mutate(bufs, sizes, 0.5, seed=91)
+    _, b2 = _checkpoint_bytes(s)
+    e2, *_ = o.checkpoint(host_copies(bufs))
+    assert parse_header(b2)["flags"] == 0 and first_diff(b2, e2) is None
+    s.unregister(ids[1])
+    o.unregister(ids[1])
+    kept = [bufs[0], bufs[2]]
+    _, b3 = _checkpoint_bytes(s)
+    e3, *_ = o.checkpoint(host_copies(kept))
+    assert parse_header(b3)["flags"] == 1 and parse_header(b3)["seq"] == 3
+    assert first_diff(b3, e3) is None
+    mutate(kept, [sizes[0], sizes[2]], 0.5, seed=92)
+    _, b4 = _checkpoint_bytes(s)
+    e4, *_ = o.checkpoint(host_copies(kept))
+    assert first_diff(b4, e4) is None
+    s.destroy()
     s.destroy()
 
 
@@ -381,9 +404,14 @@ def test_graph_launch_matches_oracle(hm):
         assert info["t_hash_ms"] > 0 and info["t_compact_ms"] > 0
     extra = device_buffers([3 * P + 1], seed=99)
     s.register(extra[0].data_ptr(), extra[0].numel())
-    _, got = _checkpoint_bytes(s)
-    exp, *_ = oracle.OracleSet(sizes + [3 * P + 1]).checkpoint(host_copies(bufs + extra))
-    assert first_diff(got[32:-8], exp[32:-8]) is None and parse_header(got)["flags"] == 1
+    o.register(3 * P + 1)
+    for step in range(2):
+        if step:
+            mutate(bufs + extra, sizes + [3 * P + 1], 0.3, seed=610 + step)
+        _, got = _checkpoint_bytes(s)
+        exp, *_ = o.checkpoint(host_copies(bufs + extra))
+        assert first_diff(got, exp) is None, f"after the change, step {step}"
+        assert parse_header(got)["flags"] == (1 if step == 0 else 0)
     s.destroy()
 
 

@@ -290,6 +290,55 @@ def test_checkpoint_restore_chain_roundtrip():
         assert d_n.sum() == 0 and _parse(img_n)["parent"] == k
 
 
+def test_registration_change_starts_a_new_full_chain():
+    """Algorithm 1: a region that starts being tracked has every page dirty.
+    After register or unregister the next image is full (no parent, every
+    page of every registered allocation, ids as assigned), sequence numbers
+    keep counting, and the next image after that is an ordinary incremental
+    of the new table.  Checked with the independent struct parser, the
+    big-integer hash and a restore of the new chain onto garbage."""
+    rng = np.random.default_rng(8)
+    sizes = [2 * 65536 + 12, 65536]
+    allocs = [rng.integers(0, 256, size=s, dtype=np.uint8) for s in sizes]
+    s = oracle.OracleSet(sizes)
+    s.checkpoint(allocs)
+    _mutate(allocs, rng, 0.5)
+    s.checkpoint(allocs)
+    extra = rng.integers(0, 256, size=3 * 65536 + 4096, dtype=np.uint8)
+    assert s.register(extra.size) == 2
+    allocs3 = allocs + [extra]
+    img, d, h, _ = s.checkpoint(allocs3)
+    p = _parse(img)
+    assert p["flags"] == 1 and p["seq"] == 2 and p["parent"] == 0xFFFFFFFFFFFFFFFF
+    assert d.all() and p["n"] == 3 + 1 + 4
+    assert p["allocs"] == [(0, 0, sizes[0]), (1, 0, sizes[1]), (2, 0, extra.size)]
+    assert p["ptab"] == [(0, 0), (0, 1), (0, 2), (1, 0), (2, 0), (2, 1), (2, 2), (2, 3)]
+    assert p["hashes"][5] == B.hash_bytes(extra[65536:131072].tobytes())
+    assert p["payload"][7] == extra[3 * 65536:].tobytes() + b"\0" * (65536 - 4096)
+    assert p["trailer"] == B.hash_bytes(img[:-8])
+    # the next image is incremental again, parented on the new base
+    touched = _mutate(allocs3, rng, 0.4)
+    img2, d2, _, _ = s.checkpoint(allocs3)
+    p2 = _parse(img2)
+    assert p2["flags"] == 0 and p2["seq"] == 3 and p2["parent"] == 2
+    assert set(np.nonzero(d2)[0].tolist()) == touched
+    # unregistering the first allocation: ids 1 and 2 stay, a full image again
+    s.unregister(0)
+    img3, d3, _, _ = s.checkpoint(allocs3[1:])
+    p3 = _parse(img3)
+    assert p3["flags"] == 1 and p3["seq"] == 4 and p3["parent"] == 0xFFFFFFFFFFFFFFFF
+    assert p3["allocs"] == [(1, 0, sizes[1]), (2, 0, extra.size)] and d3.all() and p3["n"] == 5
+    assert p3["ptab"][0] == (0, 0) and p3["ptab"][1] == (1, 0)
+    assert p3["payload"][0] == allocs[1].tobytes()
+    assert p3["trailer"] == B.hash_bytes(img3[:-8])
+    # the chain that began at the registration change restores onto garbage
+    garbage = [rng.integers(0, 256, size=a.size, dtype=np.uint8) for a in allocs3]
+    r = oracle.OracleSet([a.size for a in allocs3])
+    assert r.restore([img, img2], garbage) == oracle.OK
+    for got, exp in zip(garbage, allocs3):
+        assert np.array_equal(got, exp)
+
+
 def test_restore_mismatch():
     a = np.zeros(70000, dtype=np.uint8)
     img, *_ = oracle.OracleSet([a.size]).checkpoint([a])
