@@ -1,10 +1,14 @@
 """Parity at full workload sizes, in the launch configuration bench.py times
 (staging halves that hold every page, autotuned mappings).  The oracle is
-too slow for whole images here, so: page tables are checked in full against
-the workload's known dirty set, every page hash against the oracle (hashed
-on all host cores over page-aligned slices: page hashes are page-local),
-the incremental image's checksum by the oracle's image checker, payload
-slots on a seeded sample, and the restored chain on a seeded sample."""
+too slow for whole images here, so each image is checked part by part, in
+full: the page table against the workload's known dirty set, every payload
+slot against the pages' bytes copied from the device (valid bytes, then
+zeros), every committed page hash against the oracle (hashed on all host
+cores over page-aligned slices: page hashes are page-local), and the image
+trailer by the oracle's image checker; a restore of the chain end onto
+scribbled memory must give back the whole footprint.  At 140 GiB the page
+tables and every committed hash are checked in full, payloads and the
+restore on samples (a 140 GiB full image does not fit in host memory)."""
 from concurrent.futures import ThreadPoolExecutor
 import os
 
@@ -47,61 +51,98 @@ def oracle_hashes(host_allocs, chunk_pages=4096):
     return np.concatenate(parts)
 
 
-def make_bench_set(bufs):
+def make_bench_set(bufs, **cfg):
     n_pages = sum(W.pages_of(b.numel()) for b in bufs)
-    s = crum.CheckpointSet(staging_bytes=2 * (n_pages + 1) * P)
+    s = crum.CheckpointSet(staging_bytes=2 * (n_pages + 1) * P, **cfg)
     for b in bufs:
         s.register(b.data_ptr(), b.numel())
     return s
 
 
-def check_image_sample(img_bytes, host_allocs, offsets, rng, n_sample=64):
-    h = parse_header(img_bytes)
-    pt = page_table(img_bytes)
-    idx = rng.choice(h["n"], size=min(n_sample, h["n"]), replace=False)
-    for s in idx:
-        a, p = int(pt[s, 0]), int(pt[s, 1])
-        src = host_allocs[a][p * P:(p + 1) * P]
-        slot = np.frombuffer(img_bytes, dtype=np.uint8, count=P, offset=h["poff"] + int(s) * P)
-        assert np.array_equal(slot[:src.size], src) and not slot[src.size:].any(), f"slot {s}"
+def image_array(img, out=None):
+    """The image's bytes in a (reused) host array, one copy out of the
+    library's pinned buffer."""
+    n = img.info()["image_bytes"]
+    if out is None or out.size < n:
+        out = np.empty(n, dtype=np.uint8)
+    img.copy_into(out.ctypes.data, n)
+    return out[:n]
+
+
+def check_payload_full(img, bufs):
+    """Every payload slot of an image equals its page's valid bytes, followed
+    by zeros; the pages are read straight from the device allocations
+    `bufs` (torch indexing, not the library) and compared on the device."""
+    t = torch()
+    h = parse_header(img)
+    pt = page_table(img)
+    n = h["n"]
+    if n == 0:
+        return
+    payload = t.from_numpy(img[h["poff"]:h["poff"] + n * P]).to("cuda").view(n, P)
+    for a in np.unique(pt[:, 0]):
+        rows = np.flatnonzero(pt[:, 0] == a)
+        pages = pt[rows, 1].astype(np.int64)
+        buf = bufs[int(a)]
+        n_full = buf.numel() // P
+        full = pages < n_full
+        if full.any():
+            exp = buf[:n_full * P].view(n_full, P)[t.as_tensor(pages[full], device="cuda")]
+            got = payload[t.as_tensor(rows[full], device="cuda")]
+            assert t.equal(got, exp), f"allocation {a}"
+        for r in rows[~full]:
+            v = buf.numel() - n_full * P
+            assert t.equal(payload[int(r), :v], buf[n_full * P:]), f"allocation {a} tail"
+            assert not payload[int(r), v:].any(), f"allocation {a} tail padding"
+    del payload
 
 
 def test_uint32_8g_full_size():
+    """The 8 GiB uint32 configuration: a full checkpoint, then 10 incremental
+    checkpoints of 5 % clustered page runs, each image checked in full, then
+    the chain end (full + 10 incrementals) restored onto scribbled memory
+    and the whole footprint compared."""
     t = torch()
     wl = W.workload("uint32_8g")
     buf = t.empty(wl.sizes[0], dtype=t.uint8, device="cuda")
     W.fill_(buf, wl.seed, wl.kind)
     s = make_bench_set([buf])
-    s.checkpoint(stream_handle(), crum.FULL).wait()
+    chain = [s.checkpoint(stream_handle(), crum.FULL)]
+    chain[0].wait()
     s.autotune()
-    chain, rng = [], np.random.default_rng(11)
-    for step in (1, 2):
+    for step in range(1, 11):
         pages = W.choose_step(wl, step, wl.n_pages)
         W.mutate_pages_(buf, pages, wl.seed + step)
         img = s.checkpoint(stream_handle())
         img.wait()
         chain.append(img)
-        b = img.to_bytes()
+        b = image_array(img)
         assert page_table(b)[:, 1].tolist() == pages.tolist()  # in full, ascending
         assert oracle.check_image(b) == oracle.OK               # trailer over every byte
-        host = buf.cpu().numpy()
-        check_image_sample(b, [host], [0], rng)
-        assert np.array_equal(s.hashes(), oracle_hashes([host]))
+        check_payload_full(b, [buf])
+        assert np.array_equal(s.hashes(), oracle_hashes([buf.cpu().numpy()]))
         del b
-    state = buf.cpu().numpy()
-    sample = rng.choice(wl.n_pages, size=256, replace=False)
+    expect = buf.clone()
     W.fill_(buf, 4242, "u32")
     s.restore(chain[-1], stream_handle())
     t.cuda.synchronize()
-    got = buf.cpu().numpy()
-    for p in sample:
-        assert np.array_equal(got[p * P:(p + 1) * P], state[p * P:(p + 1) * P]), p
+    assert t.equal(buf, expect)
     for img in chain:
         img.release()
     s.destroy()
+    del expect
 
 
 def test_stencil_full_size():
+    """The stencil configuration (200 fp64 fields, 24 GiB): 20 checkpoints,
+    each after a 27-point stencil step over interior z-ranges (30 % of
+    pages), batched, autotuned; every image checked in full (page table,
+    payload, trailer of the first and last; committed hashes against the
+    oracle at the first new chain and at the end), then the chain end restored onto scribbled memory and
+    the whole footprint compared.  A chain is capped at 5 incrementals
+    (``max_chain``) so that host memory holds one chain (24 GiB + 5 x 7 GiB):
+    checkpoints 6, 12 and 18 are full, and the chain end (checkpoint 20) is
+    the full image of checkpoint 18 plus two incrementals."""
     t = torch()
     wl = W.workload("stencil")
     bufs = []
@@ -109,39 +150,60 @@ def test_stencil_full_size():
         b = t.empty(n, dtype=t.uint8, device="cuda")
         W.fill_(b, wl.seed * 7919 + i, wl.kind)
         bufs.append(b)
-    s = make_bench_set(bufs)
+    s = make_bench_set(bufs, max_chain=5)
     s.checkpoint(stream_handle(), crum.FULL).wait()
     s.autotune()
-    offsets = np.cumsum([0] + [W.pages_of(n) for n in wl.sizes])
-    plans = [W.stencil_plan(n, wl.dirty_frac, 77 + i) for i, n in enumerate(wl.sizes)]
-    for b, plan in zip(bufs, plans):
-        W.stencil_step_(b, plan)
-    img = s.checkpoint(stream_handle())
-    img.wait()
-    b = img.to_bytes()
     plane = 8 * W.STENCIL_NX * W.STENCIL_NY
-    exp = []
-    for a, plan in enumerate(plans):
-        if plan is not None:
-            _, z0, L = plan
-            exp.extend((a, p) for p in range(z0 * plane // P, ((z0 + L) * plane - 1) // P + 1))
-    assert page_table(b).tolist() == [list(x) for x in exp]  # in full
-    assert oracle.check_image(b) == oracle.OK
-    hosts = [x.cpu().numpy() for x in bufs]
-    check_image_sample(b, hosts, offsets, np.random.default_rng(5))
-    assert np.array_equal(s.hashes(), oracle_hashes(hosts))
-    img.release()
+    last, arr = None, None
+    for step in range(1, 21):
+        plans = [W.stencil_plan(n, wl.dirty_frac, 77 + 1000 * step + i) for i, n in enumerate(wl.sizes)]
+        for b, plan in zip(bufs, plans):
+            W.stencil_step_(b, plan)
+        img = s.checkpoint(stream_handle())
+        img.wait()
+        arr = image_array(img, arr)
+        b = arr[:img.info()["image_bytes"]]
+        hdr = parse_header(b)
+        if hdr["flags"] & 1:  # every sixth image starts a new chain
+            assert step % 6 == 0 and hdr["n"] == wl.n_pages
+        else:
+            exp = []
+            for a, plan in enumerate(plans):
+                if plan is not None:
+                    _, z0, L = plan
+                    exp.extend((a, p) for p in range(z0 * plane // P, ((z0 + L) * plane - 1) // P + 1))
+            assert page_table(b).tolist() == [list(x) for x in exp]  # in full
+        assert (hdr["flags"] & 1) == (step % 6 == 0)
+        if step in (1, 20):
+            assert oracle.check_image(b) == oracle.OK
+        check_payload_full(b, bufs)
+        if step in (6, 20):
+            assert np.array_equal(s.hashes(), oracle_hashes([x.cpu().numpy() for x in bufs]))
+        del b
+        if last is not None:
+            last.release()
+        last = img
+    expect = [x.clone() for x in bufs]
+    for i, x in enumerate(bufs):
+        W.fill_(x, 555 + i, "u32")
+    s.restore(last, stream_handle())
+    t.cuda.synchronize()
+    assert all(t.equal(x, e) for x, e in zip(bufs, expect))
+    last.release()
     s.destroy()
+    del expect
 
 
 def test_large_4096_allocations_sampled():
     """The 140 GiB / 4,096-allocation footprint: the base image is drained
     without keeping its payload (it exceeds host memory); two incremental
     steps of a seeded 2 % scatter are checked: page table in full, the image
-    checksum by the oracle's checker, sampled payload slots, committed hashes
-    on a seeded sample of pages after each step, and after the last step
-    every committed hash (2.3 million pages) against the oracle's, 8 GiB of
-    the footprint at a time on all host cores."""
+    checksum by the oracle's checker, every payload slot against the pages
+    gathered on the device in 4 KiB blocks (allocation sizes are 4 KiB
+    multiples), committed hashes on a seeded sample of pages after each
+    step, and after the last step every committed hash (2.3 million pages)
+    against the oracle's, 8 GiB of the footprint at a time on all host
+    cores."""
     t = torch()
     free, _ = t.cuda.mem_get_info()
     wl = W.workload("large")
@@ -155,6 +217,8 @@ def test_large_4096_allocations_sampled():
     first = np.cumsum([0] + [W.pages_of(n) for n in wl.sizes])
     page_alloc = np.repeat(np.arange(len(wl.sizes)), np.diff(first))
     page_local = np.arange(wl.n_pages) - first[page_alloc]
+    sizes_np = np.asarray(wl.sizes, dtype=np.int64)
+    assert not (sizes_np % 4096).any()
     k = int(round(wl.dirty_frac * wl.n_pages))
     s = crum.CheckpointSet(staging_bytes=2 * (int(1.5 * k) + 1) * P)
     for b in bufs:
@@ -170,20 +234,24 @@ def test_large_4096_allocations_sampled():
                                               device="cuda")
         img = s.checkpoint(stream_handle())
         img.wait()
-        b = img.to_bytes()
+        b = image_array(img)
         pt = page_table(b)
         assert pt[:, 0].tolist() == page_alloc[chosen].tolist()
         assert pt[:, 1].tolist() == page_local[chosen].tolist()
         assert oracle.check_image(b) == oracle.OK
         h = parse_header(b)
         hashes = s.hashes()
-        for slot in rng.choice(h["n"], size=64, replace=False):
-            a, p = int(pt[slot, 0]), int(pt[slot, 1])
-            lo = int(offs[a]) + p * P
-            n_valid = min(P, int(wl.sizes[a]) - p * P)
-            page = big[lo:lo + n_valid].cpu().numpy()
-            got = np.frombuffer(b, dtype=np.uint8, count=P, offset=h["poff"] + int(slot) * P)
-            assert np.array_equal(got[:n_valid], page)
+        n = h["n"]
+        valid = np.minimum(P, sizes_np[page_alloc[chosen]] - page_local[chosen] * P)
+        cnt = valid // 4096
+        within = np.arange(int(cnt.sum())) - np.repeat(np.cumsum(cnt) - cnt, cnt)
+        src_blk = np.repeat((offs[page_alloc[chosen]] + page_local[chosen] * P) // 4096, cnt) + within
+        dst_blk = np.repeat(np.arange(n) * (P // 4096), cnt) + within
+        exp = t.zeros((n * (P // 4096), 4096), dtype=t.uint8, device="cuda")
+        exp[t.as_tensor(dst_blk, device="cuda")] = big.view(-1, 4096)[t.as_tensor(src_blk, device="cuda")]
+        payload = np.frombuffer(b, dtype=np.uint8, count=n * P, offset=h["poff"])
+        assert np.array_equal(exp.cpu().numpy().reshape(-1), payload)
+        del exp
         for g in rng.choice(wl.n_pages, size=512, replace=False):
             a = int(page_alloc[g])
             lo = int(offs[a]) + int(page_local[g]) * P
