@@ -24,13 +24,33 @@ using dev::hash_vec;
 using dev::ld_stream;
 
 // present[plane][value] for every byte of one 16-byte vector of the slot
-// (several threads may store the same 1; no atomics needed).
-__device__ __forceinline__ void bpd_mark(const uint4& x, BpdSmem& m) {
+// that falls in a plane of `planes` (bit j: plane j); several threads may
+// store the same 1, no atomics needed.
+__device__ __forceinline__ void bpd_mark(const uint4& x, BpdSmem& m, uint32_t planes) {
   const uint32_t w[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
   for (int q = 0; q < 4; ++q)
 #pragma unroll
-    for (int t = 0; t < 4; ++t) m.present[(q & 1) * 4 + t][(w[q] >> (8 * t)) & 255u] = 1;
+    for (int t = 0; t < 4; ++t)
+      if (planes & (1u << ((q & 1) * 4 + t))) m.present[(q & 1) * 4 + t][(w[q] >> (8 * t)) & 255u] = 1;
+}
+
+// After the sample marks: the planes that may still have b < 8 (sample
+// alphabet below kBpdRawAlphabet), into m.open (CTA-wide; leaves the CTA
+// synchronised).  Warp j counts plane j.
+__device__ __forceinline__ void bpd_open_planes(BpdSmem& m) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) m.open = 0;
+  __syncthreads();
+  if (warp < 8) {
+    const uint2 p = reinterpret_cast<const uint2*>(m.present[warp])[lane];
+    // each byte is 0 or 1: the byte sum of a word is its popcount
+    uint32_t c = __popc(p.x) + __popc(p.y);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0 && c < kBpdRawAlphabet) atomicOr(&m.open, 1u << warp);
+  }
+  __syncthreads();
 }
 
 // Alphabet size, width, ranks and section layout of every plane (CTA-wide,
@@ -79,7 +99,16 @@ __global__ void __launch_bounds__(kBpdThreads) k_bpd_size(BpdSizeArgs a) {
       reinterpret_cast<uint32_t*>(m.present)[i] = 0;
     __syncthreads();
     const uint8_t* slot = a.payload + s * kPage;
-    for (uint32_t v = threadIdx.x; v < kPageVecs; v += blockDim.x) bpd_mark(ld_stream(slot + 16ull * v), m);
+    // the sample: the first 8 KiB of the slot (1,024 bytes of every plane)
+    constexpr uint32_t kSampleVecs = kPlaneBytes / 8 * 8 / 16;
+    for (uint32_t v = threadIdx.x; v < kSampleVecs; v += blockDim.x)
+      bpd_mark(ld_stream(slot + 16ull * v), m, 0xffu);
+    __syncthreads();
+    bpd_open_planes(m);
+    const uint32_t open = m.open;
+    if (open != 0)
+      for (uint32_t v = kSampleVecs + threadIdx.x; v < kPageVecs; v += blockDim.x)
+        bpd_mark(ld_stream(slot + 16ull * v), m, open);
     __syncthreads();
     bpd_plan(m);
     if (threadIdx.x == 0) a.enc_len[s] = m.len;
@@ -177,13 +206,30 @@ __global__ void __launch_bounds__(kBpdThreads, 2) k_bpd_encode(BpdEncodeArgs a) 
       w[2 * q] = (static_cast<uint64_t>(x.y) << 32) | x.x;
       w[2 * q + 1] = (static_cast<uint64_t>(x.w) << 32) | x.z;
     }
-    // a byte equal to the one before it in its plane needs no second mark
-    // (float planes holding sign and exponent repeat often)
+    // the sample: each thread's first 4 words (1,024 bytes of every plane,
+    // spread over the slot); a byte equal to the one before it in its plane
+    // needs no second mark (float planes holding sign and exponent repeat
+    // often)
+    constexpr int kSampleWords = 4;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       uint32_t prev = 256u;
 #pragma unroll
-      for (int q = 0; q < 32; ++q) {
+      for (int q = 0; q < kSampleWords; ++q) {
+        const uint32_t x = static_cast<uint32_t>(w[q] >> (8 * j)) & 255u;
+        if (x != prev) m.present[j][x] = 1;
+        prev = x;
+      }
+    }
+    __syncthreads();
+    bpd_open_planes(m);
+    const uint32_t open = m.open;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (!(open & (1u << j))) continue;  // stored as is: no more marks, no ranks
+      uint32_t prev = static_cast<uint32_t>(w[kSampleWords - 1] >> (8 * j)) & 255u;
+#pragma unroll
+      for (int q = kSampleWords; q < 32; ++q) {
         const uint32_t x = static_cast<uint32_t>(w[q] >> (8 * j)) & 255u;
         if (x != prev) m.present[j][x] = 1;
         prev = x;

@@ -38,7 +38,15 @@ struct BpdSmem {
   uint32_t sec[9];  // section offsets in the encoded slot; sec[8] = code length
   uint32_t len;     // encoded length (kPage: stored as is)
   int skip;
+  uint32_t open;    // planes whose sample alphabet left b < 8 possible (bit j)
 };
+
+// A plane holding 129 or more distinct byte values has b = 8 and is stored
+// as is, whatever its other bytes are: an alphabet only grows as bytes are
+// added.  The capture kernels therefore mark a sample of every plane first
+// (1,024 of its 8,192 bytes), and only the planes whose sample alphabet is
+// still at most 128 values are marked in full and ranked.
+constexpr uint32_t kBpdRawAlphabet = 129;
 
 __device__ __forceinline__ uint32_t ceil_log2(uint32_t k) {
   uint32_t b = 0;
