@@ -420,6 +420,11 @@ typedef struct crum_server_config {
                                  captures overlap, so max_checkpoints > 1 keeps the link
                                  busy without sharing it; negative: each drain starts as
                                  soon as its capture is done */
+    int keep_images;          /* 1: a completed checkpoint request keeps a reference
+                                 to its image until crum_server_take_image hands it
+                                 out (or the server is destroyed or its statistics
+                                 reset), so a caller can read every request's image;
+                                 0 (default): the server drops it at completion */
 } crum_server_config;
 
 #define CRUM_REQ_CHECKPOINT 0      /* incremental checkpoint of the client's set */
@@ -474,6 +479,13 @@ crum_status crum_server_submit(crum_server *srv, uint32_t client, int kind, uint
    or ETIMEOUT. */
 crum_status crum_server_wait(crum_server *srv, uint64_t request_id, int stage, int64_t timeout_ns,
                              crum_request_info *info);
+
+/* The image of a completed checkpoint request of a server created with
+   keep_images = 1: *out receives the server's reference to it (the caller
+   releases it with crum_image_release); a second call for the same request
+   is EINVAL.  Errors: EINVAL (unknown, unfinished, failed or restore
+   request, image already taken, or keep_images off). */
+crum_status crum_server_take_image(crum_server *srv, uint64_t request_id, crum_image **out);
 
 /* Wait for every submitted request, then fill *stats (latencies over all
    completed requests since create or the last reset). */

@@ -53,7 +53,8 @@ class Config(ctypes.Structure):
 class ServerConfig(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("staging_budget", ctypes.c_uint64),
                 ("max_inflight", ctypes.c_int), ("max_checkpoints", ctypes.c_int),
-                ("max_restores", ctypes.c_int), ("serialize_drains", ctypes.c_int)]
+                ("max_restores", ctypes.c_int), ("serialize_drains", ctypes.c_int),
+                ("keep_images", ctypes.c_int)]
 
 
 class RequestInfo(ctypes.Structure):
@@ -133,6 +134,7 @@ SIGNATURES = {
     "crum_server_add_client": ([_VP, _VP, _VP, ctypes.POINTER(_U32)], _I),
     "crum_server_submit": ([_VP, _U32, _I, ctypes.POINTER(_U64)], _I),
     "crum_server_wait": ([_VP, _U64, _I, _I64, ctypes.POINTER(RequestInfo)], _I),
+    "crum_server_take_image": ([_VP, _U64, ctypes.POINTER(_VP)], _I),
     "crum_server_drain": ([_VP, ctypes.POINTER(ServerStats)], _I),
     "crum_server_reset_stats": ([_VP], _I),
 }
@@ -346,9 +348,10 @@ class Server:
     """Checkpoint/restore request server (``crum_server``)."""
 
     def __init__(self, device: int = 0, staging_budget: int = 16 << 30, max_inflight: int = 8,
-                 max_checkpoints: int = 0, max_restores: int = 0, serialize_drains: int = 0):
+                 max_checkpoints: int = 0, max_restores: int = 0, serialize_drains: int = 0,
+                 keep_images: int = 0):
         cfg = ServerConfig(device, staging_budget, max_inflight, max_checkpoints, max_restores,
-                           serialize_drains)
+                           serialize_drains, keep_images)
         h = _VP()
         _check(load().crum_server_create(ctypes.byref(cfg), ctypes.byref(h)), "crum_server_create")
         self.handle = h.value
@@ -372,6 +375,13 @@ class Server:
         _check(load().crum_server_wait(self.handle, request_id, stage, t, ctypes.byref(info)),
                "crum_server_wait", allow)
         return info.as_dict()
+
+    def take_image(self, request_id: int) -> Image:
+        """The image of a completed checkpoint request (keep_images=1)."""
+        h = _VP()
+        _check(load().crum_server_take_image(self.handle, request_id, ctypes.byref(h)),
+               "crum_server_take_image")
+        return Image(h.value)
 
     def drain(self) -> dict:
         st = ServerStats()

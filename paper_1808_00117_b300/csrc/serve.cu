@@ -47,7 +47,8 @@ struct Request {
   bool captured = false;
   crum_status status = CRUM_OK;
   Clock::time_point t_submit, t_admit, t_done;
-  crum_image* img = nullptr;  // running checkpoint's image (released at completion)
+  crum_image* img = nullptr;  // running checkpoint's image (released at completion,
+                              // or kept for crum_server_take_image with keep_images)
   cudaEvent_t ev_done = nullptr;  // running restore's completion
   uint64_t region_off = 0, region_len = 0;
   uint64_t n_dirty = 0, bytes = 0, image_seq = 0, checksum = 0;
@@ -167,6 +168,19 @@ void finish(crum_server* S, Request& r, crum_status st) {
   S->t_last = r.t_done;
 }
 
+bool done_failed(crum_status st) { return st != CRUM_OK && st != CRUM_ECOLLISION; }
+
+// Drops the images completed requests still hold (server lock held).
+void drop_kept_images(crum_server* S) {
+  for (auto& kv : S->reqs) {
+    Request& r = kv.second;
+    if (r.state == 2 && r.img != nullptr) {
+      crum_image_release(r.img);
+      r.img = nullptr;
+    }
+  }
+}
+
 // Polls running requests for completion (server lock held).
 void poll_running(crum_server* S) {
   for (size_t i = 0; i < S->running.size();) {
@@ -195,8 +209,10 @@ void poll_running(crum_server* S) {
         r.bytes = info.image_bytes;
         r.image_seq = info.seq;
         r.checksum = info.checksum;
-        crum_image_release(r.img);
-        r.img = nullptr;
+        if (!S->cfg.keep_images || done_failed(st)) {
+          crum_image_release(r.img);
+          r.img = nullptr;
+        }
       }
     }
     if (done) {
@@ -362,6 +378,7 @@ crum_status crum_server_destroy(crum_server* S) {
     S->wake.notify_all();
   }
   if (S->th.joinable()) S->th.join();
+  drop_kept_images(S);
   for (Client& c : S->clients) {
     if (c.newest) crum_image_release(c.newest);
     if (S->sequencer) crum::set_drain_sequencer(c.set, nullptr);
@@ -437,6 +454,22 @@ crum_status crum_server_wait(crum_server* S, uint64_t id, int stage, int64_t tim
   return r.status;
 }
 
+crum_status crum_server_take_image(crum_server* S, uint64_t id, crum_image** out) {
+  if (S == nullptr || out == nullptr) return srv_fail(CRUM_EINVAL, "null server or out");
+  *out = nullptr;
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (!S->cfg.keep_images) return srv_fail(CRUM_EINVAL, "server created without keep_images");
+  auto it = S->reqs.find(id);
+  if (it == S->reqs.end()) return srv_fail(CRUM_EINVAL, "unknown request");
+  Request& r = it->second;
+  if (r.kind == CRUM_REQ_RESTORE) return srv_fail(CRUM_EINVAL, "a restore request has no image");
+  if (r.state != 2) return srv_fail(CRUM_EINVAL, "request not finished");
+  if (r.img == nullptr) return srv_fail(CRUM_EINVAL, "image already taken, or the request failed");
+  *out = r.img;  // the server's reference passes to the caller
+  r.img = nullptr;
+  return CRUM_OK;
+}
+
 crum_status crum_server_drain(crum_server* S, crum_server_stats* st) {
   if (S == nullptr) return srv_fail(CRUM_EINVAL, "null server");
   std::unique_lock<std::mutex> lk(S->mu);
@@ -465,6 +498,7 @@ crum_status crum_server_reset_stats(crum_server* S) {
   if (S == nullptr) return srv_fail(CRUM_EINVAL, "null server");
   std::unique_lock<std::mutex> lk(S->mu);
   S->done_cv.wait(lk, [&] { return S->pending.empty() && S->running.empty(); });
+  drop_kept_images(S);
   S->reqs.clear();
   S->submitted = S->completed = S->failed = S->bytes_ckpt = S->bytes_restored = 0;
   S->lat_all.clear();

@@ -169,3 +169,152 @@ def test_managed_clients_in_the_mix():
     for c in mix:
         assert got[c.idx] == exp[c.idx], f"client {c.idx} ({kinds[c.idx - 20]}) differs from the oracle"
     srv.destroy()
+
+
+# The serving configuration's request mix, scaled to a test: 8 clients with
+# footprints log-uniform 1 MiB..1 GiB (4 KiB granularity, so tail pages are
+# partial; 1.32 GiB in all, the largest 781 MiB), int32/fp32/fp64 data in
+# turn, each request preceded by a rewrite of U[1 %, 50 %] of the client's
+# pages, 80 % checkpoints (every fourth of a client full) and 20 % restores
+# (a restore rolls the rewrite back).
+MIX_SEED = 0x5EED + 30
+MIX_KINDS = ["u32", "fp32", "fp64"]
+
+
+class MixClient:
+    def __init__(self, server, idx, size):
+        t = torch()
+        self.idx, self.size = idx, size
+        self.pages = W.pages_of(size)
+        self.stream = t.cuda.Stream()
+        self.buf = t.empty(size, dtype=t.uint8, device="cuda")
+        W.fill_(self.buf, 6100 + idx, MIX_KINDS[idx % 3])
+        t.cuda.synchronize()
+        self.set = crum.CheckpointSet(external_staging=1, restore_mode=crum.RESTORE_DELTA)
+        self.set.register(self.buf.data_ptr(), size)
+        self.cid = server.add_client(self.set, self.stream.cuda_stream)
+        self.oracle = oracle.OracleSet([size])
+        self.n_ckpt = 0
+        self.state = None
+
+    def host(self):
+        self.stream.synchronize()
+        return self.buf.cpu().numpy().copy()
+
+    def rewrite(self, rnd, frac):
+        k = max(1, int(round(frac * self.pages)))
+        pages = W.choose_uniform(MIX_SEED + 97 * rnd + self.idx, self.pages, k)
+        with torch().cuda.stream(self.stream):
+            W.mutate_pages_(self.buf, pages, MIX_SEED + 131 * rnd + self.idx)
+
+
+def run_mix(server, clients, rounds, plan):
+    """Every round each client rewrites its share of pages and submits its
+    request of that round (they run on the device together).  A checkpoint
+    request's image, taken from the server, must equal the oracle's image of
+    the client's memory at its capture, byte for byte; a restore must bring
+    back the memory of the client's newest checkpoint.  Returns the SHA-256
+    of every image, per client."""
+    import hashlib
+    digests = {c.idx: [] for c in clients}
+    for rnd in range(rounds):
+        ids = []
+        for c in clients:
+            restore, frac = plan[c.idx][rnd]
+            if rnd:
+                c.rewrite(rnd, frac)
+            if restore:
+                kind = crum.REQ_RESTORE
+            else:
+                kind = crum.REQ_CHECKPOINT_FULL if c.n_ckpt % 4 == 0 else crum.REQ_CHECKPOINT
+                c.n_ckpt += 1
+            ids.append((c, kind, server.submit(c.cid, kind)))
+        for c, kind, rid in ids:
+            if kind == crum.REQ_RESTORE:
+                info = server.wait(rid)
+                assert info["status"] == crum.OK
+                assert np.array_equal(c.host(), c.state), f"client {c.idx} restore, round {rnd}"
+                continue
+            server.wait(rid, crum.WAIT_CAPTURED)
+            c.state = c.host()
+            exp, *_ = c.oracle.checkpoint([c.state], full=kind == crum.REQ_CHECKPOINT_FULL)
+            info = server.wait(rid)
+            assert info["status"] == crum.OK and info["checksum"] == int.from_bytes(exp[-8:], "little")
+            img = server.take_image(rid)
+            got = img.to_bytes()
+            img.release()
+            assert got == exp, f"client {c.idx} round {rnd}: image differs from the oracle's"
+            digests[c.idx].append(hashlib.sha256(got).hexdigest())
+    return digests
+
+
+def mix_plan(sizes, rounds):
+    rng = np.random.default_rng(MIX_SEED)
+    plan = {}
+    for i in range(len(sizes)):
+        restore = rng.random(rounds) < 0.2
+        restore[0] = False  # a client's first request is a checkpoint
+        plan[i] = [(bool(r), float(f)) for r, f in zip(restore, rng.uniform(0.01, 0.50, rounds))]
+    return plan
+
+
+@pytest.mark.parametrize("lanes,serial", [((0, 0), 0), ((-1, -1), -1)],
+                         ids=["default_lanes", "unrestricted"])
+def test_config_mix_images_equal_the_oracle_alone_and_in_the_mix(lanes, serial):
+    """The scaled serving mix under a 1.5 GiB staging budget: GiB-sized
+    staging regions, the drain sequencer and long drains.  Every checkpoint
+    image equals the oracle's byte for byte in the mix, and each client run
+    alone through its own server gives the same images."""
+    sizes = W.loguniform_sizes(MIX_SEED, 8, W.MiB, W.GiB, None, round_to=4096)
+    rounds = 6
+    plan = mix_plan(sizes, rounds)
+    budget = 3 << 29
+    srv = crum.Server(staging_budget=budget, max_inflight=8, max_checkpoints=lanes[0],
+                      max_restores=lanes[1], serialize_drains=serial, keep_images=1)
+    mix = [MixClient(srv, i, s) for i, s in enumerate(sizes)]
+    in_mix = run_mix(srv, mix, rounds, plan)
+    stats = srv.drain()
+    assert stats["failed"] == 0 and stats["completed"] == rounds * len(sizes)
+    assert stats["peak_staging"] <= budget and stats["peak_inflight"] >= 2
+    srv.destroy()
+    for c in mix:
+        c.set.destroy()
+    del mix
+    for i, s in enumerate(sizes):
+        srv1 = crum.Server(staging_budget=budget, max_inflight=8, keep_images=1)
+        alone = MixClient(srv1, i, s)
+        got = run_mix(srv1, [alone], rounds, plan)
+        assert got[i] == in_mix[i], f"client {i} alone differs from the mix"
+        srv1.destroy()
+        alone.set.destroy()
+
+
+def test_take_image_rules():
+    """take_image: only with keep_images, only for a finished checkpoint
+    request, and only once."""
+    srv = crum.Server(staging_budget=1 << 28, max_inflight=2, keep_images=1)
+    c = MixClient(srv, 0, 3 * P + 4096)
+    rid = srv.submit(c.cid, crum.REQ_CHECKPOINT)
+    srv.wait(rid)
+    img = srv.take_image(rid)
+    exp, *_ = c.oracle.checkpoint([c.host()])
+    assert img.to_bytes() == exp
+    img.release()
+    with pytest.raises(crum.CrumError):
+        srv.take_image(rid)
+    rr = srv.submit(c.cid, crum.REQ_RESTORE)
+    srv.wait(rr)
+    with pytest.raises(crum.CrumError):
+        srv.take_image(rr)
+    rid2 = srv.submit(c.cid, crum.REQ_CHECKPOINT)
+    srv.wait(rid2)
+    srv.destroy()  # drops the image nobody took
+    c.set.destroy()
+    srv0 = crum.Server(staging_budget=1 << 28, max_inflight=2)
+    c0 = MixClient(srv0, 1, 2 * P)
+    r0 = srv0.submit(c0.cid, crum.REQ_CHECKPOINT)
+    srv0.wait(r0)
+    with pytest.raises(crum.CrumError):
+        srv0.take_image(r0)
+    srv0.destroy()
+    c0.set.destroy()
