@@ -1095,7 +1095,10 @@ def run_e2e_carved(torch, crum, W, bufs, big, wl, page_byte, page_valid, steps, 
         es.register(b.data_ptr(), b.numel())
     turn = [0]
 
-    def upload(j_plan, ev=None):
+    def copy_in(j_plan, ev=None):
+        # the step's new page contents: one pinned host->device copy into a
+        # landing buffer, on the copy stream (once the scatter that last read
+        # that buffer is done)
         idx, _ = plan[j_plan]
         m, j = int(idx.numel()), turn[0]
         turn[0] ^= 1
@@ -1109,11 +1112,19 @@ def run_e2e_carved(torch, crum, W, bufs, big, wl, page_byte, page_valid, steps, 
                 ev[1].record(copy_stream)
             landed = torch.cuda.Event()
             landed.record(copy_stream)
+        return idx, m, j, landed
+
+    def scatter(c):
+        # on the application's stream: into place, 4 KiB blocks
+        idx, m, j, landed = c
         stream.wait_event(landed)
         blocks.index_copy_(0, idx, landing[j][:m])
         scattered[j] = torch.cuda.Event()
         scattered[j].record(stream)
         return m * BLK
+
+    def upload(j_plan, ev=None):
+        return scatter(copy_in(j_plan, ev))
 
     def finish(im, infos):
         im.wait()
@@ -1128,6 +1139,11 @@ def run_e2e_carved(torch, crum, W, bufs, big, wl, page_byte, page_valid, steps, 
         im.release()
 
     def timed(first, pipelined):
+        # pipelined: the copy of step k+1's pages is issued before step k's
+        # checkpoint call, which returns only once the hash pass is done when
+        # staging cannot hold every page of the set, so the link carries that
+        # copy while step k is captured and step k-1 drains; two images stay
+        # in flight.  Serial: each step waits for its image first.
         h2d, infos, ev = [], [], []
         for warm in range(2):
             upload(first + warm)
@@ -1136,10 +1152,20 @@ def run_e2e_carved(torch, crum, W, bufs, big, wl, page_byte, page_valid, steps, 
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         pending = []
+        pair = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        nxt = None
         for step in range(e_steps):
-            u = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-            h2d.append(upload(first + 2 + step, u))
-            ev.append(u)
+            if nxt is None:
+                u = pair()
+                cur = (copy_in(first + 2 + step, u), u)
+            else:
+                cur = nxt
+            nxt = None
+            if pipelined and step + 1 < e_steps:
+                u = pair()
+                nxt = (copy_in(first + 3 + step, u), u)
+            ev.append(cur[1])
+            h2d.append(scatter(cur[0]))
             pending.append(es.checkpoint(sh))
             while len(pending) > (2 if pipelined else 0):
                 finish(pending.pop(0), infos)
@@ -1160,8 +1186,9 @@ def run_e2e_carved(torch, crum, W, bufs, big, wl, page_byte, page_valid, steps, 
             "d2h_bytes_per_step": int(statistics.mean(i["image_bytes"] for i in infos)),
             "ms_per_step": round(dt * 1e3 / e_steps, 3), "steps": e_steps,
             "what": "pinned H2D of the step's new page contents (copy stream, two landing "
-                    "buffers) + device scatter of 4 KiB blocks + crum_checkpoint (memory sink) + "
-                    "image read back (PERSISTED); two images in flight",
+                    "buffers; step k+1's copy issued before step k's checkpoint call) + device "
+                    "scatter of 4 KiB blocks + crum_checkpoint (memory sink) + image read back "
+                    "(PERSISTED); two images in flight",
             "submit_to_persisted_ms": round(statistics.mean(i["t_persisted_ms"] for i in infos), 3),
             "upload_ms": round(up_ms, 3),
             "serial": {"value": per(dt_s), "ms_per_step": round(dt_s * 1e3 / e_steps, 3),
@@ -1409,7 +1436,10 @@ def run_batched(args):
         line["config"]["l2"] = (f"inputs ({S / 2**30:g} GiB) larger than L2 (126 MB); no flush")
         line["config"]["value_def"] = ("footprint bytes / capture-kernel device time "
                                        "(hash+scan+gather)")
-        line["config"]["capture_launch"] = "cuda graph" if args.graph else "one launch per op"
+        line["config"]["capture_launch"] = (
+            ("cuda graph" if args.graph else "one launch per op") if staging // 2 // W.PAGE >= n_pages
+            else "chunked: staging halves hold 1.5x a step's dirty pages, so the call waits for "
+                 "the dirty count after the hash pass and launches the gather itself")
         line["config"]["parallelism"] = f"replica per GPU x{world}"
         line["capture"]["frac_of_hbm"] = round(S / (statistics.mean(cap_ms) * 1e-3) / 1e9
                                                / peaks["hbm_gbs"], 4)
@@ -1489,12 +1519,16 @@ def run_serving(args):
     short) and 20 % restores of the client's newest chain, each checkpoint
     and each restore preceded by the client rewriting U[1 %, 50 %] of its
     pages (a restore rolls them back: delta restores copy the pages that
-    differ).  Runs:
-    plain sequential form (one request on the device at a time) saturated,
-    which gives its service rate mu; then Poisson arrivals at 0.8 mu through
-    the sequential form and through continuous batching (8 slots, 16 GiB
-    staging budget); then batching saturated.  One driver thread per client
-    replays that client's requests at their arrival times."""
+    differ).  For each of 3 seeds (request mix and arrival times):
+    the sequential form of the server (one request on the device at a time)
+    saturated gives its service rate mu; then Poisson arrivals at 0.8 mu
+    through the sequential form, through continuous batching (8 slots,
+    16 GiB staging budget; two lane settings) and through the plain form
+    (one request at a time: synchronize, then copy the client's whole
+    footprint device->host for a checkpoint or host->device for a restore,
+    the paper's naive capture, Section 3.4).  Then batching and the plain
+    form saturated.  One driver thread per client replays that client's
+    requests at their arrival times."""
     import threading
     import torch
     import paper_1808_00117_b300 as crum
@@ -1505,10 +1539,6 @@ def run_serving(args):
     n_clients, n_req = 32, args.requests
     sizes = W.workload("serving").sizes
     kinds = ["i32", "fp32", "fp64"]
-    rng = np.random.default_rng(0x5EED + 3)
-    req_client = rng.integers(0, n_clients, size=n_req)
-    req_restore = rng.random(n_req) < 0.2
-    req_frac = rng.uniform(0.01, 0.50, size=n_req)
     budget = 16 << 30
 
     class C:
@@ -1529,7 +1559,28 @@ def run_serving(args):
                                    restore_mode=crum.RESTORE_DELTA)
         c.set.register(c.buf.data_ptr(), c.size)
 
-    def run(max_inflight, rate_hz, label, max_ckpt=0, max_rest=0, serial=0):
+    def requests(seed):
+        rng = np.random.default_rng(0x5EED + 3 + 1000 * seed)
+        return (rng.integers(0, n_clients, size=n_req), rng.random(n_req) < 0.2,
+                rng.uniform(0.01, 0.50, size=n_req))
+
+    def arrivals(seed, rate_hz):
+        gaps = (np.random.default_rng(17 + seed).exponential(1.0 / rate_hz, size=n_req)
+                if rate_hz else np.zeros(n_req))
+        return np.cumsum(gaps)
+
+    def summary(label, lat_all, lat_ck, lat_rs, wall_s, bytes_ck, extra=None):
+        out = {"label": label, "completed": len(lat_all),
+               "throughput_req_s": round(len(lat_all) / wall_s, 2),
+               "checkpointed_gbs": round(bytes_ck / wall_s / 1e9, 2),
+               "p50_ms": round(pct(lat_all, 50), 3), "p99_ms": round(pct(lat_all, 99), 3),
+               "p50_ckpt_ms": round(pct(lat_ck, 50), 3), "p99_ckpt_ms": round(pct(lat_ck, 99), 3),
+               "p50_restore_ms": round(pct(lat_rs, 50), 3), "p99_restore_ms": round(pct(lat_rs, 99), 3)}
+        out.update(extra or {})
+        return out
+
+    def run(seed, max_inflight, rate_hz, label, max_ckpt=0, max_rest=0, serial=0):
+        req_client, req_restore, req_frac = requests(seed)
         srv = crum.Server(staging_budget=budget, max_inflight=max_inflight,
                           max_checkpoints=max_ckpt, max_restores=max_rest, serialize_drains=serial)
         for c in clients:
@@ -1540,8 +1591,7 @@ def run_serving(args):
             srv.wait(srv.submit(c.cid, crum.REQ_CHECKPOINT_FULL))
             c.n_ckpt = 1
         srv.reset_stats()
-        gaps = np.random.default_rng(17).exponential(1.0 / rate_hz, size=n_req) if rate_hz else np.zeros(n_req)
-        arrivals = np.cumsum(gaps)
+        arr = arrivals(seed, rate_hz)
         per_client = [[] for _ in clients]
         for r in range(n_req):
             per_client[req_client[r]].append(r)
@@ -1552,7 +1602,7 @@ def run_serving(args):
             c = clients[ci]
             last = None
             for r in per_client[ci]:
-                delay = t0 + arrivals[r] - time.perf_counter()
+                delay = t0 + arr[r] - time.perf_counter()
                 if delay > 0:
                     time.sleep(delay)
                 if last is not None:  # the client's consistency rule
@@ -1578,8 +1628,8 @@ def run_serving(args):
             t.join()
         st = srv.drain()
         wall_s = st["wall_ms"] * 1e-3
-        out = {"label": label, "max_inflight": max_inflight, "max_checkpoints": max_ckpt,
-               "max_restores": max_rest, "serialize_drains": serial,
+        out = {"label": label, "seed": seed, "max_inflight": max_inflight,
+               "max_checkpoints": max_ckpt, "max_restores": max_rest, "serialize_drains": serial,
                "arrival_rate_hz": None if not rate_hz else round(rate_hz, 2),
                "completed": st["completed"], "failed": st["failed"],
                "throughput_req_s": round(st["completed"] / wall_s, 2),
@@ -1592,34 +1642,82 @@ def run_serving(args):
         srv.destroy()
         return out
 
+    # the plain form's host images: one pinned buffer per client
+    plain_host = [torch.empty(c.size, dtype=torch.uint8, pin_memory=True) for c in clients]
+
+    def run_plain(seed, rate_hz, label):
+        """One request at a time in arrival order: the client's rewrite, a
+        device synchronize, then the whole footprint copied across the link
+        (device->host for a checkpoint, host->device for a restore)."""
+        req_client, req_restore, req_frac = requests(seed)
+        for c, h in zip(clients, plain_host):  # warm-up: every client's first image
+            h.copy_(c.buf)
+        torch.cuda.synchronize()
+        arr = arrivals(seed, rate_hz)
+        t0 = time.perf_counter() + 0.05
+        lat_all, lat_ck, lat_rs, bytes_ck = [], [], [], 0
+        for r in range(n_req):
+            ci = int(req_client[r])
+            c, h = clients[ci], plain_host[ci]
+            delay = t0 + arr[r] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            k = max(1, int(round(req_frac[r] * c.pages)))
+            pages = W.choose_uniform(int(r) * 31 + ci, c.pages, k)
+            with torch.cuda.stream(c.stream):
+                W.mutate_pages_(c.buf, pages, int(r))
+            torch.cuda.synchronize()
+            if req_restore[r]:
+                c.buf.copy_(h)
+            else:
+                h.copy_(c.buf)
+                bytes_ck += c.size
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - (t0 + arr[r])) * 1e3
+            lat_all.append(ms)
+            (lat_rs if req_restore[r] else lat_ck).append(ms)
+        wall_s = time.perf_counter() - t0 - (arr[0] if rate_hz else 0.0)
+        return summary(label, lat_all, lat_ck, lat_rs, wall_s, bytes_ck,
+                       {"seed": seed, "arrival_rate_hz": None if not rate_hz else round(rate_hz, 2),
+                        "what": "plain form: synchronize + whole-footprint copy per request"})
+
     launches0 = crum.kernel_launches()
-    seq_sat = run(1, 0, "sequential, saturated", serial=-1)
-    mu = seq_sat["throughput_req_s"]
-    lam = 0.8 * mu
-    seq = run(1, lam, "sequential, Poisson 0.8 mu", serial=-1)
-    lanes = ((-1, -1, -1), (2, 1, -1), (1, 1, -1), (3, 2, -1), (2, 1, 1), (3, 1, 1))
-    sweep = [run(8, lam, f"batched {c}/{r}{' serialized drains' if q > 0 else ''}, Poisson 0.8 mu", c, r, q)
-             for c, r, q in lanes]
-    bat = min(sweep, key=lambda x: x["p99_ms"])
-    bat_sat = run(8, 0, "batched, saturated", bat["max_checkpoints"], bat["max_restores"],
-                  bat["serialize_drains"])
-    # the other policy saturated too, for comparison at equal load
-    alt = (1, 1, -1) if bat["serialize_drains"] > 0 else (2, 1, 1)
-    alt_sat = run(8, 0, f"batched {alt[0]}/{alt[1]}{' serialized drains' if alt[2] > 0 else ''}, saturated",
-                  *alt)
+    runs, per_seed = [], []
+    for seed in range(3):
+        seq_sat = run(seed, 1, 0, "sequential, saturated", serial=-1)
+        lam = 0.8 * seq_sat["throughput_req_s"]
+        seq = run(seed, 1, lam, "sequential, Poisson 0.8 mu", serial=-1)
+        bat_s = run(seed, 8, lam, "batched 2/1 serialized drains, Poisson 0.8 mu", 2, 1, 1)
+        bat_u = run(seed, 8, lam, "batched 1/1, Poisson 0.8 mu", 1, 1, -1)
+        plain = run_plain(seed, lam, "plain, Poisson 0.8 mu")
+        runs += [seq_sat, seq, bat_s, bat_u, plain]
+        best = min((bat_s, bat_u), key=lambda x: x["p99_ms"])
+        per_seed.append({"seed": seed, "lambda_req_s": round(lam, 2),
+                         "p50_ms": {"plain": plain["p50_ms"], "sequential": seq["p50_ms"],
+                                    "batched_serialized": bat_s["p50_ms"], "batched_1_1": bat_u["p50_ms"]},
+                         "p99_ms": {"plain": plain["p99_ms"], "sequential": seq["p99_ms"],
+                                    "batched_serialized": bat_s["p99_ms"], "batched_1_1": bat_u["p99_ms"]},
+                         "batched_p99_below_plain": best["p99_ms"] < plain["p99_ms"],
+                         "batched_p99_below_sequential": best["p99_ms"] < seq["p99_ms"]})
+    bat_sat = run(0, 8, 0, "batched 2/1 serialized drains, saturated", 2, 1, 1)
+    alt_sat = run(0, 8, 0, "batched 1/1, saturated", 1, 1, -1)
+    plain_sat = run_plain(0, 0, "plain, saturated")
+    seq_sat0 = runs[0]
+    runs += [bat_sat, alt_sat, plain_sat]
     line = {
         "metric": METRIC, "value": bat_sat["checkpointed_gbs"], "unit": UNIT, "n_gpus": 1,
         "steps": n_req, "warmup": n_clients, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": "serving", "clients": n_clients, "requests": n_req,
                    "footprint_bytes": int(sum(sizes)), "staging_budget": budget,
-                   "restore_share": 0.2, "dirty": "U[1%,50%] per checkpoint request",
+                   "restore_share": 0.2, "dirty": "U[1%,50%] per request", "seeds": 3,
                    "value_def": "footprint bytes checkpointed per second, batched saturated"},
-        "runs": [seq_sat, seq] + sweep + [bat_sat, alt_sat],
-        "batched_vs_sequential_at_lambda": {
-            "p50_speedup": round(seq["p50_ms"] / bat["p50_ms"], 3),
-            "p99_speedup": round(seq["p99_ms"] / bat["p99_ms"], 3)},
-        "saturated_throughput_gain": round(bat_sat["throughput_req_s"] / seq_sat["throughput_req_s"], 3),
+        "per_seed": per_seed,
+        "runs": runs,
+        "saturated_throughput_req_s": {"plain": plain_sat["throughput_req_s"],
+                                       "sequential": seq_sat0["throughput_req_s"],
+                                       "batched_serialized": bat_sat["throughput_req_s"],
+                                       "batched_1_1": alt_sat["throughput_req_s"]},
         "gpu_launches": int(crum.kernel_launches() - launches0),
     }
     for c in clients:
