@@ -4,60 +4,111 @@ The paper checkpoints MPI applications by quiescing every rank and the
 network before the per-process checkpoints are taken (Section 3.3: each MPI
 process drains its GPU and a child of each process writes the image;
 Section 4.5: quiescing and draining in-flight messages cost 0.01 % of the
-total).  On
-this path each rank checkpoints its own registered set, so a cut needs only
-host coordination: every rank stops sending, meets the others at a barrier,
-then submits its checkpoint; the images' sequence numbers name the cut, and
-all ranks must agree on it (a rank that skipped or repeated a checkpoint is
-out of step and the cut is refused on every rank).  Restoring a cut is the
-same: a barrier, each rank's restore, a barrier.
+total).  On this path each rank checkpoints its own registered set, so a
+cut needs only host coordination: every rank stops sending, meets the
+others at a barrier, then takes its checkpoint; an all-gather of each
+rank's cut number and outcome decides, identically on every rank, whether
+the cut stands.  Restoring a cut is the same: an agreement that every rank
+holds an image of that cut, a barrier, each rank's restore, a barrier.
+
+Rules (the same decision on every rank, from the gathered values only):
+
+* A cut stands when every rank is at the same cut number and every rank's
+  checkpoint call succeeded (the image was queued; its capture is the
+  rank's consistency point).  The cut is named by that number; each rank
+  keeps its own image of it.
+* Otherwise the cut is refused on every rank.  Each rank drops its handle of
+  the refused cut's image.  An image that was captured stays a link of its
+  rank's chain (it holds that rank's state at that moment, so restoring a
+  later cut through it is exact); a rank whose checkpoint failed gets a full
+  image at its next checkpoint when the library marked its set so (a failed
+  capture does).
+* Cut numbers continue from one past the largest any rank held, so ranks
+  that were out of step (one a cut ahead) are in step for the next cut.
 
 Host logic only (torch.distributed); the device work is each rank's own
 crum_checkpoint / crum_restore.
 """
 from __future__ import annotations
 
-from typing import Any, Optional
+from typing import Any, Dict, Optional
 
-__all__ = ["CutError", "checkpoint_cut", "restore_cut"]
+__all__ = ["CutError", "CutCoordinator"]
 
 
 class CutError(RuntimeError):
     pass
 
 
-def _gather_int(value: int, group) -> list:
+def _gather(values, group) -> list:
     import torch
     import torch.distributed as dist
     world = dist.get_world_size(group)
-    t = torch.tensor([value], dtype=torch.int64)
-    out = [torch.zeros(1, dtype=torch.int64) for _ in range(world)]
+    t = torch.tensor(list(values), dtype=torch.int64)
+    out = [torch.zeros(len(values), dtype=torch.int64) for _ in range(world)]
     dist.all_gather(out, t, group=group)
-    return [int(x.item()) for x in out]
+    return [[int(v) for v in x.tolist()] for x in out]
 
 
-def checkpoint_cut(cset: Any, stream: int, flags: int = 0, group: Optional[Any] = None):
-    """Barrier, then this rank's checkpoint.  Returns (image, cut) where cut
-    is the image sequence number every rank agreed on.  Raises CutError (on
-    every rank) if the ranks' sequence numbers differ."""
-    import torch.distributed as dist
-    dist.barrier(group)
-    img = cset.checkpoint(stream, flags)
-    seq = int(img.info()["seq"])
-    seqs = _gather_int(seq, group)
-    if len(set(seqs)) != 1:
-        raise CutError(f"ranks are at different checkpoints: {seqs}")
-    return img, seq
+class CutCoordinator:
+    """One rank's side of the cut protocol over its checkpoint set.
 
+    `cset` needs ``checkpoint(stream, flags) -> image`` and
+    ``restore(image, stream)``; images need ``info() -> {"seq": ...}`` and
+    ``release()``."""
 
-def restore_cut(cset: Any, image: Any, stream: int, group: Optional[Any] = None) -> int:
-    """Every rank restores its image of the same cut.  Returns the cut."""
-    import torch.distributed as dist
-    seq = int(image.info()["seq"])
-    seqs = _gather_int(seq, group)
-    if len(set(seqs)) != 1:
-        raise CutError(f"ranks would restore different cuts: {seqs}")
-    dist.barrier(group)
-    cset.restore(image, stream)
-    dist.barrier(group)
-    return seq
+    def __init__(self, cset: Any, group: Optional[Any] = None, first_cut: int = 0):
+        self.cset = cset
+        self.group = group
+        self.next_cut = first_cut
+        self.images: Dict[int, Any] = {}   # cut number -> this rank's image
+        self.seqs: Dict[int, list] = {}    # cut number -> every rank's image seq
+
+    def checkpoint(self, stream: int, flags: int = 0):
+        """Barrier, this rank's checkpoint, agreement.  Returns (image, cut
+        number); raises CutError on every rank when the cut is refused."""
+        import torch.distributed as dist
+        dist.barrier(self.group)
+        img, err = None, ""
+        try:
+            img = self.cset.checkpoint(stream, flags)
+        except Exception as e:  # the rank reports the failure instead of leaving
+            err = str(e)
+        seq = int(img.info()["seq"]) if img is not None else -1
+        rows = _gather([self.next_cut, int(img is not None), seq], self.group)
+        cuts = [r[0] for r in rows]
+        ok = len(set(cuts)) == 1 and all(r[1] for r in rows)
+        self.next_cut = max(cuts) + 1
+        if not ok:
+            if img is not None:
+                img.release()
+            why = (f"ranks are at different cuts: {cuts}" if len(set(cuts)) != 1 else
+                   f"checkpoint failed on ranks {[i for i, r in enumerate(rows) if not r[1]]}")
+            raise CutError(why + (f" (this rank: {err})" if err else ""))
+        cut = cuts[0]
+        self.images[cut] = img
+        self.seqs[cut] = [r[2] for r in rows]
+        return img, cut
+
+    def restore(self, cut: int, stream: int, wait=None) -> int:
+        """Every rank restores its image of cut `cut`; refused on every rank
+        unless all ranks hold one.  `wait` (a callable, e.g. a stream
+        synchronize) runs after the stream-ordered restore is queued and
+        before the closing barrier, so that the barrier means every rank's
+        memory is back."""
+        import torch.distributed as dist
+        mine = self.images.get(cut)
+        rows = _gather([cut, int(mine is not None)], self.group)
+        if len({r[0] for r in rows}) != 1 or not all(r[1] for r in rows):
+            raise CutError(f"not every rank holds an image of cut {cut}: {rows}")
+        dist.barrier(self.group)
+        self.cset.restore(mine, stream)
+        if wait is not None:
+            wait()
+        dist.barrier(self.group)
+        return cut
+
+    def release(self) -> None:
+        for img in self.images.values():
+            img.release()
+        self.images.clear()

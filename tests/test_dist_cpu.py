@@ -54,20 +54,31 @@ def test_single_rank_needs_no_process_group():
 class _FakeImage:
     def __init__(self, seq):
         self.seq = seq
+        self.released = False
 
     def info(self):
         return {"seq": self.seq}
+
+    def release(self):
+        self.released = True
 
 
 class _FakeSet:
     """Host stand-in for a rank's CheckpointSet (the cut logic is host-only)."""
 
-    def __init__(self, skip_first=False):
-        self.seq = 1 if skip_first else 0
+    def __init__(self, fail_at=()):
+        self.seq = 0
+        self.calls = 0
+        self.fail_at = set(fail_at)
         self.restored = None
+        self.taken = []
 
     def checkpoint(self, stream, flags=0):
+        self.calls += 1
+        if self.calls in self.fail_at:
+            raise RuntimeError("injected checkpoint failure")
         img = _FakeImage(self.seq)
+        self.taken.append(img)
         self.seq += 1
         return img
 
@@ -75,41 +86,66 @@ class _FakeSet:
         self.restored = image.seq
 
 
-def _cut_worker(rank, world, port, out, skew):
+def _cut_worker(rank, world, port, out, mode):
     import sys
     sys.path.insert(0, ROOT)
     import torch.distributed as dist
     from paper_1808_00117_b300 import cut
     dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
                             world_size=world)
-    s = _FakeSet(skip_first=skew and rank == 1)
+    # "skew": rank 1 believes it is one cut ahead; "fail": rank 1's second
+    # checkpoint raises
+    s = _FakeSet(fail_at=(2,) if mode == "fail" and rank == 1 else ())
+    co = cut.CutCoordinator(s, first_cut=1 if mode == "skew" and rank == 1 else 0)
     res = []
-    for _ in range(2):
+    for _ in range(3):
         try:
-            img, c = cut.checkpoint_cut(s, 0)
-            res.append(("ok", c))
-        except cut.CutError as e:
-            res.append(("refused", str(e)))
-    try:
-        res.append(("restored", cut.restore_cut(s, _FakeImage(0), 0), s.restored))
-    except cut.CutError:
-        res.append(("restore refused",))
+            img, c = co.checkpoint(0)
+            res.append(("ok", c, img.seq))
+        except cut.CutError:
+            res.append(("refused",))
+    res.append(("released", [img.released for img in s.taken]))
+    ok_cuts = sorted(co.images)
+    for c in (ok_cuts[0], 99):
+        try:
+            res.append(("restored", co.restore(c, 0), s.restored))
+        except cut.CutError:
+            res.append(("restore refused", c))
+    res.append(("seqs", {k: v for k, v in co.seqs.items()}))
     out[rank] = res
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("skew", [False, True])
-def test_consistent_cut_two_ranks(skew):
-    """In step, both ranks agree on cuts 0 and 1 and restore cut 0; a rank
-    that is one checkpoint ahead makes every rank refuse each cut."""
+@pytest.mark.parametrize("mode", ["in_step", "skew", "fail"])
+def test_consistent_cut_two_ranks(mode):
+    """In step: cuts 0, 1, 2 stand on both ranks.  Skew (rank 1 one cut
+    ahead): the first cut is refused on both ranks, each drops the image it
+    took, and both continue in step from cut 2.  Fail (rank 1's second
+    checkpoint raises): that cut is refused on both ranks, the rank that did
+    capture drops its image, and the next cut stands.  A restore of a cut
+    every rank holds runs everywhere; of one nobody holds, is refused
+    everywhere."""
     port = _free_port()
     with mp.Manager() as m:
         out = m.dict()
-        mp.spawn(_cut_worker, args=(2, port, out, skew), nprocs=2, join=True)
+        mp.spawn(_cut_worker, args=(2, port, out, mode), nprocs=2, join=True)
         res = dict(out)
     for r in (0, 1):
-        if not skew:
-            assert res[r] == [("ok", 0), ("ok", 1), ("restored", 0, 0)]
+        got = res[r]
+        if mode == "in_step":
+            assert got[:3] == [("ok", 0, 0), ("ok", 1, 1), ("ok", 2, 2)]
+            assert got[3] == ("released", [False, False, False])
+            assert got[4] == ("restored", 0, 0)
+        elif mode == "skew":
+            assert got[:3] == [("refused",), ("ok", 2, 1), ("ok", 3, 2)]
+            assert got[3] == ("released", [True, False, False])
+            assert got[4] == ("restored", 2, 1)
+            assert got[6] == ("seqs", {2: [1, 1], 3: [2, 2]})
         else:
-            assert [x[0] for x in res[r][:2]] == ["refused", "refused"]
-            assert res[r][2] == ("restored", 0, 0)
+            assert got[0] == ("ok", 0, 0) and got[1] == ("refused",)
+            # rank 0 captured at the refused cut; its image stays in its
+            # chain, so its sequence number runs one ahead of rank 1's
+            assert got[2] == ("ok", 2, 2 if r == 0 else 1)
+            assert got[3] == ("released", [False, True, False] if r == 0 else [False, False])
+            assert got[6] == ("seqs", {0: [0, 0], 2: [2, 1]})
+        assert got[5] == ("restore refused", 99)
