@@ -5,12 +5,14 @@ allocator hook or CUDA-call interposer that must not re-enter the
 allocator).  Its scratch is a fixed device array inside the library.
 
 Checked through the C ABI against the regular path (crum_checkpoint's page
-table and the set's committed hashes) on calls made back to back, so the
-second call runs over what the first left in the shared scratch.  The file
+table and the set's committed hashes) and against the oracle (its page
+hashes and dirty rule) on calls made back to back, so the second call runs
+over what the first left in the shared scratch.  The file
 name makes pytest collect it last."""
 import numpy as np
 import pytest
 
+import oracle
 import paper_1808_00117_b300 as crum
 from paper_1808_00117_b300 import workloads as W
 
@@ -52,10 +54,18 @@ def test_static_matches_checkpoint_on_consecutive_calls():
     # call 1: full listing, hashes from zero
     img0 = s.checkpoint(stream_handle())
     img0.wait()
+    h_prev = np.zeros(n, dtype=np.uint64)
     got_pages, c = _static_call(buf, hashes, full=True)
     exp_pages = page_table(img0.to_bytes())[:, 1].astype(np.int64)
     assert c == n and np.array_equal(got_pages, exp_pages)
     assert np.array_equal(hashes.cpu().numpy().view(np.uint64), s.hashes())
+    # and against the oracle directly: its page hashes and its dirty rule
+    host = buf.cpu().numpy()
+    h_exp = oracle.hash_all([host])
+    assert np.array_equal(hashes.cpu().numpy().view(np.uint64), h_exp)
+    d_exp, _ = oracle.dirty(h_exp, h_prev, None, True)
+    assert np.array_equal(got_pages, np.flatnonzero(d_exp))
+    h_prev = h_exp
 
     # call 2, straight after: incremental over the scratch call 1 left behind
     W.mutate_pages_(buf, W.choose_uniform(5, n, 97), 6)
@@ -66,6 +76,11 @@ def test_static_matches_checkpoint_on_consecutive_calls():
     assert c == img1.info()["n_dirty"] == 97
     assert np.array_equal(got_pages, exp_pages)
     assert np.array_equal(hashes.cpu().numpy().view(np.uint64), s.hashes())
+    host = buf.cpu().numpy()
+    h_exp = oracle.hash_all([host])
+    assert np.array_equal(hashes.cpu().numpy().view(np.uint64), h_exp)
+    d_exp, _ = oracle.dirty(h_exp, h_prev, None, False)
+    assert np.array_equal(got_pages, np.flatnonzero(d_exp))
 
     # call 3: nothing changed, nothing listed
     _, c = _static_call(buf, hashes, full=False)
