@@ -27,12 +27,73 @@ using dev::ld_stream;
 // that falls in a plane of `planes` (bit j: plane j); several threads may
 // store the same 1, no atomics needed.
 __device__ __forceinline__ void bpd_mark(const uint4& x, BpdSmem& m, uint32_t planes) {
-  const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+  const uint32_t w[4] = {tslot4(x.x), tslot4(x.y), tslot4(x.z), tslot4(x.w)};
 #pragma unroll
   for (int q = 0; q < 4; ++q)
 #pragma unroll
     for (int t = 0; t < 4; ++t)
       if (planes & (1u << ((q & 1) * 4 + t))) m.present[(q & 1) * 4 + t][(w[q] >> (8 * t)) & 255u] = 1;
+}
+
+// 4 x 4 byte transpose: o_c gets byte c of a0, a1, a2, a3 (in that order).
+__device__ __forceinline__ void transpose4(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                           uint32_t& o0, uint32_t& o1, uint32_t& o2, uint32_t& o3) {
+  const uint32_t t0 = __byte_perm(a0, a1, 0x5140), t1 = __byte_perm(a0, a1, 0x7362);
+  const uint32_t t2 = __byte_perm(a2, a3, 0x5140), t3 = __byte_perm(a2, a3, 0x7362);
+  o0 = __byte_perm(t0, t2, 0x5410);
+  o1 = __byte_perm(t0, t2, 0x7632);
+  o2 = __byte_perm(t1, t3, 0x5410);
+  o3 = __byte_perm(t1, t3, 0x7632);
+}
+
+// Starts the asynchronous copy of one 64 KiB slot into the encoder's
+// swizzled shared-memory layout (enc_chunk_pos): each thread copies 16
+// chunks of 16 bytes, a warp's copies covering 512 contiguous bytes each.
+// The caller waits for it with cp.async.wait_all and a barrier.
+__device__ __forceinline__ void enc_prefetch(const uint8_t* slot, uint4* slot_sm, int tid) {
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const uint32_t v = tid + 256u * i;
+    const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(slot_sm + enc_chunk_pos(v >> 4, v & 15u)));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(slot + 16ull * v) : "memory");
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+// Presence marks of the four plane bytes in w (several threads may store
+// the same 1).
+__device__ __forceinline__ void mark4(uint8_t* present, uint32_t w) {
+  const uint32_t t = tslot4(w);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) present[(t >> (8 * i)) & 255u] = 1;
+}
+
+// This thread's 32 bytes of a plane (pw) as B-bit ranks, LSB first: exactly
+// B words at `words`.  B is a template argument, so every rank's bit
+// position is known at compile time.
+template <int B>
+__device__ __forceinline__ void pack_ranks(const uint32_t (&pw)[8], const uint8_t* rank, uint32_t* words) {
+  uint32_t out[B];
+#pragma unroll
+  for (int e = 0; e < B; ++e) out[e] = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const uint32_t t = tslot4(pw[k]);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint32_t r = rank[(t >> (8 * i)) & 255u];
+      const int bit = (4 * k + i) * B;  // a constant once unrolled
+      out[bit >> 5] |= r << (bit & 31);
+      if ((bit & 31) + B > 32) out[(bit >> 5) + 1] |= r >> (32 - (bit & 31));
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < B; ++e) words[e] = out[e];
+}
+
+__device__ __forceinline__ void plane_words(const uint32_t (&p)[8], uint32_t (&pw)[8]) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) pw[k] = p[k];
 }
 
 // After the sample marks: the planes that may still have b < 8 (sample
@@ -60,7 +121,7 @@ __device__ void bpd_plan(BpdSmem& m) {
   if (warp < 8) {
     uint32_t c = 0;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) c += m.present[warp][lane * 8 + j];
+    for (int j = 0; j < 8; ++j) c += m.present[warp][tslot(lane * 8 + j)];
     uint32_t incl = c;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -70,8 +131,8 @@ __device__ void bpd_plan(BpdSmem& m) {
     uint32_t r = incl - c;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      m.rank[warp][lane * 8 + j] = static_cast<uint8_t>(r);
-      r += m.present[warp][lane * 8 + j];
+      m.rank[warp][tslot(lane * 8 + j)] = static_cast<uint8_t>(r);
+      r += m.present[warp][tslot(lane * 8 + j)];
     }
     if (lane == 31) {
       m.k[warp] = incl;
@@ -99,16 +160,31 @@ __global__ void __launch_bounds__(kBpdThreads) k_bpd_size(BpdSizeArgs a) {
       reinterpret_cast<uint32_t*>(m.present)[i] = 0;
     __syncthreads();
     const uint8_t* slot = a.payload + s * kPage;
-    // the sample: the first 8 KiB of the slot (1,024 bytes of every plane)
-    constexpr uint32_t kSampleVecs = kPlaneBytes / 8 * 8 / 16;
-    for (uint32_t v = threadIdx.x; v < kSampleVecs; v += blockDim.x)
-      bpd_mark(ld_stream(slot + 16ull * v), m, 0xffu);
+    // the sample: the first 8 KiB of the slot (1,024 bytes of every plane),
+    // two vectors per thread, both loads in flight before the marks
+    static_assert(kPlaneBytes / 16 == 2 * kBpdThreads, "sample = two vectors per thread");
+    {
+      const uint4 x0 = ld_stream(slot + 16ull * threadIdx.x);
+      const uint4 x1 = ld_stream(slot + 16ull * (threadIdx.x + kBpdThreads));
+      bpd_mark(x0, m, 0xffu);
+      bpd_mark(x1, m, 0xffu);
+    }
     __syncthreads();
     bpd_open_planes(m);
     const uint32_t open = m.open;
-    if (open != 0)
-      for (uint32_t v = kSampleVecs + threadIdx.x; v < kPageVecs; v += blockDim.x)
-        bpd_mark(ld_stream(slot + 16ull * v), m, open);
+    // the rest only when some plane may still have b < 8 (random words:
+    // never, so only an eighth of such a slot is read), seven loads in
+    // flight per thread
+    if (open != 0) {
+#pragma unroll 1
+      for (uint32_t v0 = 2 * kBpdThreads; v0 < kPageVecs; v0 += 7 * kBpdThreads) {
+        uint4 x[7];
+#pragma unroll
+        for (int i = 0; i < 7; ++i) x[i] = ld_stream(slot + 16ull * (v0 + threadIdx.x + i * kBpdThreads));
+#pragma unroll
+        for (int i = 0; i < 7; ++i) bpd_mark(x[i], m, open);
+      }
+    }
     __syncthreads();
     bpd_plan(m);
     if (threadIdx.x == 0) a.enc_len[s] = m.len;
@@ -181,69 +257,70 @@ __global__ void __launch_bounds__(1024) k_bpd_scan(BpdScanArgs a) {
 }
 
 // Encodes slot s into out + offset[s].  Thread t owns bytes [256 t, 256 t +
-// 256) of the slot, held in registers as 32 little-endian 64-bit words: byte
-// j of word q is byte 32 t + q of plane j, so each thread packs its own 32
-// bytes of every plane (exactly b words of the plane's rank stream) and,
-// once the alphabets are known, needs no shared memory but the rank tables
-// and no further barrier.  The 16-byte loads are 256 bytes apart across a
-// warp; they go through L1, so the second half of each 32-byte sector is a
-// hit for the next load.
+// 256) of the slot: 32 little-endian 64-bit words, byte j of word q being
+// byte 32 t + q of plane j.  It holds them in registers transposed into its
+// 32 bytes of every plane, so it packs exactly b words of each plane's rank
+// stream and, once the alphabets are known, needs no shared memory but the
+// rank tables and no further barrier.  The slot arrives by coalesced 16-byte loads into
+// a swizzled shared-memory copy (enc_chunk_pos), from which each thread
+// reads its own 256 bytes without bank conflicts.
 __global__ void __launch_bounds__(kBpdThreads, 2) k_bpd_encode(BpdEncodeArgs a) {
   __shared__ BpdSmem m;
+  extern __shared__ uint4 slot_sm[];
   const int tid = threadIdx.x;
   const uint64_t n = *a.n;
   const uint64_t* off =
       a.offs != nullptr ? a.offs
                         : reinterpret_cast<const uint64_t*>(a.meta + kHeaderBytes + 16ull * a.n_allocs + 16 * n);
+  if (blockIdx.x < n) enc_prefetch(a.payload + blockIdx.x * kPage, slot_sm, tid);
   for (uint64_t s = blockIdx.x; s < n; s += gridDim.x) {
     for (uint32_t i = tid; i < 8 * 256 / 4; i += blockDim.x) reinterpret_cast<uint32_t*>(m.present)[i] = 0;
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
-    const uint4* src = reinterpret_cast<const uint4*>(a.payload + s * kPage + 256ull * tid);
-    uint64_t w[32];
+    // this thread's 32 bytes of each plane: P[j][k] holds plane-j bytes
+    // 4k .. 4k+3, taken from words 4k .. 4k+3 by a 4 x 4 byte transpose of
+    // their low halves (planes 0-3) and of their high halves (planes 4-7)
+    uint32_t P[8][8];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const uint4 x = __ldg(src + q);
-      w[2 * q] = (static_cast<uint64_t>(x.y) << 32) | x.x;
-      w[2 * q + 1] = (static_cast<uint64_t>(x.w) << 32) | x.z;
+    for (int k = 0; k < 8; ++k) {
+      const uint4 c0 = slot_sm[enc_chunk_pos(tid, 2 * k)];
+      const uint4 c1 = slot_sm[enc_chunk_pos(tid, 2 * k + 1)];
+      transpose4(c0.x, c0.z, c1.x, c1.z, P[0][k], P[1][k], P[2][k], P[3][k]);
+      transpose4(c0.y, c0.w, c1.y, c1.w, P[4][k], P[5][k], P[6][k], P[7][k]);
     }
-    // the sample: each thread's first 4 words (1,024 bytes of every plane,
-    // spread over the slot); a byte equal to the one before it in its plane
-    // needs no second mark (float planes holding sign and exponent repeat
-    // often)
-    constexpr int kSampleWords = 4;
+    __syncthreads();  // every thread has its bytes: the buffer takes the next slot
+    if (s + gridDim.x < n) enc_prefetch(a.payload + (s + gridDim.x) * kPage, slot_sm, tid);
+    // the sample: each thread's first 4 bytes of every plane (1,024 bytes
+    // of every plane, spread over the slot); a byte equal to the one before
+    // it in its plane needs no second mark (float planes holding sign and
+    // exponent repeat often)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      uint32_t prev = 256u;
-#pragma unroll
-      for (int q = 0; q < kSampleWords; ++q) {
-        const uint32_t x = static_cast<uint32_t>(w[q] >> (8 * j)) & 255u;
-        if (x != prev) m.present[j][x] = 1;
-        prev = x;
-      }
-    }
+    for (int j = 0; j < 8; ++j) mark4(m.present[j], P[j][0]);
     __syncthreads();
     bpd_open_planes(m);
     const uint32_t open = m.open;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       if (!(open & (1u << j))) continue;  // stored as is: no more marks, no ranks
-      uint32_t prev = static_cast<uint32_t>(w[kSampleWords - 1] >> (8 * j)) & 255u;
 #pragma unroll
-      for (int q = kSampleWords; q < 32; ++q) {
-        const uint32_t x = static_cast<uint32_t>(w[q] >> (8 * j)) & 255u;
-        if (x != prev) m.present[j][x] = 1;
-        prev = x;
-      }
+      for (int k = 1; k < 8; ++k) mark4(m.present[j], P[j][k]);
     }
     __syncthreads();
     bpd_plan(m);
     uint8_t* out = a.out + (off[s] - a.base);
     if (m.len == kPage) {
+      // stored as is: this thread's 256 bytes, transposed back (the byte
+      // transpose is its own inverse; the staging buffer already holds the
+      // next slot)
       uint4* dst = reinterpret_cast<uint4*>(out + 256ull * tid);
 #pragma unroll
-      for (int q = 0; q < 16; ++q)
-        dst[q] = make_uint4(static_cast<uint32_t>(w[2 * q]), static_cast<uint32_t>(w[2 * q] >> 32),
-                            static_cast<uint32_t>(w[2 * q + 1]), static_cast<uint32_t>(w[2 * q + 1] >> 32));
+      for (int k = 0; k < 8; ++k) {
+        uint4 c0, c1;
+        transpose4(P[0][k], P[1][k], P[2][k], P[3][k], c0.x, c0.z, c1.x, c1.z);
+        transpose4(P[4][k], P[5][k], P[6][k], P[7][k], c0.y, c0.w, c1.y, c1.w);
+        dst[2 * k] = c0;
+        dst[2 * k + 1] = c1;
+      }
     } else {
       if (tid < 16)
         out[tid] = tid < 8 ? static_cast<uint8_t>(m.b[tid])
@@ -252,39 +329,37 @@ __global__ void __launch_bounds__(kBpdThreads, 2) k_bpd_encode(BpdEncodeArgs a) 
       for (int j = 0; j < 8; ++j) {
         const uint32_t b = m.b[j];
         uint8_t* sec = out + m.sec[j];
+        uint32_t pw[8];  // this plane's words (a switch keeps P's indices static)
+        switch (j) {
+          case 0: plane_words(P[0], pw); break;
+          case 1: plane_words(P[1], pw); break;
+          case 2: plane_words(P[2], pw); break;
+          case 3: plane_words(P[3], pw); break;
+          case 4: plane_words(P[4], pw); break;
+          case 5: plane_words(P[5], pw); break;
+          case 6: plane_words(P[6], pw); break;
+          default: plane_words(P[7], pw); break;
+        }
         if (b == 8) {
           // the plane as is: this thread's 32 bytes of it
-          uint32_t pw[8];
-#pragma unroll
-          for (int q = 0; q < 8; ++q) pw[q] = 0;
-#pragma unroll
-          for (int q = 0; q < 32; ++q)
-            pw[q >> 2] |= static_cast<uint32_t>((w[q] >> (8 * j)) & 255u) << (8 * (q & 3));
           uint4* dst = reinterpret_cast<uint4*>(sec + 32 * tid);
           dst[0] = make_uint4(pw[0], pw[1], pw[2], pw[3]);
           dst[1] = make_uint4(pw[4], pw[5], pw[6], pw[7]);
           continue;
         }
         const uint32_t k = m.k[j], dpad = (k + 15u) & ~15u;
-        if (m.present[j][tid]) sec[m.rank[j][tid]] = static_cast<uint8_t>(tid);
+        if (m.present[j][tslot(tid)]) sec[m.rank[j][tslot(tid)]] = static_cast<uint8_t>(tid);
         for (uint32_t i = k + tid; i < dpad; i += blockDim.x) sec[i] = 0;
         if (b == 0) continue;
         uint32_t* words = reinterpret_cast<uint32_t*>(sec + dpad) + tid * b;
-        uint64_t acc = 0;
-        uint32_t nb = 0, e = 0, px = 256u, pr = 0;
-#pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          // a repeated byte reuses the rank looked up for the one before it
-          const uint32_t x = static_cast<uint32_t>(w[q] >> (8 * j)) & 255u;
-          pr = x == px ? pr : m.rank[j][x];
-          px = x;
-          acc |= static_cast<uint64_t>(pr) << nb;
-          nb += b;
-          if (nb >= 32) {
-            words[e++] = static_cast<uint32_t>(acc);
-            acc >>= 32;
-            nb -= 32;
-          }
+        switch (b) {
+          case 1: pack_ranks<1>(pw, m.rank[j], words); break;
+          case 2: pack_ranks<2>(pw, m.rank[j], words); break;
+          case 3: pack_ranks<3>(pw, m.rank[j], words); break;
+          case 4: pack_ranks<4>(pw, m.rank[j], words); break;
+          case 5: pack_ranks<5>(pw, m.rank[j], words); break;
+          case 6: pack_ranks<6>(pw, m.rank[j], words); break;
+          default: pack_ranks<7>(pw, m.rank[j], words); break;
         }
       }
     }
@@ -322,8 +397,12 @@ KernelSpec bpd_size_spec(uint64_t max_slots) {
 KernelSpec bpd_scan_spec() { return KernelSpec{reinterpret_cast<const void*>(k_bpd_scan), 1, 1024, 0}; }
 
 cudaError_t bpd_encode_spec(uint64_t max_slots, KernelSpec* out) {
-  *out = KernelSpec{reinterpret_cast<const void*>(k_bpd_encode),
-                    grid_for(k_bpd_encode, std::max<uint64_t>(max_slots, 1), 1, kBpdThreads), kBpdThreads, 0};
+  const cudaError_t e = allow_big_smem(k_bpd_encode, kEncDynSmem);
+  if (e != cudaSuccess) return e;
+  const uint64_t cap = static_cast<uint64_t>(resident_per_sm(reinterpret_cast<const void*>(k_bpd_encode),
+                                                             kBpdThreads, kEncDynSmem)) * num_sms();
+  const unsigned grid = static_cast<unsigned>(std::max<uint64_t>(1, std::min(std::max<uint64_t>(max_slots, 1), cap)));
+  *out = KernelSpec{reinterpret_cast<const void*>(k_bpd_encode), grid, kBpdThreads, kEncDynSmem};
   return cudaSuccess;
 }
 

@@ -48,6 +48,14 @@ struct BpdSmem {
 // still at most 128 values are marked in full and ranked.
 constexpr uint32_t kBpdRawAlphabet = 129;
 
+// Where value x sits in a plane's 256-byte presence and rank tables: bit 4
+// is flipped for x >= 128, so x and x + 128 (the same bank otherwise) fall
+// into banks 4 apart.  Float sign-and-exponent planes hold exactly such
+// pairs (the same exponent with either sign).
+__device__ __forceinline__ uint32_t tslot(uint32_t x) { return x ^ ((x >> 7) << 4); }
+// tslot of each byte of a word, four at a time.
+__device__ __forceinline__ uint32_t tslot4(uint32_t w) { return w ^ (((w >> 7) & 0x01010101u) << 4); }
+
 __device__ __forceinline__ uint32_t ceil_log2(uint32_t k) {
   uint32_t b = 0;
   while ((1u << b) < k) ++b;
@@ -147,7 +155,7 @@ constexpr size_t kBpdDynSmem = kPage + kPlaneBytes;  // the slot + one plane
 // Kernels that use more than 48 KiB of dynamic shared memory must say so
 // once per device.
 template <typename K>
-cudaError_t allow_big_smem(K kern) {
+cudaError_t allow_big_smem(K kern, size_t bytes = kBpdDynSmem) {
   static std::mutex mu;
   static std::map<std::pair<const void*, int>, bool> done;
   int dev = 0;
@@ -156,10 +164,18 @@ cudaError_t allow_big_smem(K kern) {
   auto key = std::make_pair(reinterpret_cast<const void*>(kern), dev);
   if (done.count(key)) return cudaSuccess;
   const cudaError_t e =
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kBpdDynSmem));
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
   if (e == cudaSuccess) done[key] = true;
   return e;
 }
+
+// The encoder stages its slot in shared memory: 4,096 chunks of 16 bytes,
+// chunk c of 256-byte group g stored at position 16 g + (c ^ (g & 7)).  A
+// warp's coalesced loads (two groups per instruction) and a thread's reads
+// of its own group (one chunk per instruction, 32 groups) then each touch
+// every bank group of shared memory exactly four times: no conflicts.
+constexpr size_t kEncDynSmem = kPage;
+__device__ __forceinline__ uint32_t enc_chunk_pos(uint32_t g, uint32_t c) { return 16u * g + (c ^ (g & 7u)); }
 
 template <typename K>
 unsigned bpd_grid(K kern, uint64_t units) {
