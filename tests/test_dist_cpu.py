@@ -33,7 +33,7 @@ def _worker(rank, world, port, out):
 
 def test_two_rank_aggregation():
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:  # no fork of a CUDA process
         out = m.dict()
         mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
         res = dict(out)
@@ -126,7 +126,7 @@ def test_consistent_cut_two_ranks(mode):
     every rank holds runs everywhere; of one nobody holds, is refused
     everywhere."""
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:  # no fork of a CUDA process
         out = m.dict()
         mp.spawn(_cut_worker, args=(2, port, out, mode), nprocs=2, join=True)
         res = dict(out)

@@ -113,7 +113,7 @@ def test_cut_on_two_ranks_sharing_the_gpu(mode):
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA device")
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:  # no fork of a CUDA process
         out = m.dict()
         mp.spawn(_worker, args=(2, port, out, mode), nprocs=2, join=True)
         res = dict(out)
