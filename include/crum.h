@@ -104,7 +104,13 @@ typedef struct crum_config {
                                   payload that is not kept (null sink,
                                   CRUM_NO_PAYLOAD) lands in a pinned bounce region
                                   of this size; 0: 64 MiB */
-    uint64_t host_pool_bytes;  /* initial pinned host pool for images; 0: grow on demand */
+    uint64_t host_pool_bytes;  /* initial pinned host pool for images; 0: grow on demand.
+                                  Size it for the most image bytes held at once (a
+                                  chain kept in memory plus the next full image while
+                                  the old chain is still referenced): growing it
+                                  pins host memory, which took about 0.3 s for
+                                  half a GB here, and the driver holds other
+                                  threads' CUDA calls meanwhile */
     int sink;                  /* crum_sink */
     const char *sink_dir;      /* directory for CRUM_SINK_FILE (copied at create) */
     int verify;                /* 1: keep a device copy of the last checkpointed
@@ -420,6 +426,11 @@ typedef struct crum_server_config {
                                  captures overlap, so max_checkpoints > 1 keeps the link
                                  busy without sharing it; negative: each drain starts as
                                  soon as its capture is done */
+    int order;                /* admission order among admissible requests: 0 (default)
+                                 arrival order; 1 the request whose client footprint
+                                 would cross the link fastest, less the time it has
+                                 waited, first (a client's own requests stay in
+                                 arrival order) */
     int keep_images;          /* 1: a completed checkpoint request keeps a reference
                                  to its image until crum_server_take_image hands it
                                  out (or the server is destroyed or its statistics

@@ -54,7 +54,7 @@ class ServerConfig(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("staging_budget", ctypes.c_uint64),
                 ("max_inflight", ctypes.c_int), ("max_checkpoints", ctypes.c_int),
                 ("max_restores", ctypes.c_int), ("serialize_drains", ctypes.c_int),
-                ("keep_images", ctypes.c_int)]
+                ("order", ctypes.c_int), ("keep_images", ctypes.c_int)]
 
 
 class RequestInfo(ctypes.Structure):
@@ -349,9 +349,9 @@ class Server:
 
     def __init__(self, device: int = 0, staging_budget: int = 16 << 30, max_inflight: int = 8,
                  max_checkpoints: int = 0, max_restores: int = 0, serialize_drains: int = 0,
-                 keep_images: int = 0):
+                 keep_images: int = 0, order: int = 0):
         cfg = ServerConfig(device, staging_budget, max_inflight, max_checkpoints, max_restores,
-                           serialize_drains, keep_images)
+                           serialize_drains, order, keep_images)
         h = _VP()
         _check(load().crum_server_create(ctypes.byref(cfg), ctypes.byref(h)), "crum_server_create")
         self.handle = h.value

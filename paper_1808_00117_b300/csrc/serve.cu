@@ -260,7 +260,70 @@ crum_status start(crum_server* S, Request& r) {
   return CRUM_OK;
 }
 
+// Admits request r (server lock held): lends its staging region, starts it.
+void launch(crum_server* S, Request& r, int* n_ckpt, int* n_rest) {
+  Client& c = S->clients[r.client];
+  r.state = 1;
+  r.t_admit = Clock::now();
+  c.busy = true;
+  const crum_status st = start(S, r);
+  if (st != CRUM_OK) {
+    finish(S, r, st);
+    S->done_cv.notify_all();
+  } else {
+    S->running.push_back(r.id);
+    (r.kind == CRUM_REQ_RESTORE ? *n_rest : *n_ckpt)++;
+    S->peak_inflight = std::max<uint32_t>(S->peak_inflight, S->running.size());
+  }
+}
+
+// Admission by expected transfer (crum_server_config.order = 1): among the
+// oldest pending request of every idle client, within the lanes, the one
+// whose client footprint would take least time across the link, less the
+// time it has waited (so a large request is not passed over for ever).  A
+// burst of small requests then no longer queues behind a few long drains.
+void admit_by_size(crum_server* S) {
+  int n_ckpt = 0, n_rest = 0;
+  for (uint64_t id : S->running) (S->reqs[id].kind == CRUM_REQ_RESTORE ? n_rest : n_ckpt)++;
+  constexpr double kBytesPerMs = 50e6;  // the host link's order of magnitude
+  const auto now = Clock::now();
+  while (S->running.size() < static_cast<size_t>(S->cfg.max_inflight)) {
+    std::vector<bool> seen(S->clients.size(), false);
+    std::vector<std::pair<double, std::deque<uint64_t>::iterator>> cand;
+    for (auto it = S->pending.begin(); it != S->pending.end(); ++it) {
+      Request& r = S->reqs[*it];
+      if (seen[r.client]) continue;  // a client's requests run in arrival order
+      seen[r.client] = true;
+      const Client& c = S->clients[r.client];
+      if (c.busy) continue;
+      const int k = r.kind == CRUM_REQ_RESTORE ? 1 : 0;
+      const int lim = k ? S->cfg.max_restores : S->cfg.max_checkpoints;
+      if (lim > 0 && (k ? n_rest : n_ckpt) >= lim) continue;
+      const double key = c.pages * crum::kPage / kBytesPerMs - ms_between(r.t_submit, now);
+      cand.emplace_back(key, it);
+    }
+    if (cand.empty()) return;
+    std::sort(cand.begin(), cand.end(),
+              [](const auto& a, const auto& b) { return a.first < b.first; });
+    bool admitted = false;
+    for (auto& kv : cand) {
+      Request& r = S->reqs[*kv.second];
+      r.region_len = S->clients[r.client].pages * crum::kPage;
+      if (!region_alloc(S, r.region_len, &r.region_off)) continue;
+      S->pending.erase(kv.second);
+      launch(S, r, &n_ckpt, &n_rest);
+      admitted = true;
+      break;  // the candidates' iterators are stale now
+    }
+    if (!admitted) return;
+  }
+}
+
 void admit(crum_server* S) {
+  if (S->cfg.order == 1) {
+    admit_by_size(S);
+    return;
+  }
   std::vector<bool> blocked(S->clients.size(), false);
   int n_ckpt = 0, n_rest = 0;
   for (uint64_t id : S->running) (S->reqs[id].kind == CRUM_REQ_RESTORE ? n_rest : n_ckpt)++;
@@ -284,19 +347,8 @@ void admit(crum_server* S) {
     }
     r.region_len = c.pages * crum::kPage;
     if (!region_alloc(S, r.region_len, &r.region_off)) break;  // wait for memory, in order
-    r.state = 1;
-    r.t_admit = Clock::now();
-    c.busy = true;
-    const crum_status st = start(S, r);
     it = S->pending.erase(it);
-    if (st != CRUM_OK) {
-      finish(S, r, st);
-      S->done_cv.notify_all();
-    } else {
-      S->running.push_back(r.id);
-      (k ? n_rest : n_ckpt)++;
-      S->peak_inflight = std::max<uint32_t>(S->peak_inflight, S->running.size());
-    }
+    launch(S, r, &n_ckpt, &n_rest);
   }
 }
 

@@ -258,9 +258,9 @@ def mix_plan(sizes, rounds):
     return plan
 
 
-@pytest.mark.parametrize("lanes,serial", [((0, 0), 0), ((-1, -1), -1)],
-                         ids=["default_lanes", "unrestricted"])
-def test_config_mix_images_equal_the_oracle_alone_and_in_the_mix(lanes, serial):
+@pytest.mark.parametrize("lanes,serial,order", [((0, 0), 0, 0), ((-1, -1), -1, 0), ((2, 1), -1, 1)],
+                         ids=["default_lanes", "unrestricted", "size_first"])
+def test_config_mix_images_equal_the_oracle_alone_and_in_the_mix(lanes, serial, order):
     """The scaled serving mix under a 1.5 GiB staging budget: GiB-sized
     staging regions, the drain sequencer and long drains.  Every checkpoint
     image equals the oracle's byte for byte in the mix, and each client run
@@ -270,7 +270,7 @@ def test_config_mix_images_equal_the_oracle_alone_and_in_the_mix(lanes, serial):
     plan = mix_plan(sizes, rounds)
     budget = 3 << 29
     srv = crum.Server(staging_budget=budget, max_inflight=8, max_checkpoints=lanes[0],
-                      max_restores=lanes[1], serialize_drains=serial, keep_images=1)
+                      max_restores=lanes[1], serialize_drains=serial, keep_images=1, order=order)
     mix = [MixClient(srv, i, s) for i, s in enumerate(sizes)]
     in_mix = run_mix(srv, mix, rounds, plan)
     stats = srv.drain()
@@ -318,3 +318,30 @@ def test_take_image_rules():
         srv0.take_image(r0)
     srv0.destroy()
     c0.set.destroy()
+
+
+def test_serving_configuration_clients_images_equal_the_oracle():
+    """The serving configuration's own 32 clients (footprints log-uniform
+    1 MiB..4 GiB for its seed: 11.1 GiB in all, the largest 2.7 GiB;
+    int32/fp32/fp64 in turn) through a server with size-first admission and
+    a 16 GiB staging budget: four rounds of the configuration's request mix
+    (U[1 %, 50 %] rewrites, 80 % checkpoints with every fourth of a client
+    full, 20 % restores), every checkpoint image equal to the oracle's byte
+    for byte and every restore exact."""
+    t = torch()
+    free, _ = t.cuda.mem_get_info()
+    sizes = W.workload("serving").sizes
+    if free < sum(sizes) + (20 << 30):
+        pytest.skip("needs about 32 GB of free device memory")
+    rounds = 4
+    plan = mix_plan(sizes, rounds)
+    srv = crum.Server(staging_budget=16 << 30, max_inflight=8, max_checkpoints=2, max_restores=1,
+                      serialize_drains=-1, keep_images=1, order=1)
+    clients = [MixClient(srv, i, s) for i, s in enumerate(sizes)]
+    got = run_mix(srv, clients, rounds, plan)
+    stats = srv.drain()
+    assert stats["failed"] == 0 and stats["completed"] == rounds * len(sizes)
+    assert all(len(v) == sum(not r for r, _ in plan[i]) for i, v in got.items())
+    srv.destroy()
+    for c in clients:
+        c.set.destroy()
