@@ -109,6 +109,23 @@ def bench_workload(args):
     return wl
 
 
+def host_budget_bytes() -> int:
+    """Host memory one rank may pin for images: 60 % of the node's available
+    memory, shared by the ranks on the node."""
+    avail = 0
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    avail = int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    if not avail:
+        avail = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_AVPHYS_PAGES")
+    ranks = int(os.environ.get("LOCAL_WORLD_SIZE", os.environ.get("WORLD_SIZE", "1")))
+    return int(0.6 * avail / max(1, ranks))
+
+
 def raw_image_bytes(info) -> int:
     """Bytes of the uncompressed image with the same pages."""
     return 64 + 16 * info["n_allocs"] + 16 * info["n_dirty"] + info["n_dirty"] * 65536 + 8
@@ -1071,7 +1088,13 @@ def run_e2e_carved(torch, crum, W, bufs, big, wl, page_byte, page_valid, steps, 
     BLK = 4096
     assert all(n % BLK == 0 for n in wl.sizes)
     n_pages = wl.n_pages
-    e_steps = min(steps, 8)
+    k_est = int(round(wl.dirty_frac * n_pages)) + 64
+    img_est = 64 + 16 * len(wl.sizes) + (16 + W.PAGE) * k_est + 8
+    # a form's images stay pinned until it ends: fit them in this rank's
+    # share of host memory (8 steps on one GPU of this node)
+    e_steps = min(steps, 8, host_budget_bytes() // img_est - 4)
+    if e_steps < 2:
+        return None
     blocks = big.view(torch.int64).view(-1, BLK // 8)
     plan = []
     for step in range(2 * e_steps + 4):
@@ -1278,10 +1301,12 @@ def run_batched(args):
         staging = 2 * (n_pages + 1) * W.PAGE  # both halves hold every page
     else:
         staging = 2 * (int(1.5 * max(dirty.values())) + 1) * W.PAGE  # halves hold a step's pages
-    max_img = 64 + 16 * len(wl.sizes) + 16 * n_pages + 8 + min(n_pages, staging // 2 // W.PAGE) * W.PAGE
+    # null sink: an image keeps only its header and tables in host memory
+    # (the payload crosses the link into the 64 MiB bounce region)
+    tables = 64 + 16 * len(wl.sizes) + 16 * n_pages + 8
     fixed = [int(x) for x in args.mapping.split(",")] if args.mapping else None
     s = crum.CheckpointSet(device=local, staging_bytes=staging, sink=crum.SINK_NULL,
-                           host_pool_bytes=max_img if stencil else 3 * max_img,
+                           host_pool_bytes=4 * ((tables + 4095) // 4096 * 4096) + (64 << 20),
                            compress=int(args.compress), managed_in_place=int(args.managed_in_place),
                            hash_mapping=fixed[0] if fixed else -1,
                            gather_mapping=fixed[1] if fixed else -1, use_graph=int(args.graph))
@@ -1560,8 +1585,12 @@ def large_legs(args, torch, crum, W, s, bufs, big, wl, page_byte, offs, steps, w
     del host_plain
     out["plain_p0"] = {"ms": round(plain_ms, 3), "gbs": round(S / (plain_ms * 1e-3) / 1e9, 2),
                        "what": "synchronize + full device->host copy of the footprint"}
-    out["restore"] = None if args.no_restore else restore_prefix(
-        torch, crum, W, bufs, big, wl, sh, stream, dev, local, tune, staging, app_update, warmup + steps + 40)
+    # the prefix's full image and incrementals must fit this rank's share of
+    # host memory (40 GiB on one GPU of this node)
+    prefix = min(40 << 30, int(host_budget_bytes() / 1.2))
+    out["restore"] = None if args.no_restore or prefix < (1 << 30) else restore_prefix(
+        torch, crum, W, bufs, big, wl, sh, stream, dev, local, tune, staging, app_update,
+        warmup + steps + 40, limit=prefix)
     out["verify"] = {"measured": False,
                      "why": "verify mode keeps a device shadow of the footprint: 140 GiB beside "
                             "140 GiB does not fit in HBM (measured on uint32_8g)"}
