@@ -1519,7 +1519,8 @@ def restore_prefix(torch, crum, W, bufs, big, wl, sh, stream, dev, local, tune, 
     incr = int(1.2 * wl.dirty_frac * pages) + 64
     rs = crum.CheckpointSet(device=local, staging_bytes=staging, sink=crum.SINK_MEMORY,
                             host_pool_bytes=full_img + (n_incr + 1) * (64 + 16 * k + (16 + W.PAGE) * incr + 8),
-                            hash_mapping=tune["hash_mapping"], gather_mapping=tune["gather_mapping"])
+                            hash_mapping=tune["hash_mapping"], gather_mapping=tune["gather_mapping"],
+                            restore_mode=crum.RESTORE_MERGED)
     for b in bufs[:k]:
         rs.register(b.data_ptr(), b.numel())
     chain = [rs.checkpoint(sh, crum.FULL)]
