@@ -133,6 +133,57 @@ def test_uint32_8g_full_size():
     del expect
 
 
+def test_compressed_fp32_8g_full_size():
+    """Compressed images of the 8 GiB workload with fp32 data (the kind that
+    shrinks): a full checkpoint, then two incrementals of 5 % clustered
+    runs.  Each incremental image in full: trailer by the oracle's checker,
+    page table against the known dirty set, every slot's code equal to the
+    oracle's code of that page (on all host cores), every committed hash
+    against the oracle; then the chain end restored onto scribbled memory
+    and the whole 8 GiB compared."""
+    t = torch()
+    wl = W.workload("uint32_8g")
+    buf = t.empty(wl.sizes[0], dtype=t.uint8, device="cuda")
+    W.fill_(buf, wl.seed + 5, "fp32")
+    s = make_bench_set([buf], compress=1)
+    chain = [s.checkpoint(stream_handle(), crum.FULL)]
+    chain[0].wait()
+    n_full = wl.n_pages
+    for step in (1, 2):
+        pages = W.choose_step(wl, 100 + step, n_full)
+        W.mutate_pages_(buf, pages, wl.seed + 100 + step)
+        img = s.checkpoint(stream_handle())
+        img.wait()
+        chain.append(img)
+        b = image_array(img)
+        h = parse_header(b)
+        n, A = h["n"], h["A"]
+        assert oracle.image_version(b) == 2 and oracle.check_image(b) == oracle.OK
+        assert page_table(b)[:, 1].tolist() == pages.tolist()
+        offs = np.frombuffer(b, dtype=np.uint64, count=n, offset=64 + 16 * A + 16 * n).astype(np.int64)
+        ends = np.append(offs[1:], h["size"] - 8 - h["poff"])
+        host = buf.cpu().numpy().reshape(n_full, P)
+
+        def slot_ok(j):
+            code = b[h["poff"] + offs[j]:h["poff"] + ends[j]].tobytes()
+            return code == oracle.bpd_encode(host[pages[j]])
+
+        with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+            ok = list(ex.map(slot_ok, range(n)))
+        assert all(ok), f"step {step}: {ok.count(False)} slots differ from the oracle's code"
+        assert np.array_equal(s.hashes(), oracle_hashes([host.reshape(-1)]))
+        del b, host
+    expect = buf.clone()
+    W.fill_(buf, 4243, "u32")
+    s.restore(chain[-1], stream_handle())
+    t.cuda.synchronize()
+    assert t.equal(buf, expect)
+    for img in chain:
+        img.release()
+    s.destroy()
+    del expect
+
+
 def test_stencil_full_size():
     """The stencil configuration (200 fp64 fields, 24 GiB): 20 checkpoints,
     each after a 27-point stencil step over interior z-ranges (30 % of
