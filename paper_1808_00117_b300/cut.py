@@ -25,6 +25,11 @@ Rules (the same decision on every rank, from the gathered values only):
   capture does).
 * Cut numbers continue from one past the largest any rank held, so ranks
   that were out of step (one a cut ahead) are in step for the next cut.
+* A rank that does not reach a cut (it left, or stalled beyond the
+  coordinator's timeout) is detected on the host, by the barrier or the
+  all-gather failing, before any rank queues device work for that cut or
+  after it has queued only its own capture: the others raise RankLost and
+  drop their image of that cut.
 
 Host logic only (torch.distributed); the device work is each rank's own
 crum_checkpoint / crum_restore.
@@ -33,11 +38,16 @@ from __future__ import annotations
 
 from typing import Any, Dict, Optional
 
-__all__ = ["CutError", "CutCoordinator"]
+__all__ = ["CutError", "RankLost", "CutCoordinator"]
 
 
 class CutError(RuntimeError):
     pass
+
+
+class RankLost(CutError):
+    """A rank did not reach the cut (it left, or its host stalled beyond the
+    timeout): the cut is abandoned on every rank that noticed."""
 
 
 def _gather(values, group) -> list:
@@ -57,25 +67,52 @@ class CutCoordinator:
     ``restore(image, stream)``; images need ``info() -> {"seq": ...}`` and
     ``release()``."""
 
-    def __init__(self, cset: Any, group: Optional[Any] = None, first_cut: int = 0):
+    def __init__(self, cset: Any, group: Optional[Any] = None, first_cut: int = 0,
+                 timeout_s: Optional[float] = None):
         self.cset = cset
         self.group = group
         self.next_cut = first_cut
+        self.timeout_s = timeout_s  # how long a barrier waits for every rank
         self.images: Dict[int, Any] = {}   # cut number -> this rank's image
         self.seqs: Dict[int, list] = {}    # cut number -> every rank's image seq
 
+    def _barrier(self) -> None:
+        """Every rank arrives, or RankLost.  With a timeout on a gloo group
+        the barrier is monitored: it names the ranks that did not arrive."""
+        import datetime
+        import torch.distributed as dist
+        try:
+            if self.timeout_s is not None and dist.get_backend(self.group) == "gloo":
+                dist.monitored_barrier(self.group, timeout=datetime.timedelta(seconds=self.timeout_s))
+            else:
+                dist.barrier(self.group)
+        except RuntimeError as e:
+            raise RankLost(f"a rank did not reach the cut: {e}") from e
+
+    def _gather(self, values) -> list:
+        try:
+            return _gather(values, self.group)
+        except RuntimeError as e:  # a peer left between the barrier and here
+            raise RankLost(f"a rank left during the cut: {e}") from e
+
     def checkpoint(self, stream: int, flags: int = 0):
         """Barrier, this rank's checkpoint, agreement.  Returns (image, cut
-        number); raises CutError on every rank when the cut is refused."""
-        import torch.distributed as dist
-        dist.barrier(self.group)
+        number); raises CutError on every rank when the cut is refused, and
+        RankLost when a rank does not take part (this rank's image, if it
+        took one, is dropped: the cut cannot stand)."""
+        self._barrier()
         img, err = None, ""
         try:
             img = self.cset.checkpoint(stream, flags)
         except Exception as e:  # the rank reports the failure instead of leaving
             err = str(e)
         seq = int(img.info()["seq"]) if img is not None else -1
-        rows = _gather([self.next_cut, int(img is not None), seq], self.group)
+        try:
+            rows = self._gather([self.next_cut, int(img is not None), seq])
+        except RankLost:
+            if img is not None:
+                img.release()
+            raise
         cuts = [r[0] for r in rows]
         ok = len(set(cuts)) == 1 and all(r[1] for r in rows)
         self.next_cut = max(cuts) + 1
@@ -96,16 +133,15 @@ class CutCoordinator:
         synchronize) runs after the stream-ordered restore is queued and
         before the closing barrier, so that the barrier means every rank's
         memory is back."""
-        import torch.distributed as dist
         mine = self.images.get(cut)
-        rows = _gather([cut, int(mine is not None)], self.group)
+        rows = self._gather([cut, int(mine is not None)])
         if len({r[0] for r in rows}) != 1 or not all(r[1] for r in rows):
             raise CutError(f"not every rank holds an image of cut {cut}: {rows}")
-        dist.barrier(self.group)
+        self._barrier()
         self.cset.restore(mine, stream)
         if wait is not None:
             wait()
-        dist.barrier(self.group)
+        self._barrier()
         return cut
 
     def release(self) -> None:

@@ -149,3 +149,45 @@ def test_consistent_cut_two_ranks(mode):
             assert got[3] == ("released", [False, True, False] if r == 0 else [False, False])
             assert got[6] == ("seqs", {0: [0, 0], 2: [2, 1]})
         assert got[5] == ("restore refused", 99)
+
+
+def _lost_worker(rank, world, port, out):
+    import datetime
+    import sys
+    import time
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    from paper_1808_00117_b300 import cut
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=world, timeout=datetime.timedelta(seconds=20))
+    s = _FakeSet()
+    co = cut.CutCoordinator(s, timeout_s=3.0)
+    res = []
+    img, c = co.checkpoint(0)
+    res.append(("ok", c))
+    if rank == 1:
+        out[rank] = res  # rank 1 leaves between cuts, without a word
+        return
+    t0 = time.time()
+    try:
+        co.checkpoint(0)
+        res.append(("ok",))
+    except cut.RankLost:
+        res.append(("lost", time.time() - t0 < 15))
+    res.append(("released", [im.released for im in s.taken]))
+    out[rank] = res
+
+
+def test_cut_detects_a_rank_that_left():
+    """Failure detection on the host: rank 1 takes cut 0 and exits; rank 0's
+    next cut raises RankLost within the coordinator's timeout instead of
+    waiting for ever, having queued no capture for it."""
+    port = _free_port()
+    with mp.get_context("spawn").Manager() as m:
+        out = m.dict()
+        mp.spawn(_lost_worker, args=(2, port, out), nprocs=2, join=True)
+        res = dict(out)
+    assert res[1] == [("ok", 0)]
+    assert res[0][0] == ("ok", 0)
+    assert res[0][1] == ("lost", True)
+    assert res[0][2] == ("released", [False])  # no image was taken for the lost cut
