@@ -280,8 +280,10 @@ void launch(crum_server* S, Request& r, int* n_ckpt, int* n_rest) {
 // Admission by expected transfer (crum_server_config.order = 1): among the
 // oldest pending request of every idle client, within the lanes, the one
 // whose client footprint would take least time across the link, less the
-// time it has waited (so a large request is not passed over for ever).  A
-// burst of small requests then no longer queues behind a few long drains.
+// time it has waited (so a large request is not passed over for ever: once
+// it has waited longer than its transfer would take, it also keeps smaller
+// requests from taking the staging memory it waits for).  A burst of small
+// requests then no longer queues behind a few long drains.
 void admit_by_size(crum_server* S) {
   int n_ckpt = 0, n_rest = 0;
   for (uint64_t id : S->running) (S->reqs[id].kind == CRUM_REQ_RESTORE ? n_rest : n_ckpt)++;
@@ -309,7 +311,12 @@ void admit_by_size(crum_server* S) {
     for (auto& kv : cand) {
       Request& r = S->reqs[*kv.second];
       r.region_len = S->clients[r.client].pages * crum::kPage;
-      if (!region_alloc(S, r.region_len, &r.region_off)) continue;
+      if (!region_alloc(S, r.region_len, &r.region_off)) {
+        // a request that has waited longer than its own transfer would take
+        // holds the budget's next free memory: nothing smaller passes it
+        if (kv.first <= 0) return;
+        continue;
+      }
       S->pending.erase(kv.second);
       launch(S, r, &n_ckpt, &n_rest);
       admitted = true;

@@ -345,3 +345,58 @@ def test_serving_configuration_clients_images_equal_the_oracle():
     srv.destroy()
     for c in clients:
         c.set.destroy()
+
+
+def test_size_first_does_not_starve_a_large_request():
+    """Size-first admission when the large client fits the staging budget
+    only with no small request on the device.  Small client 7's first
+    request is held on the device by a spin kernel on its stream; small
+    clients 0-6 each queue a run of checkpoints behind the large request.
+    The large request has waited longer than its transfer would take, so it
+    holds the next free staging memory: clients 0-6 stop after a request or
+    two, the large request runs as soon as client 7's request ends, and most
+    of their queued requests complete after it.  (With smaller requests
+    allowed to pass it, clients 0-6 run their whole queues first.)  Its image
+    equals the oracle's."""
+    import time
+    t = torch()
+    Q = 100
+    budget = (64 + 4) * P
+    srv = crum.Server(staging_budget=budget, max_inflight=8, max_checkpoints=-1, max_restores=-1,
+                      serialize_drains=-1, order=1, keep_images=1)
+    big = MixClient(srv, 0, 64 * P)
+    small = [MixClient(srv, 1 + i, 8 * P) for i in range(8)]
+    for c in [big] + small:  # every client's first checkpoint is full
+        srv.wait(srv.submit(c.cid, crum.REQ_CHECKPOINT_FULL))
+        c.oracle.checkpoint([c.host()], full=True)
+    for c in [big] + small:
+        c.rewrite(5, 0.5)
+        c.stream.synchronize()
+    with t.cuda.stream(small[7].stream):
+        t.cuda._sleep(200_000_000)  # about 0.1 s at the maximum SM clock
+    subs = []  # (client, request id, host time of the submit)
+    for c in small:
+        subs.append((c, srv.submit(c.cid, crum.REQ_CHECKPOINT), time.perf_counter()))
+    t_big = time.perf_counter()
+    rid = srv.submit(big.cid, crum.REQ_CHECKPOINT)
+    for _ in range(Q - 1):
+        for c in small[:7]:
+            subs.append((c, srv.submit(c.cid, crum.REQ_CHECKPOINT), time.perf_counter()))
+    info = srv.wait(rid)
+    exp, *_ = big.oracle.checkpoint([big.host()])
+    img = srv.take_image(rid)
+    assert info["status"] == crum.OK and img.to_bytes() == exp
+    img.release()
+    done_big = t_big + info["t_total_ms"] / 1e3
+    after = 0
+    for c, r, ts in subs:
+        si = srv.wait(r)
+        assert si["status"] == crum.OK
+        after += c is not small[7] and ts + si["t_total_ms"] / 1e3 > done_big
+    srv.drain()
+    srv.destroy()
+    # the large request waited for client 7's held request, not for the queues
+    assert info["t_queue_ms"] > 20, info
+    assert after >= 7 * Q // 2, f"{after} of {7 * Q} queued small requests completed after the large one"
+    for c in [big] + small:
+        c.set.destroy()
