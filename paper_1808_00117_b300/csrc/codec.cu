@@ -5,8 +5,8 @@
 //                   the slot's encoded length
 //   k_bpd_scan      one CTA: slot offsets (exclusive prefix of the lengths),
 //                   encoded payload size, compressed-form header words
-//   k_bpd_encode    one CTA per slot: the slot's code at its offset
-//   k_bpd_checksum  the compressed image's trailer hash
+//   k_bpd_encode    one CTA per slot: the slot's code at its offset, and
+//                   the compressed image's checksum
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -68,11 +68,21 @@ __device__ __forceinline__ void mark4(uint8_t* present, uint32_t w) {
   for (int i = 0; i < 4; ++i) present[(t >> (8 * i)) & 255u] = 1;
 }
 
+__device__ __forceinline__ uint64_t pair64(uint32_t lo, uint32_t hi) {
+  return (static_cast<uint64_t>(hi) << 32) | lo;
+}
+
 // This thread's 32 bytes of a plane (pw) as B-bit ranks, LSB first: exactly
 // B words at `words`.  B is a template argument, so every rank's bit
-// position is known at compile time.
+// position is known at compile time.  Returns the image-checksum terms of
+// the 64-bit words this thread completes: 64-bit word i of the packed
+// section (image index u0 + i) is its 32-bit words 2i and 2i + 1.  For odd
+// B a run starts (odd threads) or ends (even threads) in the middle of one;
+// the even thread takes that word, its high half from the next lane.  Every
+// lane of the warp calls it (B is uniform across the CTA).
 template <int B>
-__device__ __forceinline__ void pack_ranks(const uint32_t (&pw)[8], const uint8_t* rank, uint32_t* words) {
+__device__ __forceinline__ uint64_t pack_ranks(const uint32_t (&pw)[8], const uint8_t* rank, uint32_t* words,
+                                               uint64_t u0) {
   uint32_t out[B];
 #pragma unroll
   for (int e = 0; e < B; ++e) out[e] = 0;
@@ -89,6 +99,25 @@ __device__ __forceinline__ void pack_ranks(const uint32_t (&pw)[8], const uint8_
   }
 #pragma unroll
   for (int e = 0; e < B; ++e) words[e] = out[e];
+  const uint64_t t = threadIdx.x;
+  uint64_t h = 0;
+  if constexpr (B % 2 == 0) {
+    const uint64_t c = (u0 + t * (B / 2)) * kPhi;  // index terms: c + i kPhi
+#pragma unroll
+    for (int i = 0; i < B / 2; ++i) h += dev::mix(pair64(out[2 * i], out[2 * i + 1]) ^ (c + i * kPhi));
+  } else {
+    // one instruction stream for both parities (a divergent branch would
+    // run both): odd threads start one 32-bit word later
+    const uint32_t next = __shfl_down_sync(0xffffffffu, out[0], 1);
+    const bool odd = t & 1;
+    const uint64_t c = (u0 + (t * B + odd) / 2) * kPhi;
+#pragma unroll
+    for (int i = 0; i < B / 2; ++i)
+      h += dev::mix(pair64(odd ? out[2 * i + 1] : out[2 * i], odd ? out[2 * i + 2] : out[2 * i + 1]) ^
+                    (c + i * kPhi));
+    if (!odd) h += dev::mix(pair64(out[B - 1], next) ^ (c + (B / 2) * kPhi));
+  }
+  return h;
 }
 
 __device__ __forceinline__ void plane_words(const uint32_t (&p)[8], uint32_t (&pw)[8]) {
@@ -264,14 +293,27 @@ __global__ void __launch_bounds__(1024) k_bpd_scan(BpdScanArgs a) {
 // rank tables and no further barrier.  The slot arrives by coalesced 16-byte loads into
 // a swizzled shared-memory copy (enc_chunk_pos), from which each thread
 // reads its own 256 bytes without bank conflicts.
+//
+// The image checksum is summed as the code is written: each thread adds the
+// terms of the 64-bit words it stores from registers (a slot stored as is,
+// the header, planes stored as is, packed ranks) and, after the slot's last
+// barrier, of the dictionary words the CTA wrote; for the whole image (offs
+// null) the grid also adds the header and tables, which are final before
+// this launch.
 __global__ void __launch_bounds__(kBpdThreads, 2) k_bpd_encode(BpdEncodeArgs a) {
   __shared__ BpdSmem m;
   extern __shared__ uint4 slot_sm[];
   const int tid = threadIdx.x;
   const uint64_t n = *a.n;
+  const bool whole = a.offs == nullptr;
   const uint64_t* off =
-      a.offs != nullptr ? a.offs
-                        : reinterpret_cast<const uint64_t*>(a.meta + kHeaderBytes + 16ull * a.n_allocs + 16 * n);
+      whole ? reinterpret_cast<const uint64_t*>(a.meta + kHeaderBytes + 16ull * a.n_allocs + 16 * n) : a.offs;
+  const uint64_t poff = whole ? (kHeaderBytes + 16ull * a.n_allocs + 24 * n + 15) & ~15ull : a.poff;
+  uint64_t h = 0;  // this thread's terms of the image checksum
+  if (whole)
+    for (uint64_t v = static_cast<uint64_t>(blockIdx.x) * blockDim.x + tid; v < poff / 16;
+         v += static_cast<uint64_t>(gridDim.x) * blockDim.x)
+      h += hash_vec(ld_stream(a.meta + 16 * v), (2 * v) * kPhi);
   if (blockIdx.x < n) enc_prefetch(a.payload + blockIdx.x * kPage, slot_sm, tid);
   for (uint64_t s = blockIdx.x; s < n; s += gridDim.x) {
     for (uint32_t i = tid; i < 8 * 256 / 4; i += blockDim.x) reinterpret_cast<uint32_t*>(m.present)[i] = 0;
@@ -308,11 +350,13 @@ __global__ void __launch_bounds__(kBpdThreads, 2) k_bpd_encode(BpdEncodeArgs a) 
     __syncthreads();
     bpd_plan(m);
     uint8_t* out = a.out + (off[s] - a.base);
+    const uint64_t u0 = (poff + off[s]) / 8;  // image index of the slot's first 64-bit word
     if (m.len == kPage) {
       // stored as is: this thread's 256 bytes, transposed back (the byte
       // transpose is its own inverse; the staging buffer already holds the
       // next slot)
       uint4* dst = reinterpret_cast<uint4*>(out + 256ull * tid);
+      const uint64_t craw = (u0 + 32ull * tid) * kPhi;
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         uint4 c0, c1;
@@ -320,11 +364,23 @@ __global__ void __launch_bounds__(kBpdThreads, 2) k_bpd_encode(BpdEncodeArgs a) 
         transpose4(P[4][k], P[5][k], P[6][k], P[7][k], c0.y, c0.w, c1.y, c1.w);
         dst[2 * k] = c0;
         dst[2 * k + 1] = c1;
+        const uint64_t c = craw + (4 * k) * kPhi;  // index terms of words u0 + 32 tid + 4k + i
+        h += dev::mix(pair64(c0.x, c0.y) ^ c) + dev::mix(pair64(c0.z, c0.w) ^ (c + kPhi)) +
+             dev::mix(pair64(c1.x, c1.y) ^ (c + 2 * kPhi)) + dev::mix(pair64(c1.z, c1.w) ^ (c + 3 * kPhi));
       }
     } else {
       if (tid < 16)
         out[tid] = tid < 8 ? static_cast<uint8_t>(m.b[tid])
                            : static_cast<uint8_t>(m.b[tid - 8] == 8 ? 255u : m.k[tid - 8] - 1u);
+      if (tid == 0) {
+        uint64_t w0 = 0, w1 = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          w0 |= static_cast<uint64_t>(m.b[j] & 255u) << (8 * j);
+          w1 |= static_cast<uint64_t>((m.b[j] == 8 ? 255u : m.k[j] - 1u) & 255u) << (8 * j);
+        }
+        h += dev::hash_word(w0, u0) + dev::hash_word(w1, u0 + 1);
+      }
 #pragma unroll 1
       for (int j = 0; j < 8; ++j) {
         const uint32_t b = m.b[j];
@@ -345,6 +401,9 @@ __global__ void __launch_bounds__(kBpdThreads, 2) k_bpd_encode(BpdEncodeArgs a) 
           uint4* dst = reinterpret_cast<uint4*>(sec + 32 * tid);
           dst[0] = make_uint4(pw[0], pw[1], pw[2], pw[3]);
           dst[1] = make_uint4(pw[4], pw[5], pw[6], pw[7]);
+          const uint64_t c = (u0 + m.sec[j] / 8 + 4ull * tid) * kPhi;
+          h += dev::mix(pair64(pw[0], pw[1]) ^ c) + dev::mix(pair64(pw[2], pw[3]) ^ (c + kPhi)) +
+               dev::mix(pair64(pw[4], pw[5]) ^ (c + 2 * kPhi)) + dev::mix(pair64(pw[6], pw[7]) ^ (c + 3 * kPhi));
           continue;
         }
         const uint32_t k = m.k[j], dpad = (k + 15u) & ~15u;
@@ -352,39 +411,30 @@ __global__ void __launch_bounds__(kBpdThreads, 2) k_bpd_encode(BpdEncodeArgs a) 
         for (uint32_t i = k + tid; i < dpad; i += blockDim.x) sec[i] = 0;
         if (b == 0) continue;
         uint32_t* words = reinterpret_cast<uint32_t*>(sec + dpad) + tid * b;
+        const uint64_t uw = u0 + (m.sec[j] + dpad) / 8;
         switch (b) {
-          case 1: pack_ranks<1>(pw, m.rank[j], words); break;
-          case 2: pack_ranks<2>(pw, m.rank[j], words); break;
-          case 3: pack_ranks<3>(pw, m.rank[j], words); break;
-          case 4: pack_ranks<4>(pw, m.rank[j], words); break;
-          case 5: pack_ranks<5>(pw, m.rank[j], words); break;
-          case 6: pack_ranks<6>(pw, m.rank[j], words); break;
-          default: pack_ranks<7>(pw, m.rank[j], words); break;
+          case 1: h += pack_ranks<1>(pw, m.rank[j], words, uw); break;
+          case 2: h += pack_ranks<2>(pw, m.rank[j], words, uw); break;
+          case 3: h += pack_ranks<3>(pw, m.rank[j], words, uw); break;
+          case 4: h += pack_ranks<4>(pw, m.rank[j], words, uw); break;
+          case 5: h += pack_ranks<5>(pw, m.rank[j], words, uw); break;
+          case 6: h += pack_ranks<6>(pw, m.rank[j], words, uw); break;
+          default: h += pack_ranks<7>(pw, m.rank[j], words, uw); break;
         }
       }
     }
-    __syncthreads();  // the tables are read until here
-  }
-}
-
-// Image checksum of a compressed image: the header and tables (word index
-// from 0) plus the encoded payload (word index from the payload offset).
-__global__ void __launch_bounds__(256) k_bpd_checksum(BpdChecksumArgs a) {
-  const uint64_t n = *a.n_dirty;
-  const uint64_t A = a.n_allocs;
-  const uint64_t poff = (kHeaderBytes + 16 * A + 24 * n + 15) & ~15ull;
-  const uint64_t meta_vecs = poff / 16, enc_vecs = *a.total / 16;
-  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
-  uint64_t h = 0;
-  for (uint64_t v = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < meta_vecs + enc_vecs;
-       v += stride) {
-    if (v < meta_vecs)
-      h += hash_vec(ld_stream(a.meta + 16 * v), (2 * v) * kPhi);
-    else
-      h += hash_vec(ld_stream(a.enc + 16 * (v - meta_vecs)), (2 * v) * kPhi);
+    __syncthreads();  // the tables are read until here; the code is written
+    if (m.len != kPage && tid < 128) {
+      // the dictionaries (at most 128 bytes a plane), written byte by byte
+      // by the CTA: read back through L2, past the incoherent L1
+      const int j = tid >> 4, q = tid & 15;
+      if (m.b[j] != 8 && 8u * q < ((m.k[j] + 15u) & ~15u))
+        h += dev::hash_word(__ldcg(reinterpret_cast<const unsigned long long*>(out + m.sec[j] + 8 * q)),
+                            u0 + m.sec[j] / 8 + q);
+    }
   }
   h = dev::warp_sum(h);
-  if ((threadIdx.x & 31) == 0 && h != 0) atomicAdd(a.trailer, static_cast<unsigned long long>(h));
+  if ((tid & 31) == 0 && h != 0) atomicAdd(a.trailer, static_cast<unsigned long long>(h));
 }
 
 }  // namespace
@@ -406,11 +456,6 @@ cudaError_t bpd_encode_spec(uint64_t max_slots, KernelSpec* out) {
   return cudaSuccess;
 }
 
-KernelSpec bpd_checksum_spec(uint64_t max_bytes) {
-  return KernelSpec{reinterpret_cast<const void*>(k_bpd_checksum),
-                    grid_for(k_bpd_checksum, (max_bytes / 16 + 255) / 256 + 1, 1, 256), 256, 0};
-}
-
 cudaError_t launch_bpd_size(const BpdSizeArgs& a, uint64_t max_slots, cudaStream_t st) {
   if (max_slots == 0) return cudaSuccess;
   BpdSizeArgs copy = a;
@@ -429,11 +474,6 @@ cudaError_t launch_bpd_encode(const BpdEncodeArgs& a, uint64_t max_slots, cudaSt
   if (e != cudaSuccess) return e;
   BpdEncodeArgs copy = a;
   return launch_spec(sp, &copy, st);
-}
-
-cudaError_t launch_bpd_checksum(const BpdChecksumArgs& a, uint64_t max_bytes, cudaStream_t st) {
-  BpdChecksumArgs copy = a;
-  return launch_spec(bpd_checksum_spec(max_bytes), &copy, st);
 }
 
 }  // namespace crum

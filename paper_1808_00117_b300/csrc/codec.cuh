@@ -190,6 +190,5 @@ unsigned bpd_grid(K kern, uint64_t units) {
 KernelSpec bpd_size_spec(uint64_t max_slots);
 KernelSpec bpd_scan_spec();
 cudaError_t bpd_encode_spec(uint64_t max_slots, KernelSpec* out);
-KernelSpec bpd_checksum_spec(uint64_t max_bytes);
 
 }  // namespace crum

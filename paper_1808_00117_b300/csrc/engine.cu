@@ -586,9 +586,9 @@ crum_status checkpoint_chunked(crum_set* s, crum_image* img, cudaStream_t app,
       CK(cudaEventRecord(H.ev_sized, s->cap_stream));
       if ((st = wait_event(H.ev_sized, kBackgroundLimitNs)) != CRUM_OK) return st;
       bytes = reinterpret_cast<volatile uint64_t*>(H.mailbox)[3];
-      crum::BpdEncodeArgs ea{H.payload, H.cn, offs + s0, enc_base, H.cpay, H0.meta, static_cast<uint32_t>(A)};
+      crum::BpdEncodeArgs ea{H.payload, H.cn, offs + s0, enc_base, H.cpay, H0.meta, static_cast<uint32_t>(A),
+                             poff, reinterpret_cast<unsigned long long*>(H0.scalars + 1)};
       CK(crum::launch_bpd_encode(ea, m, s->cap_stream));
-      CK(crum::launch_hash_bytes(H.cpay, bytes, (poff + enc_base) / 8, H0.scalars + 1, s->cap_stream));
       src = H.cpay;
       host_off = poff + enc_base;
       enc_base += bytes;
@@ -723,13 +723,11 @@ crum_status graph_build(crum_set* s, int h, crum_image* img, const crum::HashArg
     const uint32_t A = static_cast<uint32_t>(s->allocs.size());
     crum::BpdSizeArgs za{H.payload, H.scalars, H.enc_len};
     crum::BpdScanArgs qa{H.enc_len, H.scalars, nullptr, 0, H.ctotal, H.mailbox_dev, H.meta, A};
-    crum::BpdEncodeArgs ea{H.payload, H.scalars, nullptr, 0, H.cpay, H.meta, A};
-    crum::BpdChecksumArgs ka{H.meta, H.cpay, H.scalars, H.ctotal, A,
-                             reinterpret_cast<unsigned long long*>(H.scalars + 1)};
+    crum::BpdEncodeArgs ea{H.payload, H.scalars, nullptr, 0, H.cpay, H.meta, A, 0,
+                           reinterpret_cast<unsigned long long*>(H.scalars + 1)};
     void* a_z[] = {&za};
     void* a_q[] = {&qa};
     void* a_e[] = {&ea};
-    void* a_k[] = {&ka};
     crum::KernelSpec es{};
     if (e == cudaSuccess) e = crum::bpd_encode_spec(s->n_pages, &es);
     kp = kparams(crum::bpd_size_spec(s->n_pages), a_z);
@@ -740,10 +738,7 @@ crum_status graph_build(crum_set* s, int h, crum_image* img, const crum::HashArg
     after(n);
     if (e == cudaSuccess) e = cudaGraphAddEventRecordNode(&n, g, &prev, 1, H.ev_sized);
     after(n);
-    kp = kparams(es, a_e);
-    if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n, g, &prev, 1, &kp);
-    after(n);
-    cudaMemsetParams zp{};
+    cudaMemsetParams zp{};  // the trailer receives the compressed image's checksum
     zp.dst = H.scalars + 1;
     zp.value = 0;
     zp.elementSize = 4;
@@ -751,7 +746,7 @@ crum_status graph_build(crum_set* s, int h, crum_image* img, const crum::HashArg
     zp.height = 1;
     if (e == cudaSuccess) e = cudaGraphAddMemsetNode(&n, g, &prev, 1, &zp);
     after(n);
-    kp = kparams(crum::bpd_checksum_spec(cmeta_bytes(A, s->n_pages) + s->n_pages * kPage), a_k);
+    kp = kparams(es, a_e);
     if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n, g, &prev, 1, &kp);
     after(n);
     if (e == cudaSuccess) e = cudaGraphAddEventRecordNode(&n, g, &prev, 1, H.ev_encoded);
@@ -1456,14 +1451,10 @@ crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, cr
       crum::BpdScanArgs qa{H.enc_len, H.scalars, nullptr, 0, H.ctotal, H.mailbox_dev, H.meta, img->n_allocs};
       if (ce == cudaSuccess) ce = crum::launch_bpd_scan(qa, s->cap_stream);
       if (ce == cudaSuccess) ce = cudaEventRecord(H.ev_sized, s->cap_stream);
-      crum::BpdEncodeArgs ea{H.payload, H.scalars, nullptr, 0, H.cpay, H.meta, img->n_allocs};
-      if (ce == cudaSuccess) ce = crum::launch_bpd_encode(ea, s->n_pages, s->cap_stream);
+      crum::BpdEncodeArgs ea{H.payload, H.scalars, nullptr, 0, H.cpay, H.meta, img->n_allocs, 0,
+                             reinterpret_cast<unsigned long long*>(H.scalars + 1)};
       if (ce == cudaSuccess) ce = cudaMemsetAsync(H.scalars + 1, 0, sizeof(uint64_t), s->cap_stream);
-      crum::BpdChecksumArgs ka{H.meta, H.cpay, H.scalars, H.ctotal, img->n_allocs,
-                               reinterpret_cast<unsigned long long*>(H.scalars + 1)};
-      if (ce == cudaSuccess)
-        ce = crum::launch_bpd_checksum(ka, cmeta_bytes(img->n_allocs, s->n_pages) + s->n_pages * kPage,
-                                       s->cap_stream);
+      if (ce == cudaSuccess) ce = crum::launch_bpd_encode(ea, s->n_pages, s->cap_stream);
       if (ce == cudaSuccess) ce = cudaEventRecord(H.ev_encoded, s->cap_stream);
       if (ce == cudaSuccess) ce = cudaEventRecord(img->ev_e1, s->cap_stream);
     }

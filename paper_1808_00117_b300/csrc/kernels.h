@@ -146,8 +146,10 @@ struct BpdScanArgs {
   uint32_t n_allocs;
 };
 
-// Encodes slot s of `payload` to out + offs[s] - base, s < n (offs null:
-// the image's own table in meta, as for BpdScanArgs).
+// Encodes slot s of `payload` to out + offs[s] - base, s < n, and adds
+// the code's terms of the image checksum to *trailer (offs null: the whole
+// image, with the image's own table in meta as for BpdScanArgs, the payload
+// offset found from n, and the header and tables' terms added too).
 struct BpdEncodeArgs {
   const uint8_t* payload;    // raw slots
   const uint64_t* n;         // device: slots
@@ -156,6 +158,8 @@ struct BpdEncodeArgs {
   uint8_t* out;              // encoded bytes
   const uint8_t* meta;
   uint32_t n_allocs;
+  uint64_t poff;             // image byte offset of the encoded payload (offs non-null)
+  unsigned long long* trailer;  // zeroed before the image's first launch
 };
 
 // Replay restore of a compressed image's slots [0, n_slots): slot s is
@@ -172,15 +176,6 @@ struct BpdRestoreArgs {
   uint64_t n_slots;
   uint64_t* h_table;
   unsigned int* error;       // set when a slot does not decode (skipped)
-};
-
-struct BpdChecksumArgs {
-  const uint8_t* meta;       // image bytes [0, payload offset)
-  const uint8_t* enc;        // encoded payload
-  const uint64_t* n_dirty;
-  const uint64_t* total;     // encoded payload bytes (device)
-  uint32_t n_allocs;
-  unsigned long long* trailer;  // pre-zeroed; receives the image checksum
 };
 
 // Launch shape of one kernel: launched directly (launch_spec) or added to a
@@ -205,7 +200,6 @@ cudaError_t launch_chain_owner(const OwnerArgs& a, cudaStream_t st);
 cudaError_t launch_bpd_size(const BpdSizeArgs& a, uint64_t max_slots, cudaStream_t st);
 cudaError_t launch_bpd_scan(const BpdScanArgs& a, cudaStream_t st);
 cudaError_t launch_bpd_encode(const BpdEncodeArgs& a, uint64_t max_slots, cudaStream_t st);
-cudaError_t launch_bpd_checksum(const BpdChecksumArgs& a, uint64_t max_bytes, cudaStream_t st);
 cudaError_t launch_bpd_restore(const BpdRestoreArgs& a, cudaStream_t st);
 cudaError_t launch_restore_merged(const MergedRestoreArgs& a, bool compressed, cudaStream_t st);
 cudaError_t launch_hash_bytes(const uint8_t* p, uint64_t n, uint64_t first_index, uint64_t* out,
