@@ -15,6 +15,7 @@
 #include "codec.cuh"
 #include "device.cuh"
 #include "kernels.h"
+#include "restore_codec.h"
 #include "launch.cuh"
 
 namespace crum {
@@ -67,6 +68,9 @@ __device__ __forceinline__ void mark4(uint8_t* present, uint32_t w) {
 #pragma unroll
   for (int i = 0; i < 4; ++i) present[(t >> (8 * i)) & 255u] = 1;
 }
+
+// One 64-bit word's term of the image checksum: word w at index i.
+__device__ __forceinline__ uint64_t hash_word(uint64_t w, uint64_t i) { return dev::mix(w ^ (i * kPhi)); }
 
 __device__ __forceinline__ uint64_t pair64(uint32_t lo, uint32_t hi) {
   return (static_cast<uint64_t>(hi) << 32) | lo;
@@ -379,7 +383,7 @@ __global__ void __launch_bounds__(kBpdThreads, 2) k_bpd_encode(BpdEncodeArgs a) 
           w0 |= static_cast<uint64_t>(m.b[j] & 255u) << (8 * j);
           w1 |= static_cast<uint64_t>((m.b[j] == 8 ? 255u : m.k[j] - 1u) & 255u) << (8 * j);
         }
-        h += dev::hash_word(w0, u0) + dev::hash_word(w1, u0 + 1);
+        h += hash_word(w0, u0) + hash_word(w1, u0 + 1);
       }
 #pragma unroll 1
       for (int j = 0; j < 8; ++j) {
@@ -429,7 +433,7 @@ __global__ void __launch_bounds__(kBpdThreads, 2) k_bpd_encode(BpdEncodeArgs a) 
       // by the CTA: read back through L2, past the incoherent L1
       const int j = tid >> 4, q = tid & 15;
       if (m.b[j] != 8 && 8u * q < ((m.k[j] + 15u) & ~15u))
-        h += dev::hash_word(__ldcg(reinterpret_cast<const unsigned long long*>(out + m.sec[j] + 8 * q)),
+        h += hash_word(__ldcg(reinterpret_cast<const unsigned long long*>(out + m.sec[j] + 8 * q)),
                             u0 + m.sec[j] / 8 + q);
     }
   }

@@ -79,9 +79,6 @@ __device__ __forceinline__ void st_stream(void* p, uint4 v) {
 
 // Contribution of one 16-byte vector whose first word has index i0:
 // words i0 and i0+1, with c0 = i0 * PHI.
-// One 64-bit word's term of the image checksum: word w at index i.
-__device__ __forceinline__ uint64_t hash_word(uint64_t w, uint64_t i) { return mix(w ^ (i * kPhi)); }
-
 __device__ __forceinline__ uint64_t hash_vec(uint4 v, uint64_t c0) {
   const uint64_t w0 = (static_cast<uint64_t>(v.y) << 32) | v.x;
   const uint64_t w1 = (static_cast<uint64_t>(v.w) << 32) | v.z;

@@ -32,6 +32,7 @@
 #include "crum.h"
 #include "device.cuh"
 #include "kernels.h"
+#include "restore_codec.h"
 
 namespace crum {
 

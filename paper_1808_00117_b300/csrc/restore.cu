@@ -17,6 +17,7 @@
 #include "codec.cuh"
 #include "device.cuh"
 #include "kernels.h"
+#include "restore_codec.h"
 #include "launch.cuh"
 
 namespace crum {
