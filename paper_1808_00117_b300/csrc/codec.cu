@@ -299,13 +299,14 @@ __global__ void __launch_bounds__(1024) k_bpd_scan(BpdScanArgs a) {
 // reads its own 256 bytes without bank conflicts.
 //
 // The image checksum is summed as the code is written: each thread adds the
-// terms of the 64-bit words it stores from registers (a slot stored as is,
-// the header, planes stored as is, packed ranks) and, after the slot's last
-// barrier, of the dictionary words the CTA wrote; for the whole image (offs
-// null) the grid also adds the header and tables, which are final before
-// this launch.
+// terms of the 64-bit words it stores (a slot stored as is, the header,
+// planes stored as is, packed ranks, and after the slot's last barrier one
+// word of the dictionaries, which the CTA builds in shared memory); for the
+// whole image (offs null) the grid also adds the header and tables, which
+// are final before this launch.
 __global__ void __launch_bounds__(kBpdThreads, 2) k_bpd_encode(BpdEncodeArgs a) {
   __shared__ BpdSmem m;
+  __shared__ uint64_t dict_sm[8][16];  // each plane's dictionary, stored and hashed after the slot
   extern __shared__ uint4 slot_sm[];
   const int tid = threadIdx.x;
   const uint64_t n = *a.n;
@@ -320,6 +321,7 @@ __global__ void __launch_bounds__(kBpdThreads, 2) k_bpd_encode(BpdEncodeArgs a) 
       h += hash_vec(ld_stream(a.meta + 16 * v), (2 * v) * kPhi);
   if (blockIdx.x < n) enc_prefetch(a.payload + blockIdx.x * kPage, slot_sm, tid);
   for (uint64_t s = blockIdx.x; s < n; s += gridDim.x) {
+    const uint64_t off_s = off[s];  // loaded now: its latency passes under the marks
     for (uint32_t i = tid; i < 8 * 256 / 4; i += blockDim.x) reinterpret_cast<uint32_t*>(m.present)[i] = 0;
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
@@ -353,8 +355,8 @@ __global__ void __launch_bounds__(kBpdThreads, 2) k_bpd_encode(BpdEncodeArgs a) 
     }
     __syncthreads();
     bpd_plan(m);
-    uint8_t* out = a.out + (off[s] - a.base);
-    const uint64_t u0 = (poff + off[s]) / 8;  // image index of the slot's first 64-bit word
+    uint8_t* out = a.out + (off_s - a.base);
+    const uint64_t u0 = (poff + off_s) / 8;  // image index of the slot's first 64-bit word
     if (m.len == kPage) {
       // stored as is: this thread's 256 bytes, transposed back (the byte
       // transpose is its own inverse; the staging buffer already holds the
@@ -411,8 +413,9 @@ __global__ void __launch_bounds__(kBpdThreads, 2) k_bpd_encode(BpdEncodeArgs a) 
           continue;
         }
         const uint32_t k = m.k[j], dpad = (k + 15u) & ~15u;
-        if (m.present[j][tslot(tid)]) sec[m.rank[j][tslot(tid)]] = static_cast<uint8_t>(tid);
-        for (uint32_t i = k + tid; i < dpad; i += blockDim.x) sec[i] = 0;
+        uint8_t* dict = reinterpret_cast<uint8_t*>(dict_sm[j]);
+        if (m.present[j][tslot(tid)]) dict[m.rank[j][tslot(tid)]] = static_cast<uint8_t>(tid);
+        for (uint32_t i = k + tid; i < dpad; i += blockDim.x) dict[i] = 0;
         if (b == 0) continue;
         uint32_t* words = reinterpret_cast<uint32_t*>(sec + dpad) + tid * b;
         const uint64_t uw = u0 + (m.sec[j] + dpad) / 8;
@@ -427,14 +430,15 @@ __global__ void __launch_bounds__(kBpdThreads, 2) k_bpd_encode(BpdEncodeArgs a) 
         }
       }
     }
-    __syncthreads();  // the tables are read until here; the code is written
+    __syncthreads();  // the tables are read until here; the dictionaries are complete
     if (m.len != kPage && tid < 128) {
-      // the dictionaries (at most 128 bytes a plane), written byte by byte
-      // by the CTA: read back through L2, past the incoherent L1
+      // the dictionaries (at most 128 bytes a plane): one 64-bit word a thread
       const int j = tid >> 4, q = tid & 15;
-      if (m.b[j] != 8 && 8u * q < ((m.k[j] + 15u) & ~15u))
-        h += hash_word(__ldcg(reinterpret_cast<const unsigned long long*>(out + m.sec[j] + 8 * q)),
-                            u0 + m.sec[j] / 8 + q);
+      if (m.b[j] != 8 && 8u * q < ((m.k[j] + 15u) & ~15u)) {
+        const uint64_t w = dict_sm[j][q];
+        *reinterpret_cast<uint64_t*>(out + m.sec[j] + 8 * q) = w;
+        h += hash_word(w, u0 + m.sec[j] / 8 + q);
+      }
     }
   }
   h = dev::warp_sum(h);
