@@ -478,6 +478,50 @@ def link_h2d_peak(torch, nbytes=2 << 30):
     return gbs
 
 
+def link_bidir_peak(torch, nbytes=1 << 30, reps=4):
+    """Pinned host->device and device->host copies at once, one stream per
+    direction (the traffic of an end-to-end step): their summed bandwidth,
+    measured with CUDA events."""
+    dev_a = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    dev_b = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    host_a = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    host_b = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    up, down = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def run(n):
+        cur = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cur)
+        up.wait_event(e0)
+        down.wait_event(e0)
+        with torch.cuda.stream(up):
+            for _ in range(n):
+                dev_a.copy_(host_a, non_blocking=True)
+        with torch.cuda.stream(down):
+            for _ in range(n):
+                host_b.copy_(dev_b, non_blocking=True)
+        cur.wait_stream(up)
+        cur.wait_stream(down)
+        e1.record(cur)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    run(1)
+    gbs = 2 * reps * nbytes / (run(reps) * 1e-3) / 1e9
+    del dev_a, dev_b, host_a, host_b
+    return gbs
+
+
+def e2e_link_fields(e2e, bidir_gbs):
+    """The end-to-end step's link traffic (its upload plus its image) per
+    second, against pinned copies in both directions at once."""
+    moved = (e2e["h2d_bytes_per_step"] + e2e["d2h_bytes_per_step"]) / (e2e["ms_per_step"] * 1e-3) / 1e9
+    return {"link_gbs": round(moved, 2), "link_bidir_measured_gbs": round(bidir_gbs, 2),
+            "frac_of_link_bidir": round(moved / bidir_gbs, 4),
+            "link_what": "upload + image bytes per step over ms_per_step, against pinned "
+                         "host->device and device->host copies running at once"}
+
+
 def run_oversub(args):
     """Section 4.4's synthetic benchmark: two vectors of 2^32 fp32 (32 GiB) in
     managed memory on a GPU that holds half of them.  A device-memory ballast
@@ -1052,7 +1096,7 @@ def run_e2e(torch, crum, W, s, bufs, wl, steps, sh, stream, step0, dist, dev, wo
     fresh_chain()
     dt_s, _, infos_s, up_ms_s = timed(steps + 2, False)
     per = lambda x: round(world * wl.total_bytes * steps / x / 1e9, 2)
-    return {"value": per(dt), "unit": UNIT,
+    out = {"value": per(dt), "unit": UNIT,
             "h2d_bytes_per_step": int(statistics.mean(h2d)),
             "d2h_bytes_per_step": int(statistics.mean(i["image_bytes"] for i in infos)),
             "ms_per_step": round(dt * 1e3 / steps, 3),
@@ -1066,6 +1110,8 @@ def run_e2e(torch, crum, W, s, bufs, wl, steps, sh, stream, step0, dist, dev, wo
                        "submit_to_persisted_ms":
                            round(statistics.mean(i["t_persisted_ms"] for i in infos_s), 3),
                        "what": "each step waits for its image before the next upload"}}
+    out.update(e2e_link_fields(out, link_bidir_peak(torch)))
+    return out
 
 
 def run_e2e_carved(torch, crum, W, bufs, big, wl, page_byte, page_valid, steps, sh, stream,
@@ -1205,8 +1251,9 @@ def run_e2e_carved(torch, crum, W, bufs, big, wl, page_byte, page_valid, steps, 
     fresh_chain()
     dt_s, _, infos_s, up_ms_s = timed(e_steps + 2, False)
     es.destroy()
+    del landing, new
     per = lambda x: round(world * wl.total_bytes * e_steps / x / 1e9, 2)
-    return {"value": per(dt), "unit": UNIT,
+    out = {"value": per(dt), "unit": UNIT,
             "h2d_bytes_per_step": int(statistics.mean(h2d)),
             "d2h_bytes_per_step": int(statistics.mean(i["image_bytes"] for i in infos)),
             "ms_per_step": round(dt * 1e3 / e_steps, 3), "steps": e_steps,
@@ -1221,6 +1268,8 @@ def run_e2e_carved(torch, crum, W, bufs, big, wl, page_byte, page_valid, steps, 
                        "persisted_p50_ms": pct([i["t_persisted_ms"] for i in infos_s], 50),
                        "persisted_p99_ms": pct([i["t_persisted_ms"] for i in infos_s], 99),
                        "what": "each step waits for its image before the next upload"}}
+    out.update(e2e_link_fields(out, link_bidir_peak(torch)))
+    return out
 
 
 def stencil_dirty_pages(wl, plans):
