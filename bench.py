@@ -1467,6 +1467,22 @@ def run_batched(args):
     for ps in p1_sets:
         ps.destroy()
 
+    # one checkpoint at a time with the pipeline empty (the application
+    # otherwise idle): the latency of a checkpoint taken every few seconds,
+    # beside the timed steps' back-to-back latency
+    iso = []
+    for t in range(warmup + steps + 4, warmup + steps + 7):
+        app_update(t)
+        torch.cuda.synchronize()
+        im = s.checkpoint(sh)
+        im.wait()
+        iso.append(im.info())
+        im.release()
+    isolated = {"n": len(iso),
+                "captured_ms": [round(i["t_captured_ms"], 2) for i in iso],
+                "drained_ms": [round(i["t_drained_ms"], 2) for i in iso],
+                "what": "one checkpoint at a time, staging and link idle at the submit"}
+
     extra = {}
     if not stencil:
         extra = large_legs(args, torch, crum, W, s, bufs, big, wl, page_byte, offs, steps, warmup,
@@ -1499,7 +1515,8 @@ def run_batched(args):
         "latency_ms": {"captured_p50": pct([i["t_captured_ms"] for i in infos], 50),
                        "captured_p99": pct([i["t_captured_ms"] for i in infos], 99),
                        "drained_p50": pct([i["t_drained_ms"] for i in infos], 50),
-                       "drained_p99": pct([i["t_drained_ms"] for i in infos], 99)},
+                       "drained_p99": pct([i["t_drained_ms"] for i in infos], 99),
+                       "isolated": isolated},
         "batched_vs_plain_p1": {"steps": p1_steps, "what": p1_what,
                                 "batched_capture_ms": [round(x, 3) for x in batched_ms],
                                 "plain_p1_capture_ms": [round(x, 3) for x in plain_ms],
