@@ -202,3 +202,65 @@ def test_compressed_chunked_capture_equals_the_oracle(kind):
 def test_compression_rejects_external_staging():
     with pytest.raises(crum.CrumError):
         crum.CheckpointSet(compress=1, external_staging=1)
+
+
+# alphabet sizes per byte plane: each code width b = 0..8 (1 value: b = 0;
+# 129 or more: the plane is stored as is)
+ALPHABETS = [1, 2, 4, 7, 16, 30, 64, 128, 256]
+
+
+def alphabet_bytes(n_bytes, seed, shift):
+    """Bytes whose page p, byte plane j (byte j of every 64-bit word) draws
+    from exactly ALPHABETS[(p + j + shift) % 9] distinct values; the last
+    whole page has 256 values in every plane (a slot stored as is) and the
+    one before it a single value in every plane (the shortest code)."""
+    rng = np.random.default_rng(seed)
+    n_pages = W.pages_of(n_bytes)
+    out = np.zeros((n_pages, P // 8, 8), dtype=np.uint8)
+    whole = n_bytes // P
+    for p in range(n_pages):
+        for j in range(8):
+            k = ALPHABETS[(p + j + shift) % 9]
+            if p == whole - 1:
+                k = 256
+            elif p == whole - 2:
+                k = 1
+            alph = rng.choice(256, size=k, replace=False).astype(np.uint8)
+            vals = alph[rng.integers(0, k, size=P // 8)]
+            vals[rng.permutation(P // 8)[:k]] = alph  # every value of the alphabet occurs
+            out[p, :, j] = vals
+    return out.reshape(-1)[:n_bytes].copy()
+
+
+@pytest.mark.parametrize("staging_pages", [None, 6])
+def test_compressed_every_code_width_equals_the_oracle(staging_pages):
+    # every width on every plane, packed words that straddle two threads'
+    # runs (odd b), dictionaries of every size, a slot stored as is and a
+    # ragged tail; whole images and chunked ones (3 slots per half),
+    # trailer included
+    t = torch()
+    sizes = [20 * P + 4104, 9 * P]
+    hosts = [alphabet_bytes(n, seed=4400 + i, shift=i) for i, n in enumerate(sizes)]
+    bufs = [t.from_numpy(h).cuda() for h in hosts]
+    t.cuda.synchronize()
+    cfg = {"compress": 1}
+    if staging_pages:
+        cfg["staging_bytes"] = staging_pages * P
+    s = make_set(bufs, **cfg)
+    o = oracle.OracleSet(sizes, compress=True)
+    img, got = _ckpt(s, crum.FULL)
+    exp, *_ = o.checkpoint(host_copies(bufs), full=True)
+    assert first_diff(got, exp) is None
+    img.release()
+    # rewrite every third page of the first allocation with shifted widths
+    new = alphabet_bytes(sizes[0], seed=4500, shift=4)
+    for p in range(0, W.pages_of(sizes[0]), 3):
+        lo, hi = p * P, min((p + 1) * P, sizes[0])
+        bufs[0][lo:hi] = t.from_numpy(new[lo:hi]).cuda()
+    t.cuda.synchronize()
+    img, got = _ckpt(s)
+    exp, *_ = o.checkpoint(host_copies(bufs))
+    assert first_diff(got, exp) is None
+    assert img.info()["n_dirty"] == len(range(0, W.pages_of(sizes[0]), 3))
+    img.release()
+    s.destroy()
