@@ -292,6 +292,7 @@ void sequencer_done(crum::DrainSequencer* q, crum_image* img, cudaStream_t drain
 
 void planner_main(crum_set* s) {
   DeviceGuard dg(s->device);
+  crum::trace_name_thread("crum planner");
   for (;;) {
     crum_image* img;
     {
@@ -301,6 +302,7 @@ void planner_main(crum_set* s) {
       img = s->plan_q.front();
       s->plan_q.pop_front();
     }
+    crum::TraceRange tr("crum plan drain");
     Half& H = s->half[img->half];
     crum_status st = wait_event(img->compressed ? H.ev_sized : H.ev_scanned, kBackgroundLimitNs);
     std::string err = st == CRUM_OK ? "" : t_err;
@@ -393,6 +395,7 @@ void finish_image(crum_set* s, crum_image* img, crum_status st, const std::strin
 // file to write to the writer and finishes the others.
 void drainer_main(crum_set* s) {
   DeviceGuard dg(s->device);
+  crum::trace_name_thread("crum drainer");
   for (;;) {
     crum_image* img;
     {
@@ -402,6 +405,7 @@ void drainer_main(crum_set* s) {
       img = s->done_q.front();
       s->done_q.pop_front();
     }
+    crum::TraceRange tr("crum await drain");
     crum_status st = wait_event(img->ev_drained, kBackgroundLimitNs);
     if (st != CRUM_OK) {
       finish_image(s, img, st, t_err);
@@ -439,6 +443,7 @@ void drainer_main(crum_set* s) {
 // Writer: persists drained images to their files, one at a time, while
 // later images keep draining (the forked child's role, Section 3.3).
 void writer_main(crum_set* s) {
+  crum::trace_name_thread("crum writer");
   for (;;) {
     crum_image* img;
     {
@@ -448,6 +453,7 @@ void writer_main(crum_set* s) {
       img = s->write_q.front();
       s->write_q.pop_front();
     }
+    crum::TraceRange tr("crum persist");
     const crum_status st = write_file(img->host, img->image_bytes, img->sink_path.c_str(), img->do_fsync);
     finish_image(s, img, st, st == CRUM_OK ? "" : t_err);
   }
@@ -528,6 +534,7 @@ crum_status restore_merged(crum_set* s, const std::vector<crum::ChainImage>& ci,
 // while the other half drains.
 crum_status checkpoint_chunked(crum_set* s, crum_image* img, cudaStream_t app,
                                std::unique_lock<std::mutex>& lk, const crum::GatherArgs& base) {
+  crum::TraceRange tr("crum chunked capture");
   Half& H0 = s->half[img->half];
   crum_status st = wait_event(H0.ev_scanned, kBackgroundLimitNs);
   if (st != CRUM_OK) return st;
@@ -1168,6 +1175,7 @@ crum_status crum_set_info(const crum_set* s, uint32_t* n_allocs, uint64_t* n_pag
 
 crum_status crum_autotune(crum_set* s, int* hash_mapping, int* gather_mapping, double* hash_ms,
                           double* gather_ms) {
+  crum::TraceRange tr("crum_autotune");
   t_err.clear();
   if (s == nullptr) return fail(CRUM_EINVAL, "null set");
   DeviceGuard dg(s->device);
@@ -1297,6 +1305,7 @@ crum_status crum_autotune(crum_set* s, int* hash_mapping, int* gather_mapping, d
 }
 
 crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, crum_image** out) {
+  crum::TraceRange tr("crum_checkpoint");
   t_err.clear();
   if (s == nullptr || out == nullptr) return fail(CRUM_EINVAL, "null set or out");
   *out = nullptr;
@@ -1772,6 +1781,7 @@ crum_status crum_image_from_bytes(crum_set* s, const void* bytes, uint64_t n, cr
 }
 
 crum_status crum_restore(crum_set* s, const crum_image* chain_end, crum_stream_t stream) {
+  crum::TraceRange tr("crum_restore");
   t_err.clear();
   if (s == nullptr || chain_end == nullptr) return fail(CRUM_EINVAL, "null set or image");
   cudaStream_t us = static_cast<cudaStream_t>(stream);

@@ -29,12 +29,32 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+#include <sys/syscall.h>
+#include <unistd.h>
+
 #include "crum.h"
 #include "device.cuh"
 #include "kernels.h"
 #include "restore_codec.h"
 
 namespace crum {
+
+// A named range on the calling thread's NVTX timeline, for a profiler that
+// records host ranges (Nsight Systems); without one attached, push and pop
+// are a test of a function pointer.
+class TraceRange {
+ public:
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
+
+// Names the calling OS thread on that timeline.
+inline void trace_name_thread(const char* name) {
+  nvtxNameOsThreadA(static_cast<uint32_t>(syscall(SYS_gettid)), name);
+}
 
 // First-fit allocator over cudaHostAlloc arenas (pinning is slow: about
 // 0.35 s per GiB, so images draw from a pool instead of pinning per image).

@@ -262,6 +262,7 @@ crum_status start(crum_server* S, Request& r) {
 
 // Admits request r (server lock held): lends its staging region, starts it.
 void launch(crum_server* S, Request& r, int* n_ckpt, int* n_rest) {
+  crum::TraceRange tr(r.kind == CRUM_REQ_RESTORE ? "crum server restore" : "crum server checkpoint");
   Client& c = S->clients[r.client];
   r.state = 1;
   r.t_admit = Clock::now();
@@ -361,6 +362,7 @@ void admit(crum_server* S) {
 
 void server_main(crum_server* S) {
   cudaSetDevice(S->cfg.device);
+  crum::trace_name_thread("crum server");
   std::unique_lock<std::mutex> lk(S->mu);
   for (;;) {
     poll_running(S);
