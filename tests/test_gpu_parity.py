@@ -729,3 +729,49 @@ def test_max_pending_bounds_unpersisted_images(tmp_path):
     files = sorted(tmp_path.iterdir(), key=lambda x: int(x.stem.rsplit("_", 1)[1]))
     assert [f.read_bytes() for f in files] == exps
     s.destroy()
+
+
+def test_twenty_thousand_small_allocations():
+    # 20,000 allocations of 1 byte to 3 pages carved from one buffer (16-byte
+    # aligned, with gaps): the allocation table, the flattened page list and
+    # the gather's search over allocations at five times the large
+    # workload's count; full, incremental, restore onto scribbled memory
+    t = torch()
+    rng = np.random.default_rng(2020)
+    sizes = [int(x) for x in rng.integers(1, 3 * P, size=20000)]
+    gaps = rng.integers(0, 4, size=len(sizes)) * 16
+    offs, at = [], 0
+    for n, g in zip(sizes, gaps):
+        offs.append(at)
+        at += (n + 15) // 16 * 16 + int(g)
+    big = t.empty(at, dtype=t.uint8, device="cuda")
+    W.fill_(big, 2021, "u32")
+    bufs = [big[o:o + n] for o, n in zip(offs, sizes)]
+
+    def state():
+        h = big.cpu().numpy()
+        return [h[o:o + n].copy() for o, n in zip(offs, sizes)]
+
+    s = make_set(bufs)
+    o = oracle.OracleSet(sizes)
+    img0, got = _checkpoint_bytes(s)
+    s0 = state()
+    exp, *_ = o.checkpoint(s0)
+    assert first_diff(got, exp) is None
+    # rewrite the first page of every seventh allocation
+    touched = list(range(0, len(sizes), 7))
+    for i in touched:
+        W.mutate_pages_(bufs[i], np.array([0]), 2022 + i)
+    t.cuda.synchronize()
+    img1, got = _checkpoint_bytes(s)
+    s1 = state()
+    exp, d, _, _ = o.checkpoint(s1)
+    assert first_diff(got, exp) is None
+    assert parse_header(got)["n"] == int(np.count_nonzero(d)) == len(touched)
+    W.fill_(big, 2023, "u32")
+    s.restore(img1, stream_handle())
+    t.cuda.synchronize()
+    assert all(np.array_equal(g, e) for g, e in zip(state(), s1))
+    img0.release()
+    img1.release()
+    s.destroy()
