@@ -400,3 +400,52 @@ def test_size_first_does_not_starve_a_large_request():
     assert after >= 7 * Q // 2, f"{after} of {7 * Q} queued small requests completed after the large one"
     for c in [big] + small:
         c.set.destroy()
+
+
+def test_failed_requests_are_reported_and_the_server_continues(tmp_path):
+    """Host-made failures under the server: a restore request before the
+    client's first checkpoint (refused when it starts) and checkpoints whose
+    file sink cannot be written (EIO once drained).  Each is reported with
+    its status, counted as failed and has no image to take; the budget and
+    both clients stay usable: the first client's next checkpoint equals the
+    oracle's, and the sink client's next checkpoint after a failed one is
+    full, as a set's is after a failed persist."""
+    t = torch()
+    srv = crum.Server(staging_budget=1 << 28, max_inflight=4, keep_images=1)
+    a = MixClient(srv, 0, 3 * P + 4096)
+    size_b = 4 * P + 8
+    buf_b = t.empty(size_b, dtype=t.uint8, device="cuda")
+    W.fill_(buf_b, 6200, "fp32")
+    t.cuda.synchronize()
+    set_b = crum.CheckpointSet(external_staging=1, sink=crum.SINK_FILE,
+                               sink_dir=str(tmp_path / "missing" / "dir"))
+    set_b.register(buf_b.data_ptr(), size_b)
+    stream_b = t.cuda.Stream()
+    cid_b = srv.add_client(set_b, stream_b.cuda_stream)
+
+    r_restore = srv.submit(a.cid, crum.REQ_RESTORE)
+    assert srv.wait(r_restore, allow=(crum.EINVAL,))["status"] == crum.EINVAL
+    r_b = srv.submit(cid_b, crum.REQ_CHECKPOINT)
+    info = srv.wait(r_b, allow=(crum.EIO,))
+    assert info["status"] == crum.EIO and info["n_dirty"] == W.pages_of(size_b)
+    for rid in (r_restore, r_b):
+        with pytest.raises(crum.CrumError):
+            srv.take_image(rid)
+
+    ra = srv.submit(a.cid, crum.REQ_CHECKPOINT)
+    assert srv.wait(ra)["status"] == crum.OK
+    img = srv.take_image(ra)
+    exp, *_ = a.oracle.checkpoint([a.host()])
+    assert img.to_bytes() == exp
+    img.release()
+    with t.cuda.stream(stream_b):
+        W.mutate_pages_(buf_b, [1], 6201)
+    r_b2 = srv.submit(cid_b, crum.REQ_CHECKPOINT)
+    info = srv.wait(r_b2, allow=(crum.EIO,))
+    # one page rewritten, but the last image was not persisted: full again
+    assert info["status"] == crum.EIO and info["n_dirty"] == W.pages_of(size_b)
+    stats = srv.drain()
+    assert stats["failed"] == 3 and stats["completed"] == 1
+    srv.destroy()
+    a.set.destroy()
+    set_b.destroy()
