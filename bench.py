@@ -342,7 +342,7 @@ def oracle_sample(wl, sample_mib: int):
     return sizes, allocs
 
 
-def oracle_cpu_baseline(wl, sample_mib: int, steps: int, warmup: int):
+def oracle_cpu_baseline(wl, sample_mib: int, steps: int, warmup: int, compress: bool = False):
     """Time the CPU oracle's incremental checkpoint on a bounded sample of
     the workload (`oracle_sample`), the workload's dirty share of pages
     rewritten per step (each word of a chosen page xored with a nonzero
@@ -356,6 +356,9 @@ def oracle_cpu_baseline(wl, sample_mib: int, steps: int, warmup: int):
       the interpreter lock), then the oracle's dirty rule and image writer
       on one thread.  Its image must equal the single-thread image byte for
       byte at every step.
+
+    With `compress` the images are the compressed form (the oracle's codec
+    on every dirty page), as the GPU arm's are with --compress.
     """
     import oracle
     from concurrent.futures import ThreadPoolExecutor
@@ -366,7 +369,7 @@ def oracle_cpu_baseline(wl, sample_mib: int, steps: int, warmup: int):
     first = np.cumsum([0] + pages)
     n_pages = int(first[-1])
     words = [a.view(np.uint64) for a in allocs]
-    o = oracle.OracleSet(sizes)
+    o = oracle.OracleSet(sizes, compress=compress)
     o.checkpoint(allocs)  # the full base, untimed
     cores = len(os.sched_getaffinity(0))
     span = 256  # pages per slice (16 MiB): many slices per thread for balance
@@ -388,7 +391,8 @@ def oracle_cpu_baseline(wl, sample_mib: int, steps: int, warmup: int):
             a1 = time.perf_counter()
             h = np.concatenate(list(ex.map(lambda x: oracle.hash_all([x]), slices)))
             dn, _ = oracle.dirty(h, h_prev, None, False)
-            img_n = oracle.build_image(allocs, list(range(len(sizes))), h, dn, False, seq, last)
+            img_n = oracle.build_image(allocs, list(range(len(sizes))), h, dn, False, seq, last,
+                                       compress)
             a2 = time.perf_counter()
             assert int(d.sum()) == chosen.size, "oracle dirty count differs from the rewrite"
             assert img_n == img, "all-core oracle image differs from the single-thread image"
@@ -398,7 +402,8 @@ def oracle_cpu_baseline(wl, sample_mib: int, steps: int, warmup: int):
                 tn.append(a2 - a1)
     k = int(round(wl.dirty_frac * n_pages))
     sample = (f"{len(sizes)} allocation(s), {S / 2**20:.0f} MiB of the {wl.name} workload "
-              f"({n_pages} pages, {k} rewritten per step), {steps} incremental checkpoints")
+              f"({n_pages} pages, {k} rewritten per step), {steps} incremental checkpoints"
+              + (", compressed images" if compress else ""))
     m1, mn = statistics.mean(t1), statistics.mean(tn)
     return {"value": S / m1 / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": sample + ", single-thread C oracle",
@@ -417,7 +422,7 @@ def run_reference(args):
         return 0
     wl = bench_workload(args)
     t0 = time.perf_counter()
-    cb = oracle_cpu_baseline(wl, args.cpu_sample_mib, args.steps, args.warmup)
+    cb = oracle_cpu_baseline(wl, args.cpu_sample_mib, args.steps, args.warmup, bool(args.compress))
     wall = time.perf_counter() - t0
     line = {
         "impl": "reference", "metric": METRIC, "value": round(cb["value"], 4), "unit": UNIT,
@@ -919,7 +924,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:  # a single-GPU run's baseline
-        cb = oracle_cpu_baseline(wl, args.cpu_sample_mib, 3, 1)
+        cb = oracle_cpu_baseline(wl, args.cpu_sample_mib, 3, 1, bool(args.compress))
         cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "all_cores")}
 
     traffic = traffic_from_profile("k_hash_dirty", wl.name)
@@ -1664,7 +1669,7 @@ def large_legs(args, torch, crum, W, s, bufs, big, wl, page_byte, offs, steps, w
                             "140 GiB does not fit in HBM (measured on uint32_8g)"}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = oracle_cpu_baseline(wl, args.cpu_sample_mib, 3, 1)
+        cb = oracle_cpu_baseline(wl, args.cpu_sample_mib, 3, 1, bool(args.compress))
         cpu = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample", "all_cores")}
     out["cpu_baseline"] = cpu
     name = wl.name if not wl.meta.get("resized_gib") else None
