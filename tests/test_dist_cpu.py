@@ -43,6 +43,18 @@ def test_two_rank_aggregation():
         assert (rank, world) == (r, 2) and mx == 11.0 and sm == 4.5
 
 
+def test_host_budget_is_shared_by_the_ranks_of_a_node(monkeypatch):
+    # each rank pins images in its share of the node's available memory
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("LOCAL_WORLD_SIZE", "1")
+    one = bench.host_budget_bytes()
+    monkeypatch.setenv("LOCAL_WORLD_SIZE", "4")
+    four = bench.host_budget_bytes()
+    assert one > 0 and abs(4 * four - one) <= 0.05 * one  # available memory moves a little
+
+
 def test_single_rank_needs_no_process_group():
     import sys
     sys.path.insert(0, ROOT)
