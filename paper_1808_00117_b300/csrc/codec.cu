@@ -61,14 +61,6 @@ __device__ __forceinline__ void enc_prefetch(const uint8_t* slot, uint4* slot_sm
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
-// Presence marks of the four plane bytes in w (several threads may store
-// the same 1).
-__device__ __forceinline__ void mark4(uint8_t* present, uint32_t w) {
-  const uint32_t t = tslot4(w);
-#pragma unroll
-  for (int i = 0; i < 4; ++i) present[(t >> (8 * i)) & 255u] = 1;
-}
-
 // One 64-bit word's term of the image checksum: word w at index i.
 __device__ __forceinline__ uint64_t hash_word(uint64_t w, uint64_t i) { return dev::mix(w ^ (i * kPhi)); }
 
@@ -185,6 +177,8 @@ __device__ void bpd_plan(BpdSmem& m) {
   __syncthreads();
 }
 
+static_assert(kBpdAlphBytes == kBpdThreads, "one alphabet byte per thread");
+
 __global__ void __launch_bounds__(kBpdThreads) k_bpd_size(BpdSizeArgs a) {
   __shared__ BpdSmem m;
   const uint64_t n = *a.n_dirty;
@@ -221,6 +215,15 @@ __global__ void __launch_bounds__(kBpdThreads) k_bpd_size(BpdSizeArgs a) {
     __syncthreads();
     bpd_plan(m);
     if (threadIdx.x == 0) a.enc_len[s] = m.len;
+    {
+      // the alphabets for the encoder: thread t packs plane t / 32's
+      // presence of values 8 (t % 32) .. 8 (t % 32) + 7
+      const uint32_t j = threadIdx.x >> 5, v0 = 8u * (threadIdx.x & 31);
+      uint32_t bits = 0;
+#pragma unroll
+      for (uint32_t i = 0; i < 8; ++i) bits |= static_cast<uint32_t>(m.present[j][tslot(v0 + i)]) << i;
+      a.alph[s * kBpdAlphBytes + threadIdx.x] = static_cast<uint8_t>(bits);
+    }
     __syncthreads();
   }
 }
@@ -321,8 +324,9 @@ __global__ void __launch_bounds__(kBpdThreads, 2) k_bpd_encode(BpdEncodeArgs a) 
       h += hash_vec(ld_stream(a.meta + 16 * v), (2 * v) * kPhi);
   if (blockIdx.x < n) enc_prefetch(a.payload + blockIdx.x * kPage, slot_sm, tid);
   for (uint64_t s = blockIdx.x; s < n; s += gridDim.x) {
-    const uint64_t off_s = off[s];  // loaded now: its latency passes under the marks
-    for (uint32_t i = tid; i < 8 * 256 / 4; i += blockDim.x) reinterpret_cast<uint32_t*>(m.present)[i] = 0;
+    // loaded now, used after the transposition
+    const uint64_t off_s = off[s];
+    const uint32_t alph = a.alph[s * kBpdAlphBytes + tid];
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
     // this thread's 32 bytes of each plane: P[j][k] holds plane-j bytes
@@ -338,20 +342,13 @@ __global__ void __launch_bounds__(kBpdThreads, 2) k_bpd_encode(BpdEncodeArgs a) 
     }
     __syncthreads();  // every thread has its bytes: the buffer takes the next slot
     if (s + gridDim.x < n) enc_prefetch(a.payload + (s + gridDim.x) * kPage, slot_sm, tid);
-    // the sample: each thread's first 4 bytes of every plane (1,024 bytes
-    // of every plane, spread over the slot); a byte equal to the one before
-    // it in its plane needs no second mark (float planes holding sign and
-    // exponent repeat often)
+    // the slot's alphabets as the size kernel found them (so both plan the
+    // same layout): thread t expands plane t / 32's presence of values
+    // 8 (t % 32) .. 8 (t % 32) + 7
+    {
+      const uint32_t j = tid >> 5, v0 = 8u * (tid & 31);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) mark4(m.present[j], P[j][0]);
-    __syncthreads();
-    bpd_open_planes(m);
-    const uint32_t open = m.open;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      if (!(open & (1u << j))) continue;  // stored as is: no more marks, no ranks
-#pragma unroll
-      for (int k = 1; k < 8; ++k) mark4(m.present[j], P[j][k]);
+      for (uint32_t i = 0; i < 8; ++i) m.present[j][tslot(v0 + i)] = static_cast<uint8_t>((alph >> i) & 1u);
     }
     __syncthreads();
     bpd_plan(m);

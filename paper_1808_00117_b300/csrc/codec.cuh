@@ -48,6 +48,10 @@ struct BpdSmem {
 // still at most 128 values are marked in full and ranked.
 constexpr uint32_t kBpdRawAlphabet = 129;
 
+// The alphabets the size kernel found, handed to the encoder: bit v % 8 of
+// byte 32 j + v / 8 is plane j's presence of value v (256 bytes a slot).
+constexpr uint32_t kBpdAlphBytes = 8 * 256 / 8;
+
 // Where value x sits in a plane's 256-byte presence and rank tables: bit 4
 // is flipped for x >= 128, so x and x + 128 (the same bank otherwise) fall
 // into banks 4 apart.  Float sign-and-exponent planes hold exactly such

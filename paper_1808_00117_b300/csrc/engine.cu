@@ -585,7 +585,7 @@ crum_status checkpoint_chunked(crum_set* s, crum_image* img, cudaStream_t app,
       // this chunk's slots: sizes, offsets after enc_base, code, checksum
       const uint64_t m = s1 - s0;
       CK(cudaMemcpyAsync(H.cn, &m, sizeof m, cudaMemcpyHostToDevice, s->cap_stream));
-      crum::BpdSizeArgs za{H.payload, H.cn, H.enc_len};
+      crum::BpdSizeArgs za{H.payload, H.cn, H.enc_len, H.alph};
       CK(crum::launch_bpd_size(za, m, s->cap_stream));
       crum::BpdScanArgs qa{H.enc_len, H.cn, offs + s0, enc_base, H.ctotal, H.mailbox_dev, H0.meta,
                            static_cast<uint32_t>(A)};
@@ -594,7 +594,7 @@ crum_status checkpoint_chunked(crum_set* s, crum_image* img, cudaStream_t app,
       if ((st = wait_event(H.ev_sized, kBackgroundLimitNs)) != CRUM_OK) return st;
       bytes = reinterpret_cast<volatile uint64_t*>(H.mailbox)[3];
       crum::BpdEncodeArgs ea{H.payload, H.cn, offs + s0, enc_base, H.cpay, H0.meta, static_cast<uint32_t>(A),
-                             poff, reinterpret_cast<unsigned long long*>(H0.scalars + 1)};
+                             poff, reinterpret_cast<unsigned long long*>(H0.scalars + 1), H.alph};
       CK(crum::launch_bpd_encode(ea, m, s->cap_stream));
       src = H.cpay;
       host_off = poff + enc_base;
@@ -728,10 +728,10 @@ crum_status graph_build(crum_set* s, int h, crum_image* img, const crum::HashArg
     // the encoding stage behind the capture: its arguments are this half's
     // buffers, fixed for the graph's life, so the nodes are never updated
     const uint32_t A = static_cast<uint32_t>(s->allocs.size());
-    crum::BpdSizeArgs za{H.payload, H.scalars, H.enc_len};
+    crum::BpdSizeArgs za{H.payload, H.scalars, H.enc_len, H.alph};
     crum::BpdScanArgs qa{H.enc_len, H.scalars, nullptr, 0, H.ctotal, H.mailbox_dev, H.meta, A};
     crum::BpdEncodeArgs ea{H.payload, H.scalars, nullptr, 0, H.cpay, H.meta, A, 0,
-                           reinterpret_cast<unsigned long long*>(H.scalars + 1)};
+                           reinterpret_cast<unsigned long long*>(H.scalars + 1), H.alph};
     void* a_z[] = {&za};
     void* a_q[] = {&qa};
     void* a_e[] = {&ea};
@@ -1027,6 +1027,7 @@ crum_status crum_set_create(const crum_config* cfg_in, crum_set** out) {
                     (unsigned long long)(s->half_slots * kPage));
       }
       CK(cudaMalloc(&H.enc_len, std::max<uint64_t>(s->half_slots, 1) * sizeof(uint32_t)));
+      CK(cudaMalloc(&H.alph, std::max<uint64_t>(s->half_slots, 1) * crum::kBpdAlphBytes));
       CK(cudaMalloc(&H.ctotal, sizeof(uint64_t)));
       CK(cudaMalloc(&H.cn, 2 * sizeof(uint64_t)));
       CK(cudaEventCreateWithFlags(&H.ev_sized, cudaEventDisableTiming));
@@ -1081,6 +1082,7 @@ crum_status crum_set_destroy(crum_set* s) {
     cudaEventDestroy(H.ev_drained);
     cudaFree(H.cpay);
     cudaFree(H.enc_len);
+    cudaFree(H.alph);
     cudaFree(H.ctotal);
     cudaFree(H.cn);
     if (H.ev_sized) cudaEventDestroy(H.ev_sized);
@@ -1453,7 +1455,7 @@ crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, cr
     if (ce == cudaSuccess && fast && img->compressed) {
       // the application has its memory back; the staged slots are encoded
       // behind it: sizes, offsets and header, then the code and checksum
-      crum::BpdSizeArgs za{H.payload, H.scalars, H.enc_len};
+      crum::BpdSizeArgs za{H.payload, H.scalars, H.enc_len, H.alph};
       ce = crum::launch_bpd_size(za, s->n_pages, s->cap_stream);
       // the whole image: the kernels place the offset table after the
       // hashes once n is known on the device
@@ -1461,7 +1463,7 @@ crum_status crum_checkpoint(crum_set* s, crum_stream_t app_stream, int flags, cr
       if (ce == cudaSuccess) ce = crum::launch_bpd_scan(qa, s->cap_stream);
       if (ce == cudaSuccess) ce = cudaEventRecord(H.ev_sized, s->cap_stream);
       crum::BpdEncodeArgs ea{H.payload, H.scalars, nullptr, 0, H.cpay, H.meta, img->n_allocs, 0,
-                             reinterpret_cast<unsigned long long*>(H.scalars + 1)};
+                             reinterpret_cast<unsigned long long*>(H.scalars + 1), H.alph};
       if (ce == cudaSuccess) ce = cudaMemsetAsync(H.scalars + 1, 0, sizeof(uint64_t), s->cap_stream);
       if (ce == cudaSuccess) ce = crum::launch_bpd_encode(ea, s->n_pages, s->cap_stream);
       if (ce == cudaSuccess) ce = cudaEventRecord(H.ev_encoded, s->cap_stream);

@@ -101,6 +101,7 @@ struct Half {
   // compressed images (cfg.compress)
   uint8_t* cpay = nullptr;           // encoded payload
   uint32_t* enc_len = nullptr;       // encoded length of every slot
+  uint8_t* alph = nullptr;           // every slot's alphabets, size kernel -> encoder
   uint64_t* ctotal = nullptr;        // device: encoded payload bytes
   uint64_t* cn = nullptr;            // device: [0] slots of a chunk, [1] scratch
   cudaEvent_t ev_sized = nullptr;    // encoded sizes, offsets and header written

@@ -63,6 +63,7 @@ struct BpdSizeArgs {
   const uint8_t* payload;    // raw slots, slot s at payload + s * 64 KiB
   const uint64_t* n_dirty;   // device
   uint32_t* enc_len;         // out: encoded length of every slot
+  uint8_t* alph;             // out: every slot's alphabets (kBpdAlphBytes a slot)
 };
 
 // Offsets of `n` encoded slots (base + exclusive prefix of their lengths)
@@ -95,6 +96,7 @@ struct BpdEncodeArgs {
   uint32_t n_allocs;
   uint64_t poff;             // image byte offset of the encoded payload (offs non-null)
   unsigned long long* trailer;  // zeroed before the image's first launch
+  const uint8_t* alph;       // the size kernel's alphabets of these slots
 };
 
 // Replay restore of a compressed image's slots [0, n_slots): slot s is
